@@ -1,0 +1,153 @@
+"""Plain FP64 CPU oracle for push/pull PageRank and BFS (ctypes over oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg are the only callers.  The CUDA library never
+imports this package and this package never imports the library; they share no
+code.  Inputs come from the ``graphgen`` package, which holds no method
+arithmetic.
+
+What each function computes, with the paper passage it follows, is documented
+in ``oracle.c``.  Parity status: every function here is pinned by the
+``-m "not gpu"`` tests in ``tests/test_oracle_pins.py`` (closed forms, a dense
+linear solve, brute-force shortest paths, a hand-derived worked example and
+finite differences).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_SO = os.path.join(_HERE, "_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+PUSH, PULL = 0, 1
+TOPDOWN, BOTTOMUP = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into _oracle.so (gcc -O2, OpenMP, strict IEEE: no -ffast-math)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _get():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            c = ctypes
+            vp = c.c_void_p
+            lib.or_graph_new.restype = vp
+            lib.or_graph_new.argtypes = [c.c_int64, c.c_int64, vp, vp, vp]
+            lib.or_graph_free.restype = None
+            lib.or_graph_free.argtypes = [vp]
+            lib.or_pagerank.restype = c.c_int
+            lib.or_pagerank.argtypes = [vp, c.c_int, c.c_double, c.c_int, c.c_double, vp, vp, vp,
+                                        c.POINTER(c.c_int), c.POINTER(c.c_double), c.c_int]
+            lib.or_bfs_fifo.restype = c.c_int64
+            lib.or_bfs_fifo.argtypes = [vp, c.c_int32, vp, vp]
+            lib.or_bfs_levelsync.restype = c.c_int
+            lib.or_bfs_levelsync.argtypes = [vp, c.c_int32, vp, c.c_int, vp, vp, vp, c.c_int]
+            lib.or_pagerank_adjoint.restype = c.c_int
+            lib.or_pagerank_adjoint.argtypes = [vp, c.c_double, vp, vp, c.c_int, c.c_double, vp, vp, vp,
+                                                c.POINTER(c.c_double)]
+            lib.or_max_threads.restype = c.c_int
+            lib.or_max_threads.argtypes = []
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+class OracleGraph:
+    """The oracle's own adjacency, rebuilt from an edge list (src[e] -> dst[e],
+    optional per-edge weight w[e] = P_{dst,src})."""
+
+    def __init__(self, n: int, src, dst, w=None):
+        self._lib = _get()
+        self.n = int(n)
+        self._src = np.ascontiguousarray(src, dtype=np.int32)
+        self._dst = np.ascontiguousarray(dst, dtype=np.int32)
+        self.m = int(self._src.shape[0])
+        if self.m and (self._src.min() < 0 or self._src.max() >= n or self._dst.min() < 0
+                       or self._dst.max() >= n):
+            raise ValueError("edge endpoint outside [0, n)")
+        self._w = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+        self._h = self._lib.or_graph_new(self.n, self.m, _ptr(self._src), _ptr(self._dst), _ptr(self._w))
+
+    @classmethod
+    def from_graph(cls, g, weighted: bool = True):
+        """From a graphgen.Graph: its edge list in CSR order (and CSR weights)."""
+        src, dst = g.edges()
+        return cls(g.n, src, dst, g.csr_w if weighted else None)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.or_graph_free(h)
+            self._h = None
+
+    # ------------------------------------------------------------ PageRank
+    def pagerank(self, variant: int = PULL, damping: float = 0.85, iters: int = 20, tol: float = 0.0,
+                 personalization=None, x0=None, nthreads: int = 1):
+        """Power iteration (Algorithm 1).  Returns (x, iters_done, residual, converged)."""
+        x = np.empty(self.n, dtype=np.float64)
+        s = None if personalization is None else np.ascontiguousarray(personalization, dtype=np.float64)
+        x0a = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+        k = ctypes.c_int(0)
+        r = ctypes.c_double(0.0)
+        rc = self._lib.or_pagerank(self._h, int(variant), float(damping), int(iters), float(tol),
+                                   _ptr(s), _ptr(x0a), _ptr(x), ctypes.byref(k), ctypes.byref(r),
+                                   int(nthreads))
+        return x, k.value, r.value, rc == 0
+
+    # ------------------------------------------------------------ BFS
+    def bfs(self, src: int):
+        """FIFO BFS over out-edges.  Returns (level, parent) int32 arrays."""
+        level = np.empty(self.n, dtype=np.int32)
+        parent = np.empty(self.n, dtype=np.int32)
+        self._lib.or_bfs_fifo(self._h, int(src), _ptr(level), _ptr(parent))
+        return level, parent
+
+    def bfs_levelsync(self, src: int, dirs=(TOPDOWN,), max_levels: int = 4096):
+        """Level-synchronous BFS (Algorithm 3, ready = 1) with one direction per
+        level (0 top-down/push, 1 bottom-up/pull; the last entry repeats).
+        Returns (level, parent, dirs_used)."""
+        level = np.empty(self.n, dtype=np.int32)
+        parent = np.empty(self.n, dtype=np.int32)
+        d = np.ascontiguousarray(np.asarray(dirs, dtype=np.int8))
+        used = np.full(max_levels, -1, dtype=np.int8)
+        L = self._lib.or_bfs_levelsync(self._h, int(src), _ptr(d), int(d.shape[0]), _ptr(level),
+                                       _ptr(parent), _ptr(used), max_levels)
+        return level, parent, used[:min(L, max_levels)].copy()
+
+    # ------------------------------------------------------------ adjoint
+    def pagerank_adjoint(self, x, g, damping: float = 0.85, iters: int = 10000, tol: float = 1e-14):
+        """Adjoint of the fixed point for L = g.x.  Returns (lambda, grad_s,
+        grad_w in input edge order, iters_done, residual)."""
+        lam = np.empty(self.n, dtype=np.float64)
+        gs = np.empty(self.n, dtype=np.float64)
+        gw = np.empty(self.m, dtype=np.float64)
+        r = ctypes.c_double(0.0)
+        xa = np.ascontiguousarray(x, dtype=np.float64)
+        ga = np.ascontiguousarray(g, dtype=np.float64)
+        k = self._lib.or_pagerank_adjoint(self._h, float(damping), _ptr(xa), _ptr(ga), int(iters),
+                                          float(tol), _ptr(lam), _ptr(gs), _ptr(gw), ctypes.byref(r))
+        return lam, gs, gw, k, r.value
+
+
+def max_threads() -> int:
+    return int(_get().or_max_threads())

@@ -1,0 +1,356 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle for push/pull PageRank and BFS.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg may load this file.  The CUDA library never calls it and it
+ * never calls the CUDA library; the two share no code, headers or tables.  The
+ * only thing both sides consume is the graph produced by the input generator.
+ *
+ * Everything here is the definition written out, in the order the paper states
+ * it, in double precision, with no blocking, fusion or reordering:
+ *
+ *   - Graph (Section 2.2): the oracle rebuilds its own adjacency arrays (out-
+ *     and in-neighbours, n+1 offsets each) from the raw edge list it is given.
+ *     Directed graphs (Section 4.8, "Directed Graphs"): pushing walks out-edges,
+ *     pulling walks in-edges.
+ *   - PageRank (Section 3.1 formula; Algorithm 1, push- and pull-based PR):
+ *       y[v] = (1-d) s[v] + d * sum_{(u->v) in E} P_vu x[u]
+ *     with P_vu = 1/deg_out(u) (unweighted) or the stored weight w_uv
+ *     (weighted), s = 1/n unless a personalization vector is given.  Pull
+ *     computes each y[v] from v's in-edges; push zeroes y, lets every u add
+ *     d*P_vu*x[u] into y[v] for its out-edges, then adds (1-d)s.
+ *   - BFS (Section 3.3; Algorithm 3 with every ready counter equal to one): a
+ *     textbook FIFO BFS, and the level-synchronous form whose levels are
+ *     explored either top-down (push: frontier vertices scan out-edges) or
+ *     bottom-up (pull: unvisited vertices scan in-edges for a frontier vertex).
+ *   - Adjoint of the PageRank fixed point (not in the paper): lambda solves
+ *     (I - d P^T) lambda = g; dL/ds = (1-d) lambda; dL/dP_vu = d lambda_v x_u.
+ *
+ * Readings of the paper where it is silent or ambiguous (each is a choice the
+ * CUDA path makes identically):
+ *   - x0 = 1/n (Algorithm 1 initialises the ranks to the damping factor; the
+ *     fixed point does not depend on x0, fixed-sweep comparisons do).
+ *   - `iters` counts the sweeps actually performed (Algorithm 1's loop runs
+ *     L-1 sweeps for L steps).
+ *   - Jacobi double buffering: every y is computed from the previous x, then
+ *     x <- y (Algorithm 1 writes pr[v] inside the parallel loop).
+ *   - Dangling vertices (deg_out = 0) contribute nothing; no redistribution.
+ *   - Convergence: L1 norm of y - x after each sweep, stop when < tol or after
+ *     `iters` sweeps; tol = 0 runs exactly `iters` sweeps.
+ *   - Bottom-up BFS stops scanning a vertex's in-edges at the first frontier
+ *     neighbour (with ready = 1 the counter reaches zero there).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct or_graph {
+    int64_t n, m;
+    int64_t *out_off; /* n+1 */
+    int32_t *out_idx; /* m: heads of out-edges */
+    int64_t *out_eid; /* m: input edge id of each out-edge slot */
+    int64_t *in_off;  /* n+1 */
+    int32_t *in_idx;  /* m: tails of in-edges */
+    int64_t *in_eid;  /* m: input edge id of each in-edge slot */
+    double *w;        /* m or NULL: weight of input edge e, P_vu for e = (u->v) */
+    int64_t *deg_out; /* n */
+} or_graph;
+
+static void or_set_threads(int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+}
+
+/* Adjacency arrays of Section 2.2 built by a counting sort of the edge list;
+ * within a vertex the neighbours keep the order of the input list. */
+or_graph *or_graph_new(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const float *w) {
+    or_graph *g = (or_graph *)calloc(1, sizeof(or_graph));
+    g->n = n;
+    g->m = m;
+    g->out_off = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    g->in_off = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    g->out_idx = (int32_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int32_t));
+    g->in_idx = (int32_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int32_t));
+    g->out_eid = (int64_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int64_t));
+    g->in_eid = (int64_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int64_t));
+    g->deg_out = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+    g->w = NULL;
+    if (w) {
+        g->w = (double *)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+        for (int64_t e = 0; e < m; ++e) g->w[e] = (double)w[e];
+    }
+    for (int64_t e = 0; e < m; ++e) {
+        g->out_off[src[e] + 1]++;
+        g->in_off[dst[e] + 1]++;
+    }
+    for (int64_t v = 0; v < n; ++v) {
+        g->out_off[v + 1] += g->out_off[v];
+        g->in_off[v + 1] += g->in_off[v];
+        g->deg_out[v] = 0;
+    }
+    int64_t *po = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int64_t *pi = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    for (int64_t v = 0; v < n; ++v) {
+        po[v] = g->out_off[v];
+        pi[v] = g->in_off[v];
+    }
+    for (int64_t e = 0; e < m; ++e) {
+        const int32_t u = src[e], v = dst[e];
+        g->out_idx[po[u]] = v;
+        g->out_eid[po[u]++] = e;
+        g->in_idx[pi[v]] = u;
+        g->in_eid[pi[v]++] = e;
+        g->deg_out[u]++;
+    }
+    free(po);
+    free(pi);
+    return g;
+}
+
+void or_graph_free(or_graph *g) {
+    if (!g) return;
+    free(g->out_off);
+    free(g->in_off);
+    free(g->out_idx);
+    free(g->in_idx);
+    free(g->out_eid);
+    free(g->in_eid);
+    free(g->w);
+    free(g->deg_out);
+    free(g);
+}
+
+/* Transition entry P_vu of input edge e = (u -> v). */
+static inline double or_P(const or_graph *g, int64_t e, int32_t u) {
+    if (g->w) return g->w[e];
+    return 1.0 / (double)g->deg_out[u];
+}
+
+/*
+ * PageRank power iteration (Section 3.1; Algorithm 1).
+ *   variant 0 = push: y = 0; for u, for (u->v): y[v] += d P_vu x[u]; y += (1-d) s.
+ *   variant 1 = pull: for v: y[v] = (1-d) s[v] + d sum_{(u->v)} P_vu x[u].
+ * s (nullable) is the personalization vector (uniform 1/n when NULL); x0
+ * (nullable) the starting vector (1/n when NULL).  Runs until the L1 norm of
+ * y - x is below tol or `iters` sweeps are done; x_out receives the last y.
+ * nthreads > 1 parallelises the pull variant over v (each y[v] is still summed
+ * in in-edge order by one thread, so the result does not change).
+ * Returns 0 if converged (or tol == 0), 1 if the sweep cap was hit.
+ */
+int or_pagerank(const or_graph *g, int variant, double d, int iters, double tol, const double *s,
+                const double *x0, double *x_out, int *iters_done, double *residual, int nthreads) {
+    const int64_t n = g->n;
+    double *x = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    double *y = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    for (int64_t v = 0; v < n; ++v) x[v] = x0 ? x0[v] : 1.0 / (double)n;
+    or_set_threads(nthreads);
+    int k = 0;
+    double r = 0.0;
+    int converged = 0;
+    while (k < iters) {
+        if (variant == 0) {
+            for (int64_t v = 0; v < n; ++v) y[v] = 0.0;
+            for (int64_t u = 0; u < n; ++u)
+                for (int64_t j = g->out_off[u]; j < g->out_off[u + 1]; ++j)
+                    y[g->out_idx[j]] += d * or_P(g, g->out_eid[j], (int32_t)u) * x[u];
+            for (int64_t v = 0; v < n; ++v) y[v] += (1.0 - d) * (s ? s[v] : 1.0 / (double)n);
+        } else {
+#pragma omp parallel for schedule(dynamic, 1024) if (nthreads > 1)
+            for (int64_t v = 0; v < n; ++v) {
+                double acc = 0.0;
+                for (int64_t j = g->in_off[v]; j < g->in_off[v + 1]; ++j) {
+                    const int32_t u = g->in_idx[j];
+                    acc += or_P(g, g->in_eid[j], u) * x[u];
+                }
+                y[v] = (1.0 - d) * (s ? s[v] : 1.0 / (double)n) + d * acc;
+            }
+        }
+        r = 0.0;
+        for (int64_t v = 0; v < n; ++v) r += fabs(y[v] - x[v]);
+        double *t = x;
+        x = y;
+        y = t;
+        ++k;
+        if (r < tol) {
+            converged = 1;
+            break;
+        }
+    }
+    if (iters <= 0) r = 0.0;
+    memcpy(x_out, x, (size_t)n * sizeof(double));
+    if (iters_done) *iters_done = k;
+    if (residual) *residual = r;
+    free(x);
+    free(y);
+    return (converged || tol <= 0.0) ? 0 : 1;
+}
+
+/*
+ * Textbook FIFO BFS from src over out-edges (Section 3.3): level[src] = 0,
+ * parent[src] = src; a vertex is labelled by the first vertex that discovers
+ * it in queue order.  Unreached vertices get level -1 and parent -1.
+ * Returns the number of vertices reached.
+ */
+int64_t or_bfs_fifo(const or_graph *g, int32_t src, int32_t *level, int32_t *parent) {
+    const int64_t n = g->n;
+    for (int64_t v = 0; v < n; ++v) {
+        level[v] = -1;
+        parent[v] = -1;
+    }
+    if (src < 0 || src >= n) return 0;
+    int32_t *queue = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int64_t head = 0, tail = 0;
+    queue[tail++] = src;
+    level[src] = 0;
+    parent[src] = src;
+    while (head < tail) {
+        const int32_t v = queue[head++];
+        for (int64_t j = g->out_off[v]; j < g->out_off[v + 1]; ++j) {
+            const int32_t w = g->out_idx[j];
+            if (level[w] == -1) {
+                level[w] = level[v] + 1;
+                parent[w] = v;
+                queue[tail++] = w;
+            }
+        }
+    }
+    free(queue);
+    return tail;
+}
+
+/*
+ * Level-synchronous BFS of Algorithm 3 with ready = 1 (so the accumulated value
+ * R is the level and the vertex it came from), one direction per level:
+ *   dir 0, top-down (push): for every v in the frontier F, in frontier order,
+ *     for every out-edge (v->w) with w unvisited: w gets level L+1 and parent v
+ *     and joins the next frontier.
+ *   dir 1, bottom-up (pull): for every unvisited v in vertex order, scan its
+ *     in-edges (w->v); at the first w in F, v gets level L+1 and parent w and
+ *     joins the next frontier; the scan of v stops there.
+ * The direction of level L (the one expanding frontier L into L+1) is
+ * dirs[L] if L < ndirs, else dirs[ndirs-1] (0 when ndirs == 0).  dirs_used
+ * (nullable, capacity max_levels) receives the direction actually used per
+ * level.  Returns the number of levels (depth + 1; 0 if src is invalid).
+ */
+int or_bfs_levelsync(const or_graph *g, int32_t src, const int8_t *dirs, int ndirs, int32_t *level,
+                     int32_t *parent, int8_t *dirs_used, int max_levels) {
+    const int64_t n = g->n;
+    for (int64_t v = 0; v < n; ++v) {
+        level[v] = -1;
+        parent[v] = -1;
+    }
+    if (src < 0 || src >= n) return 0;
+    int32_t *F = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *next = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    uint8_t *inF = (uint8_t *)calloc((size_t)n, 1);
+    int64_t nf = 0;
+    F[nf++] = src;
+    level[src] = 0;
+    parent[src] = src;
+    int L = 0;
+    while (nf > 0) {
+        const int dir = ndirs == 0 ? 0 : dirs[L < ndirs ? L : ndirs - 1];
+        if (dirs_used && L < max_levels) dirs_used[L] = (int8_t)dir;
+        int64_t nn = 0;
+        if (dir == 0) {
+            for (int64_t i = 0; i < nf; ++i) {
+                const int32_t v = F[i];
+                for (int64_t j = g->out_off[v]; j < g->out_off[v + 1]; ++j) {
+                    const int32_t w = g->out_idx[j];
+                    if (level[w] == -1) {
+                        level[w] = L + 1;
+                        parent[w] = v;
+                        next[nn++] = w;
+                    }
+                }
+            }
+        } else {
+            for (int64_t i = 0; i < nf; ++i) inF[F[i]] = 1;
+            for (int64_t v = 0; v < n; ++v) {
+                if (level[v] != -1) continue;
+                for (int64_t j = g->in_off[v]; j < g->in_off[v + 1]; ++j) {
+                    const int32_t w = g->in_idx[j];
+                    if (inF[w]) {
+                        level[v] = L + 1;
+                        parent[v] = w;
+                        next[nn++] = (int32_t)v;
+                        break;
+                    }
+                }
+            }
+            for (int64_t i = 0; i < nf; ++i) inF[F[i]] = 0;
+        }
+        int32_t *t = F;
+        F = next;
+        next = t;
+        nf = nn;
+        ++L;
+    }
+    free(F);
+    free(next);
+    free(inF);
+    return L;
+}
+
+/*
+ * Adjoint of the PageRank fixed point x = (1-d) s + d P x for the loss
+ * L = g^T x (implicit differentiation; not in the paper).
+ *   lambda solves (I - d P^T) lambda = g by the Jacobi iteration
+ *     lambda_u <- g_u + d sum_{(u->v) in E} P_vu lambda_v
+ *   started from lambda = g, until the L1 change is below tol or `iters`.
+ *   grad_s[v] = (1-d) lambda_v;  grad_w[e] = d lambda_v x_u for edge e = (u->v),
+ *   in input edge order.  x is the fixed point the gradient is taken at.
+ * Returns the number of iterations done.
+ */
+int or_pagerank_adjoint(const or_graph *g, double d, const double *x, const double *gv, int iters,
+                        double tol, double *lambda, double *grad_s, double *grad_w, double *residual) {
+    const int64_t n = g->n;
+    double *lam = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    double *nxt = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    for (int64_t v = 0; v < n; ++v) lam[v] = gv[v];
+    int k = 0;
+    double r = 0.0;
+    while (k < iters) {
+        for (int64_t u = 0; u < n; ++u) {
+            double acc = 0.0;
+            for (int64_t j = g->out_off[u]; j < g->out_off[u + 1]; ++j)
+                acc += or_P(g, g->out_eid[j], (int32_t)u) * lam[g->out_idx[j]];
+            nxt[u] = gv[u] + d * acc;
+        }
+        r = 0.0;
+        for (int64_t v = 0; v < n; ++v) r += fabs(nxt[v] - lam[v]);
+        double *t = lam;
+        lam = nxt;
+        nxt = t;
+        ++k;
+        if (r < tol) break;
+    }
+    for (int64_t v = 0; v < n; ++v) {
+        lambda[v] = lam[v];
+        grad_s[v] = (1.0 - d) * lam[v];
+    }
+    if (grad_w)
+        for (int64_t u = 0; u < n; ++u)
+            for (int64_t j = g->out_off[u]; j < g->out_off[u + 1]; ++j)
+                grad_w[g->out_eid[j]] = d * lam[g->out_idx[j]] * x[u];
+    if (residual) *residual = r;
+    free(lam);
+    free(nxt);
+    return k;
+}
+
+/* Number of OpenMP threads a parallel region gets (1 without OpenMP). */
+int or_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

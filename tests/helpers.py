@@ -1,0 +1,156 @@
+"""Test helpers: golden-file parsing and independent reference computations
+(numpy linear algebra, brute-force shortest paths) used to pin the oracle."""
+from __future__ import annotations
+
+import os
+from fractions import Fraction
+
+import numpy as np
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _frac(tok: str) -> Fraction:
+    return Fraction(tok)
+
+
+def parse_pagerank_cases(path=os.path.join(GOLDEN, "pagerank_worked_examples.txt")):
+    cases, cur = [], None
+    for line in open(path):
+        line = line.split("#", 1)[0].strip()
+        if not line:
+            continue
+        key, *vals = line.split()
+        if key == "case":
+            cur = {"name": vals[0]}
+        elif key == "end":
+            cases.append(cur)
+            cur = None
+        elif key == "n":
+            cur["n"] = int(vals[0])
+        elif key == "d":
+            cur["d"] = _frac(vals[0])
+        elif key == "edges":
+            src, dst, w = [], [], []
+            for tok in vals:
+                uv, _, wt = tok.partition(":")
+                u, v = uv.split(">")
+                src.append(int(u))
+                dst.append(int(v))
+                w.append(_frac(wt) if wt else None)
+            cur["src"], cur["dst"] = src, dst
+            cur["w"] = None if all(x is None for x in w) else w
+        elif key in ("sweep1", "sweep2", "fixed"):
+            cur[key] = [_frac(t) for t in vals]
+        elif key in ("res1", "res2"):
+            cur[key] = _frac(vals[0])
+    return cases
+
+
+def parse_bfs_case(path=os.path.join(GOLDEN, "bfs_worked_example.txt")):
+    out = {}
+    for line in open(path):
+        line = line.split("#", 1)[0].strip()
+        if not line:
+            continue
+        key, *vals = line.split()
+        if key == "edges":
+            out["src_e"] = [int(t.split(">")[0]) for t in vals]
+            out["dst_e"] = [int(t.split(">")[1]) for t in vals]
+        elif key in ("n", "src"):
+            out[key] = int(vals[0])
+        else:
+            out[key] = [int(t) for t in vals]
+    return out
+
+
+def dense_transition(n, src, dst, w=None):
+    """Column-stochastic-or-leaky P with P[v, u] = w_e or 1/deg_out(u) for edge e=(u->v)."""
+    src = np.asarray(src)
+    dst = np.asarray(dst)
+    P = np.zeros((n, n))
+    deg = np.bincount(src, minlength=n) if len(src) else np.zeros(n, dtype=np.int64)
+    for e in range(len(src)):
+        u, v = src[e], dst[e]
+        P[v, u] += (float(w[e]) if w is not None else 1.0 / deg[u])
+    return P
+
+
+def dense_pagerank(n, src, dst, d, s=None, w=None):
+    """Fixed point of x = (1-d)s + dPx by LU with partial pivoting (numpy.linalg.solve)."""
+    P = dense_transition(n, src, dst, w)
+    s = np.full(n, 1.0 / n) if s is None else np.asarray(s, dtype=np.float64)
+    return np.linalg.solve(np.eye(n) - d * P, (1 - d) * s)
+
+
+def floyd_warshall_levels(n, src, dst, root):
+    """Unit-weight all-pairs shortest paths by Floyd-Warshall; row `root` as BFS levels."""
+    INF = np.inf
+    D = np.full((n, n), INF)
+    np.fill_diagonal(D, 0.0)
+    for u, v in zip(src, dst):
+        if u != v:
+            D[u, v] = min(D[u, v], 1.0)
+    for k in range(n):
+        D = np.minimum(D, D[:, k:k + 1] + D[k:k + 1, :])
+    row = D[root]
+    return np.where(np.isinf(row), -1, row).astype(np.int64)
+
+
+def check_parents(n, src_e, dst_e, root, level, parent):
+    """BFS-tree validity: root is its own parent at level 0; every reached v != root
+    has an edge parent[v] -> v and level[parent[v]] == level[v] - 1; unreached
+    vertices have parent -1.  Returns a list of violations (empty when valid)."""
+    edges = set(zip(np.asarray(src_e).tolist(), np.asarray(dst_e).tolist()))
+    bad = []
+    if level[root] != 0 or parent[root] != root:
+        bad.append(("root", root))
+    for v in range(n):
+        if v == root:
+            continue
+        if level[v] == -1:
+            if parent[v] != -1:
+                bad.append(("unreached-has-parent", v))
+            continue
+        p = parent[v]
+        if p < 0 or (p, v) not in edges or level[p] != level[v] - 1:
+            bad.append(("bad-parent", v, p))
+    return bad
+
+
+def check_parents_np(csr_off, csr_idx, root, level, parent):
+    """Vectorised check_parents for large graphs (edge existence by searching the
+    sorted CSR row of the parent).  Returns the number of violations."""
+    n = level.shape[0]
+    level = level.astype(np.int64)
+    parent = parent.astype(np.int64)
+    bad = 0
+    bad += int(level[root] != 0) + int(parent[root] != root)
+    reached = level >= 0
+    reached[root] = False
+    bad += int(np.count_nonzero(parent[level < 0] != -1))
+    v = np.nonzero(reached)[0]
+    p = parent[v]
+    okp = (p >= 0) & (p < n)
+    bad += int(np.count_nonzero(~okp))
+    v, p = v[okp], p[okp]
+    bad += int(np.count_nonzero(level[p] != level[v] - 1))
+    beg = csr_off[p]
+    end = csr_off[p + 1]
+    # edge p->v exists iff v appears in sorted row p
+    found = np.zeros(v.shape[0], dtype=bool)
+    # vectorised binary search over rows
+    lo, hi = beg.copy(), end.copy()
+    while True:
+        active = lo < hi
+        if not active.any():
+            break
+        mid = (lo + hi) // 2
+        mv = np.where(active, csr_idx[np.minimum(mid, len(csr_idx) - 1)], 0)
+        less = active & (mv < v)
+        lo = np.where(less, mid + 1, lo)
+        hi = np.where(active & ~less, mid, hi)
+    inrow = lo < end
+    found[inrow] = csr_idx[lo[inrow]] == v[inrow]
+    bad += int(np.count_nonzero(~found))
+    return bad

@@ -1,0 +1,314 @@
+"""Pins for the CPU oracle: each check compares it with something other than
+itself -- hand-derived worked examples, closed forms, invariants, a dense linear
+solve (LU, numpy) and brute-force shortest paths (Floyd-Warshall)."""
+import math
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from helpers import (check_parents, dense_pagerank, dense_transition, floyd_warshall_levels,
+                     parse_bfs_case, parse_pagerank_cases)
+
+VARIANTS = [oracle.PUSH, oracle.PULL]
+
+
+def og(g, weighted=True):
+    return oracle.OracleGraph.from_graph(g, weighted=weighted)
+
+
+# ----------------------------------------------------------------- worked examples
+
+@pytest.mark.parametrize("case", parse_pagerank_cases(), ids=lambda c: c["name"])
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_pagerank_worked_example(case, variant):
+    """Section 3.1 / Algorithm 1 on hand-derived sweeps (tests/golden)."""
+    w = None if case["w"] is None else np.array([float(x) for x in case["w"]], dtype=np.float32)
+    G = oracle.OracleGraph(case["n"], case["src"], case["dst"], w)
+    d = float(case["d"])
+    for k, key, rkey in ((1, "sweep1", "res1"), (2, "sweep2", "res2")):
+        x, done, r, _ = G.pagerank(variant, d, iters=k, tol=0.0)
+        assert done == k
+        np.testing.assert_allclose(x, [float(f) for f in case[key]], rtol=0, atol=1e-15)
+        assert abs(r - float(case[rkey])) < 1e-15
+    x, done, r, conv = G.pagerank(variant, d, iters=10000, tol=1e-15)
+    assert conv
+    np.testing.assert_allclose(x, [float(f) for f in case["fixed"]], rtol=0, atol=1e-13)
+
+
+def test_bfs_worked_example():
+    """Section 3.3 / Algorithm 3 on a hand-derived directed example (tests/golden)."""
+    c = parse_bfs_case()
+    G = oracle.OracleGraph(c["n"], c["src_e"], c["dst_e"])
+    level, parent = G.bfs(c["src"])
+    assert level.tolist() == c["level"]
+    assert parent.tolist() == c["parent"]
+    for dirs in ([0], [1], [0, 1], [1, 0], [1, 1, 0, 0, 1]):
+        lv, pa, _ = G.bfs_levelsync(c["src"], dirs)
+        assert lv.tolist() == c["level"]
+        assert check_parents(c["n"], c["src_e"], c["dst_e"], c["src"], lv, pa) == []
+
+
+# ----------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("n", [2, 3, 7, 16])
+def test_complete_graph_uniform(variant, n):
+    """K_n: x = 1/n is the fixed point and every sweep from x0 = 1/n stays there."""
+    G = og(gg.complete(n))
+    for k in (1, 2, 5):
+        x, _, r, _ = G.pagerank(variant, 0.85, iters=k)
+        np.testing.assert_allclose(x, 1.0 / n, rtol=1e-14, atol=0)
+        assert r < 1e-14
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_directed_cycle_and_regular(variant):
+    """Directed n-cycle and a 3-regular circulant: uniform ranks at every sweep."""
+    G = og(gg.cycle(11))
+    x, _, _, _ = G.pagerank(variant, 0.85, iters=7)
+    np.testing.assert_allclose(x, 1 / 11, rtol=1e-14)
+    n = 10
+    s = np.repeat(np.arange(n), 3)
+    t = (s + np.tile([1, 3, 7], n)) % n
+    G = og(gg.from_edges(n, s, t))
+    x, _, _, _ = G.pagerank(variant, 0.85, iters=9)
+    np.testing.assert_allclose(x, 1 / n, rtol=1e-14)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("k", [1, 2, 5, 40])
+def test_star_closed_form(variant, k):
+    """Undirected star S_k: x_c = (1-d)(1+dk)/(n(1-d^2)), x_l = (1-d)(1+d/k)/(n(1-d^2))."""
+    d, n = 0.85, k + 1
+    G = og(gg.star(k))
+    # the FP64 rounding floor of the L1 residual on this graph is ~6e-15
+    x, _, _, conv = G.pagerank(variant, d, iters=100000, tol=1e-13)
+    assert conv
+    xc = (1 - d) * (1 + d * k) / (n * (1 - d * d))
+    xl = (1 - d) * (1 + d / k) / (n * (1 - d * d))
+    np.testing.assert_allclose(x[0], xc, rtol=1e-12)
+    np.testing.assert_allclose(x[1:], xl, rtol=1e-12)
+
+
+# ----------------------------------------------------------------- dense linear solve
+
+@pytest.mark.parametrize("seed", range(12))
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_dense_solve(seed, variant):
+    """Random directed graphs, n <= 12, with dangling vertices and self-loops:
+    the iterated fixed point equals (I - d P)^-1 (1-d) s solved by LU."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 13))
+    mask = rng.random((n, n)) < 0.3
+    u, v = np.nonzero(mask)
+    d = float(rng.uniform(0.5, 0.95))
+    weighted = seed % 3 == 0
+    w = None
+    if weighted:  # P_vu = w_uv with every source's out-weights summing to at most one
+        w = rng.uniform(0.05, 1.0, size=len(u))
+        w = (w / np.bincount(u, weights=w, minlength=n)[u] * rng.uniform(0.5, 1.0)).astype(np.float32)
+    s = rng.random(n)
+    s /= s.sum()
+    G = oracle.OracleGraph(n, u, v, w)
+    x, _, _, conv = G.pagerank(variant, d, iters=100000, tol=1e-14, personalization=s)
+    assert conv
+    ref = dense_pagerank(n, u, v, d, s=s, w=w)
+    np.testing.assert_allclose(x, ref, rtol=0, atol=1e-12)
+
+
+# ----------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_mass_and_isolated(variant):
+    """sum(y) = (1-d) + d * sum_{deg_out(u) > 0} x_u after one sweep; isolated
+    vertices hold exactly (1-d)/n."""
+    g = gg.rmat(8, 8, seed=3, symmetrize=False)
+    G = og(g)
+    d = 0.85
+    rng = np.random.default_rng(0)
+    x0 = rng.random(g.n)
+    x0 /= x0.sum()
+    y, _, _, _ = G.pagerank(variant, d, iters=1, x0=x0)
+    live = g.out_degree() > 0
+    assert abs(y.sum() - ((1 - d) + d * x0[live].sum())) < 1e-13
+    iso = (g.out_degree() == 0) & (g.in_degree() == 0)
+    assert iso.any()
+    np.testing.assert_array_equal(y[iso], (1 - d) / g.n)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_push_equals_pull(seed):
+    """The two sweep forms compute the same iterate (to rounding)."""
+    g = gg.rmat(9 + seed % 3, 8, seed=seed, symmetrize=seed % 2 == 0)
+    if seed % 3 == 0:
+        g = g.with_weights(seed + 100)
+    G = og(g)
+    a, _, _, _ = G.pagerank(oracle.PUSH, 0.85, iters=25)
+    b, _, _, _ = G.pagerank(oracle.PULL, 0.85, iters=25)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-13)
+
+
+def test_pull_threads_identical():
+    """The threaded pull sums each vertex in the same order: bitwise equal."""
+    g = gg.rmat(11, 8, seed=4)
+    G = og(g)
+    a, _, _, _ = G.pagerank(oracle.PULL, 0.85, iters=10, nthreads=1)
+    b, _, _, _ = G.pagerank(oracle.PULL, 0.85, iters=10, nthreads=4)
+    assert np.array_equal(a, b)
+
+
+def test_convergence_contract():
+    """tol stops at the first sweep with residual < tol; tol = 0 runs `iters` sweeps."""
+    G = og(gg.rmat(9, 8, seed=2))
+    x, k, r, conv = G.pagerank(oracle.PULL, 0.85, iters=500, tol=1e-9)
+    assert conv and r < 1e-9
+    _, k1, r1, _ = G.pagerank(oracle.PULL, 0.85, iters=k - 1, tol=0.0)
+    assert r1 >= 1e-9
+    _, k2, _, conv2 = G.pagerank(oracle.PULL, 0.85, iters=5, tol=1e-9)
+    assert k2 == 5 and not conv2
+
+
+# ----------------------------------------------------------------- personalised PR
+
+def test_ppr_linearity():
+    """The mean of the n one-hot personalised vectors equals global PageRank."""
+    g = gg.rmat(5, 4, seed=9, symmetrize=False)
+    G = og(g)
+    n = g.n
+    glob, _, _, _ = G.pagerank(oracle.PULL, 0.85, iters=4000, tol=1e-15)
+    acc = np.zeros(n)
+    for v in range(n):
+        e = np.zeros(n)
+        e[v] = 1.0
+        x, _, _, _ = G.pagerank(oracle.PULL, 0.85, iters=4000, tol=1e-15, personalization=e, x0=e)
+        acc += x
+    np.testing.assert_allclose(acc / n, glob, rtol=0, atol=1e-13)
+
+
+def test_ppr_complete_graph():
+    """PPR on K_n seeded at 0: by symmetry x_0 = a and x_v = b with
+    a = (1-d) + d b and b (n-1-d(n-2)) = d a."""
+    n, d = 9, 0.85
+    G = og(gg.complete(n))
+    e = np.zeros(n)
+    e[0] = 1.0
+    x, _, _, _ = G.pagerank(oracle.PUSH, d, iters=5000, tol=1e-15, personalization=e)
+    c = d / (n - 1 - d * (n - 2))
+    a = (1 - d) / (1 - d * c)
+    np.testing.assert_allclose(x[0], a, rtol=1e-12)
+    np.testing.assert_allclose(x[1:], c * a, rtol=1e-12)
+
+
+# ----------------------------------------------------------------- BFS
+
+def test_bfs_path_tree_star_disconnected():
+    G = og(gg.path(50))
+    lv, pa = G.bfs(0)
+    assert lv.tolist() == list(range(50))
+    assert pa.tolist() == [0] + list(range(49))
+    G = og(gg.binary_tree(100))
+    lv, _ = G.bfs(0)
+    assert lv.tolist() == [int(math.floor(math.log2(i + 1))) for i in range(100)]
+    G = og(gg.star(20))
+    lv, _ = G.bfs(0)
+    assert lv.tolist() == [0] + [1] * 20
+    lv, _ = G.bfs(5)
+    assert lv[0] == 1 and lv[5] == 0 and (lv[1:5] == 2).all()
+    G = og(gg.empty(4))
+    lv, pa = G.bfs(2)
+    assert lv.tolist() == [-1, -1, 0, -1] and pa.tolist() == [-1, -1, 2, -1]
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_bfs_brute_force(seed):
+    """Levels equal Floyd-Warshall unit distances on tiny directed graphs, for
+    the FIFO form and level-synchronous forms with any per-level direction."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 11))
+    mask = rng.random((n, n)) < rng.uniform(0.05, 0.5)
+    u, v = np.nonzero(mask)
+    G = oracle.OracleGraph(n, u, v)
+    for root in range(n):
+        ref = floyd_warshall_levels(n, u, v, root)
+        lv, pa = G.bfs(root)
+        assert lv.tolist() == ref.tolist()
+        assert check_parents(n, u, v, root, lv, pa) == []
+        for dirs in ([0], [1], [0, 1], [1, 0], rng.integers(0, 2, size=12).tolist()):
+            lv2, pa2, used = G.bfs_levelsync(root, dirs)
+            assert lv2.tolist() == ref.tolist()
+            assert check_parents(n, u, v, root, lv2, pa2) == []
+
+
+def test_bfs_directions_recorded():
+    g = gg.rmat(10, 8, seed=5)
+    G = og(g)
+    lv, _, used = G.bfs_levelsync(0, [0, 1, 1, 0])
+    ref, _ = G.bfs(0)
+    assert lv.tolist() == ref.tolist()
+    dirs = [0, 1, 1, 0]
+    assert len(used) == int(ref.max()) + 1
+    assert used.tolist() == [dirs[min(i, 3)] for i in range(len(used))]
+
+
+# ----------------------------------------------------------------- adjoint
+
+@pytest.mark.parametrize("seed", range(6))
+def test_adjoint_dense(seed):
+    """lambda = (I - d P^T)^-1 g, grad_s = (1-d) lambda, grad_P[v,u] = d lambda_v x_u,
+    against LU solves."""
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(2, 13))
+    mask = rng.random((n, n)) < 0.35
+    u, v = np.nonzero(mask)
+    w = None
+    if seed % 2:  # sub-stochastic columns: every source's out-weights sum to one
+        w = rng.uniform(0.1, 1.0, size=len(u))
+        w = (w / np.bincount(u, weights=w, minlength=n)[u]).astype(np.float32)
+    d = 0.85
+    G = oracle.OracleGraph(n, u, v, w)
+    x, _, _, _ = G.pagerank(oracle.PULL, d, iters=100000, tol=1e-14)
+    gvec = rng.normal(size=n)
+    lam, gs, gw, _, _ = G.pagerank_adjoint(x, gvec, d)
+    P = dense_transition(n, u, v, w)
+    lam_ref = np.linalg.solve(np.eye(n) - d * P.T, gvec)
+    np.testing.assert_allclose(lam, lam_ref, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(gs, (1 - d) * lam_ref, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(gw, d * lam_ref[v] * x[u], rtol=0, atol=1e-11)
+
+
+def test_adjoint_finite_differences():
+    """Central differences of L = g . x*(P, s) through the FP64 forward solve."""
+    g = gg.rmat(6, 8, seed=11, symmetrize=False).with_weights(12)
+    src, dst = g.edges()
+    w = g.csr_w.astype(np.float64)
+    d = 0.85
+    rng = np.random.default_rng(10)
+    gvec = rng.normal(size=g.n)
+    s0 = np.full(g.n, 1.0 / g.n)
+
+    def loss(wv, s):
+        # the forward of the oracle with explicit double weights: rebuild with float32
+        # would round the perturbation away, so solve densely at FP64 for FD only
+        P = np.zeros((g.n, g.n))
+        np.add.at(P, (dst, src), wv)
+        x = np.linalg.solve(np.eye(g.n) - d * P, (1 - d) * s)
+        return float(gvec @ x)
+
+    G = oracle.OracleGraph(g.n, src, dst, g.csr_w)
+    x, _, _, _ = G.pagerank(oracle.PULL, d, iters=100000, tol=1e-15)
+    _, gs, gw, _, _ = G.pagerank_adjoint(x, gvec, d)
+    h = 1e-4
+    for e in rng.choice(g.m, size=12, replace=False):
+        wp, wm = w.copy(), w.copy()
+        wp[e] += h
+        wm[e] -= h
+        fd = (loss(wp, s0) - loss(wm, s0)) / (2 * h)
+        assert abs(fd - gw[e]) <= 1e-6 * max(1.0, abs(fd)), (e, fd, gw[e])
+    for vtx in rng.choice(g.n, size=8, replace=False):
+        sp, sm = s0.copy(), s0.copy()
+        sp[vtx] += h
+        sm[vtx] -= h
+        fd = (loss(w, sp) - loss(w, sm)) / (2 * h)
+        assert abs(fd - gs[vtx]) <= 1e-7 * max(1.0, abs(fd))
