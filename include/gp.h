@@ -1,0 +1,264 @@
+/*
+ * gp.h -- C ABI of libgp, the push/pull graph-sweep library for NVIDIA GB300 (sm_103a).
+ *
+ * The library runs the per-iteration vertex-centric edge sweep studied in
+ * "To Push or To Pull: On Reducing Communication and Synchronization in Graph
+ * Computations" (Besta, Podstawski, Groner, Solomonik, Hoefler; HPDC 2017) in
+ * its two forms (Section 3, "Push-Pull: Applicability"; Section 3.8):
+ *   push -- the thread that owns vertex v writes state of other vertices: v
+ *           scatters along its out-edges into shared state with atomics;
+ *   pull -- only the owner of v writes v: v gathers along its in-edges into
+ *           its own state, with no atomics;
+ * applied to PageRank power iteration (Section 3.1; Algorithm 1) and to BFS
+ * frontier expansion (Section 3.3; Algorithm 3): top-down = push, bottom-up =
+ * pull, and a per-level switch between the two (Generic-Switch, Section 5).
+ *
+ * Conventions shared by every entry point
+ *  - Status: every function returns GP_OK (0) or a negative gp_status.  No
+ *    entry point aborts, prints or exits.  gp_status_string() names a status;
+ *    gp_last_error() returns a message for the last failure on the calling
+ *    host thread.
+ *  - Memory kinds: "device" = CUDA device (or managed) memory of the current
+ *    device; "host" = ordinary or pinned host memory; "any" = either (the
+ *    library detects the kind and copies host data through its own device
+ *    buffers, synchronising the stream before returning).
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  All device work of a call is enqueued on it.  A call
+ *    returns once its work is enqueued, except that gp_pagerank reads its
+ *    convergence flag back every few sweeps, gp_bfs reads its frontier
+ *    counters back once per level, and any "any" output in host memory or a
+ *    non-NULL stats pointer makes the call synchronise the stream.
+ *  - Ownership: the caller owns every pointer it passes.  The library never
+ *    frees caller memory.  Arrays handed to gp_graph_upload without
+ *    GP_UPLOAD_COPY are read in place and must stay alive and unchanged until
+ *    gp_graph_free.  Library-owned device memory (degree arrays, vertex bins,
+ *    queues, bitmaps, partial sums) is obtained from the allocator registered
+ *    with gp_set_allocator (default: cudaMallocAsync/cudaFreeAsync).
+ *  - Graph layout (Section 2.2): neighbours of each vertex form one contiguous
+ *    array; n+1 offsets (int64) mark where each vertex's list begins.  CSR
+ *    lists out-neighbours (row u = heads of u->v; what push walks), CSC lists
+ *    in-neighbours (column v = tails of u->v; what pull walks), Section 4.8
+ *    ("Directed Graphs").  Indices are int32 (n < 2^31), offsets int64.
+ *  - Threads: one graph handle may be used by one host thread at a time.
+ */
+#ifndef GP_H
+#define GP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GP_VERSION 1
+
+/* Sweep form.  For PageRank: PUSH = scatter with FP32 atomics, PULL = gather
+ * with no atomics, AUTO = the library picks one per graph (the result is the
+ * same up to FP32 rounding).  For BFS: PUSH = top-down, PULL = bottom-up,
+ * AUTO = switch per level. */
+typedef enum gp_mode { GP_PUSH = 0, GP_PULL = 1, GP_AUTO = 2 } gp_mode;
+
+typedef enum gp_status {
+    GP_OK = 0,
+    GP_ERR_INVALID = -1,       /* bad argument or malformed graph */
+    GP_ERR_OOM = -2,           /* the allocator returned NULL */
+    GP_ERR_CUDA = -3,          /* a CUDA runtime call failed (message in gp_last_error) */
+    GP_ERR_NOT_CONVERGED = -4, /* sweep cap reached before tol; the last iterate is written */
+    GP_ERR_TIMEOUT = -5,       /* a bounded device wait ran out */
+    GP_ERR_UNSUPPORTED = -6    /* feature not available for this input */
+} gp_status;
+
+typedef struct gp_graph gp_graph; /* opaque handle */
+
+/* ------------------------------------------------------------------ errors */
+
+/* Static text for a status code (never NULL). */
+const char *gp_status_string(int status);
+
+/* Thread-local message describing the last failure on this host thread ("" if none). */
+const char *gp_last_error(void);
+
+/* GP_VERSION of the library actually loaded. */
+int gp_version(void);
+
+/* ------------------------------------------------------------------ memory */
+
+/* Allocation callbacks for library-owned device memory.  alloc returns a device
+ * pointer of at least `bytes` bytes aligned to 256 bytes, usable in stream
+ * order on `stream`, or NULL on failure (the call then fails with GP_ERR_OOM).
+ * free releases it in stream order.  Passing NULL for both restores the
+ * default (cudaMallocAsync / cudaFreeAsync).  Applies to later allocations
+ * only; memory is always released with the callbacks that allocated it. */
+typedef void *(*gp_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*gp_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+int gp_set_allocator(gp_alloc_fn alloc, gp_free_fn free_fn, void *ctx);
+
+/* ------------------------------------------------------------------ graph */
+
+#define GP_UPLOAD_VALIDATE 0x1u  /* check offsets (monotone, 0..m), indices (< n), and that
+                                    CSR and CSC hold the same edge multiset; GP_ERR_INVALID
+                                    with a message on failure (synchronises the stream) */
+#define GP_UPLOAD_SYMMETRIC 0x2u /* the graph is symmetric: the CSC arguments may be NULL and
+                                    the CSR arrays serve both directions */
+#define GP_UPLOAD_COPY 0x4u      /* copy all arrays into library-owned device memory; the
+                                    sources may be "any" memory and need not outlive the call */
+#define GP_UPLOAD_NORMALIZE 0x8u /* weighted graphs: P_vu = w_uv / sum_v' w_uv' (else P_vu = w_uv) */
+
+/*
+ * Upload a graph and prepare its degree data (the paper's Section 2.2 layout;
+ * Section 7.3 notes that pulling must also fetch the neighbours' degrees, so
+ * 1/deg_out is precomputed here once).
+ *   n, m          vertices and stored directed edges; 0 <= n < 2^31, m >= 0.
+ *   csr_off       int64[n+1] "any"/device: out-edge offsets, csr_off[0] = 0, csr_off[n] = m.
+ *   csr_idx       int32[m]: heads of the out-edges of each vertex.
+ *   csr_w         float[m] or NULL: weight of each CSR edge (P_vu for u->v, see NORMALIZE).
+ *   csc_off/idx/w the same edges grouped by head (in-edges); may be NULL with
+ *                 GP_UPLOAD_SYMMETRIC.  csc_w must be given iff csr_w is.
+ *   flags         GP_UPLOAD_* bits.
+ * Without GP_UPLOAD_COPY all arrays must be device memory.  Unweighted:
+ * P_vu = 1/deg_out(u).  Vertices with deg_out = 0 contribute nothing.
+ * On success *out holds a new handle; on failure *out is NULL.
+ */
+int gp_graph_upload(gp_graph **out, int64_t n, int64_t m, const int64_t *csr_off, const int32_t *csr_idx,
+                    const float *csr_w, const int64_t *csc_off, const int32_t *csc_idx, const float *csc_w,
+                    unsigned flags, void *stream);
+
+/* Release a handle and all library-owned memory (in order on the stream it was
+ * uploaded with).  NULL is accepted. */
+int gp_graph_free(gp_graph *g);
+
+typedef struct gp_graph_info {
+    int64_t n, m;
+    int64_t max_out_degree, max_in_degree;
+    int64_t pull_big_vertices; /* vertices with in-degree above pull_light_max (warp chunks) */
+    int64_t pull_big_chunks;
+    int64_t push_big_vertices; /* vertices with out-degree above push_light_max */
+    int64_t push_big_chunks;
+    int64_t isolated; /* vertices with no in- and no out-edges */
+    int32_t symmetric, weighted;
+    int64_t device_bytes; /* library-owned device memory held by the handle */
+} gp_graph_info;
+
+int gp_graph_info_get(const gp_graph *g, gp_graph_info *info);
+
+/* ------------------------------------------------------------------ options */
+
+/* Tunables (the autotuner writes these).  Correctness never depends on them. */
+typedef struct gp_options {
+    int32_t pull_light_max;   /* in-degree <= this: 32 vertices per warp, merged edge stream */
+    int32_t push_light_max;   /* out-degree <= this: same for the push scatter and top-down BFS */
+    int32_t chunk_edges;      /* edges per warp chunk for vertices above the light limits */
+    int32_t blocks_per_sm;    /* resident blocks per SM for the grid-stride sweep kernels */
+    int32_t poll_interval;    /* PageRank sweeps enqueued between convergence read-backs */
+    int32_t pr_auto_mode;     /* what GP_AUTO means for PageRank: GP_PUSH, GP_PULL, or -1 = rule */
+    float bfs_alpha;          /* top-down -> bottom-up when m_f > m_u / alpha */
+    float bfs_beta;           /* bottom-up -> top-down when n_f < n / beta (frontier shrinking) */
+    int32_t reserved[8];
+} gp_options;
+
+/* Fill *opt with the built-in defaults. */
+int gp_options_default(gp_options *opt);
+
+/* Replace the handle's options (rebuilds its vertex bins if the degree limits
+ * or chunk size change; enqueued on `stream`). */
+int gp_graph_set_options(gp_graph *g, const gp_options *opt, void *stream);
+
+int gp_graph_get_options(const gp_graph *g, gp_options *opt);
+
+/* ------------------------------------------------------------------ PageRank */
+
+typedef struct gp_pr_stats {
+    int32_t iters_done; /* sweeps performed */
+    int32_t mode_used;  /* GP_PUSH or GP_PULL */
+    double residual;    /* L1 norm (FP64) of the change made by the last sweep */
+    float ms;           /* device time of the call by CUDA events (0 when stats is NULL) */
+    int32_t converged;  /* 1 if residual < tol (or tol == 0 and all sweeps ran) */
+} gp_pr_stats;
+
+/*
+ * PageRank power iteration (Section 3.1 formula; Algorithm 1, push- and
+ * pull-based PageRank; damping d is the paper's f):
+ *     y[v] = (1-d) s[v] + d * sum_{(u->v) in E} P_vu x[u]
+ * Jacobi sweeps from x0; after each sweep the L1 norm of y - x is reduced in
+ * FP64; iteration stops at the first sweep where it is below tol, or after
+ * `iters` sweeps (then GP_ERR_NOT_CONVERGED, with the last iterate written).
+ * tol = 0 runs exactly `iters` sweeps and returns GP_OK.
+ *   mode            GP_PUSH (scatter, FP32 atomicAdd), GP_PULL (gather, no atomics) or GP_AUTO.
+ *   damping         in (0, 1).
+ *   iters           >= 1.
+ *   personalization float[n] "any" or NULL (uniform 1/n): the teleport vector s.
+ *   x0              float[n] "any" or NULL (1/n): starting vector.
+ *   ranks_out       float[n] "any": the final iterate.
+ *   stats           optional.
+ * Ranks are FP32; sums are FP32 (tree order within a warp, so pull is
+ * deterministic for fixed options; push is not, its atomics commute).
+ */
+int gp_pagerank(const gp_graph *g, int mode, float damping, int iters, double tol, const float *personalization,
+                const float *x0, float *ranks_out, gp_pr_stats *stats, void *stream);
+
+/* ------------------------------------------------------------------ BFS */
+
+#define GP_BFS_MAX_LEVELS 512
+
+typedef struct gp_bfs_stats {
+    int32_t levels;         /* levels explored (depth + 1) */
+    int32_t switches;       /* direction changes */
+    int64_t reached;        /* vertices with level >= 0 */
+    int64_t edges_examined; /* out-edges scanned top-down + in-edges scanned bottom-up */
+    int64_t edges_reached;  /* sum of out-degrees of the reached vertices */
+    float ms;               /* device time of the call by CUDA events */
+    int8_t direction[GP_BFS_MAX_LEVELS]; /* GP_PUSH (top-down) / GP_PULL (bottom-up) per level */
+    int64_t frontier[GP_BFS_MAX_LEVELS]; /* frontier size entering each level */
+    int64_t examined[GP_BFS_MAX_LEVELS]; /* edges scanned by each level */
+} gp_bfs_stats;
+
+/*
+ * Breadth-first search from `src` over out-edges (Section 3.3; Algorithm 3
+ * with every ready counter = 1, so each vertex takes the level of the frontier
+ * that first reaches it, plus one).
+ *   mode        GP_PUSH: top-down every level -- frontier vertices scan their
+ *               out-edges and claim unvisited heads with atomicCAS (Section 4.3,
+ *               "Atomics/Locks": O(m) CAS);
+ *               GP_PULL: bottom-up every level -- every unvisited vertex scans
+ *               its in-edges for a frontier vertex and stops at the first one
+ *               (owner-only writes, no atomics on vertex state);
+ *               GP_AUTO: per-level switch (top-down -> bottom-up when the
+ *               frontier's out-edges m_f exceed m_u/alpha, m_u = in-edges of
+ *               unvisited vertices; back when the frontier shrinks below n/beta).
+ *   level_out   int32[n] "any": BFS level, -1 if unreached.
+ *   parent_out  int32[n] "any" or NULL: a BFS parent (parent[src] = src, -1 if
+ *               unreached).  Levels are unique; parents are valid but may
+ *               differ between runs (any frontier in-neighbour is correct).
+ */
+int gp_bfs(const gp_graph *g, int32_t src, int mode, int32_t *level_out, int32_t *parent_out, gp_bfs_stats *stats,
+           void *stream);
+
+/* gp_bfs with the direction of every level chosen by the caller:
+ * dirs[i] (GP_PUSH or GP_PULL) is used for level i, dirs[ndirs-1] for all
+ * later levels.  Levels do not depend on the choice. */
+int gp_bfs_directed(const gp_graph *g, int32_t src, const int8_t *dirs, int ndirs, int32_t *level_out,
+                    int32_t *parent_out, gp_bfs_stats *stats, void *stream);
+
+/* ------------------------------------------------------------------ kernel timing */
+
+/* When enabled, the library brackets each of its sweep-kernel launches with
+ * CUDA events on the launching stream and accumulates their durations per
+ * kernel name.  Off by default (no events recorded). */
+int gp_profile_enable(int on);
+
+typedef struct gp_kernel_time {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+} gp_kernel_time;
+
+/* Synchronise the recorded events, write up to `cap` entries (kernels sorted
+ * by total time, descending) and return the number written in *count; reset
+ * != 0 clears the accumulators afterwards. */
+int gp_profile_read(gp_kernel_time *out, int cap, int *count, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GP_H */

@@ -1,0 +1,285 @@
+"""Push/pull graph sweeps on GB300: Python binding of libgp.
+
+Thin ctypes layer over the C ABI declared in include/gp.h, with the same names
+and argument marshalling only: every step of PageRank and BFS runs in libgp's
+CUDA kernels.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: if libgp.so is missing, load() raises.
+
+    import paper_2010_16012_gb300 as gp
+    G = gp.Graph.from_arrays(n, csr_off, csr_idx, csc_off, csc_idx)   # torch CUDA tensors
+    ranks, st = gp.pagerank(G, gp.PULL, damping=0.85, iters=300, tol=1e-7)
+    level, parent, st = gp.bfs(G, src=0, mode=gp.AUTO)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgp.so")
+
+PUSH, PULL, AUTO = 0, 1, 2
+UPLOAD_VALIDATE, UPLOAD_SYMMETRIC, UPLOAD_COPY, UPLOAD_NORMALIZE = 0x1, 0x2, 0x4, 0x8
+OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+BFS_MAX_LEVELS = 512
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GpError(RuntimeError):
+    def __init__(self, status: int, what: str, message: str):
+        super().__init__(f"{what}: status {status} ({message})")
+        self.status = status
+
+
+class gp_options(ctypes.Structure):
+    _fields_ = [("pull_light_max", ctypes.c_int32), ("push_light_max", ctypes.c_int32),
+                ("chunk_edges", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("poll_interval", ctypes.c_int32), ("pr_auto_mode", ctypes.c_int32),
+                ("bfs_alpha", ctypes.c_float), ("bfs_beta", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+class gp_graph_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("max_out_degree", ctypes.c_int64),
+                ("max_in_degree", ctypes.c_int64), ("pull_big_vertices", ctypes.c_int64),
+                ("pull_big_chunks", ctypes.c_int64), ("push_big_vertices", ctypes.c_int64),
+                ("push_big_chunks", ctypes.c_int64), ("isolated", ctypes.c_int64),
+                ("symmetric", ctypes.c_int32), ("weighted", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64)]
+
+
+class gp_pr_stats(ctypes.Structure):
+    _fields_ = [("iters_done", ctypes.c_int32), ("mode_used", ctypes.c_int32), ("residual", ctypes.c_double),
+                ("ms", ctypes.c_float), ("converged", ctypes.c_int32)]
+
+
+class gp_bfs_stats(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("switches", ctypes.c_int32), ("reached", ctypes.c_int64),
+                ("edges_examined", ctypes.c_int64), ("edges_reached", ctypes.c_int64), ("ms", ctypes.c_float),
+                ("direction", ctypes.c_int8 * BFS_MAX_LEVELS), ("frontier", ctypes.c_int64 * BFS_MAX_LEVELS),
+                ("examined", ctypes.c_int64 * BFS_MAX_LEVELS)]
+
+
+class gp_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+# (name, restype, argtypes) of every entry point of include/gp.h
+_VP, _I32, _I64, _F, _D, _U = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double, ctypes.c_uint
+SIGNATURES = [
+    ("gp_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("gp_last_error", ctypes.c_char_p, []),
+    ("gp_version", ctypes.c_int, []),
+    ("gp_set_allocator", ctypes.c_int, [ALLOC_FN, FREE_FN, _VP]),
+    ("gp_graph_upload", ctypes.c_int, [ctypes.POINTER(_VP), _I64, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _U, _VP]),
+    ("gp_graph_free", ctypes.c_int, [_VP]),
+    ("gp_graph_info_get", ctypes.c_int, [_VP, ctypes.POINTER(gp_graph_info)]),
+    ("gp_options_default", ctypes.c_int, [ctypes.POINTER(gp_options)]),
+    ("gp_graph_set_options", ctypes.c_int, [_VP, ctypes.POINTER(gp_options), _VP]),
+    ("gp_graph_get_options", ctypes.c_int, [_VP, ctypes.POINTER(gp_options)]),
+    ("gp_pagerank", ctypes.c_int, [_VP, ctypes.c_int, _F, ctypes.c_int, _D, _VP, _VP, _VP,
+                                   ctypes.POINTER(gp_pr_stats), _VP]),
+    ("gp_bfs", ctypes.c_int, [_VP, _I32, ctypes.c_int, _VP, _VP, ctypes.POINTER(gp_bfs_stats), _VP]),
+    ("gp_bfs_directed", ctypes.c_int, [_VP, _I32, _VP, ctypes.c_int, _VP, _VP, ctypes.POINTER(gp_bfs_stats),
+                                       _VP]),
+    ("gp_profile_enable", ctypes.c_int, [ctypes.c_int]),
+    ("gp_profile_read", ctypes.c_int, [ctypes.POINTER(gp_kernel_time), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+]
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libgp.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"libgp CUDA library not built ({path} missing): run "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            lib = ctypes.CDLL(path)
+            for name, res, args in SIGNATURES:
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status: int, what: str, allow=()):
+    if status != OK and status not in allow:
+        lib = load()
+        msg = lib.gp_last_error().decode() or lib.gp_status_string(status).decode()
+        raise GpError(status, what, msg)
+    return status
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    """Device or host address of a torch tensor / numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return ctypes.c_void_p(t.ctypes.data)
+    assert t.is_contiguous()
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def default_options() -> gp_options:
+    o = gp_options()
+    _check(load().gp_options_default(ctypes.byref(o)), "gp_options_default")
+    return o
+
+
+class Graph:
+    """A graph uploaded to the GPU (the gp_graph handle).
+
+    Arrays are int64 offsets / int32 indices (/ float32 weights) in CSR
+    (out-edges) and CSC (in-edges) order.  CUDA tensors are read in place and
+    kept referenced by this object; numpy arrays (or copy=True) are copied into
+    library-owned device memory by gp_graph_upload.
+    """
+
+    def __init__(self, n, csr_off, csr_idx, csc_off=None, csc_idx=None, csr_w=None, csc_w=None, *,
+                 symmetric=False, validate=False, normalize=False, copy=None, stream=None):
+        lib = load()
+        host = any(isinstance(a, np.ndarray) for a in (csr_off, csr_idx, csc_off, csc_idx, csr_w, csc_w))
+        if copy is None:
+            copy = host
+        flags = (UPLOAD_VALIDATE if validate else 0) | (UPLOAD_SYMMETRIC if symmetric else 0) | \
+                (UPLOAD_COPY if copy else 0) | (UPLOAD_NORMALIZE if normalize else 0)
+        self._keep = None if copy else (csr_off, csr_idx, csc_off, csc_idx, csr_w, csc_w)
+        self.n = int(n)
+        self.m = int(csr_idx.shape[0])
+        self.symmetric = symmetric
+        self.weighted = csr_w is not None
+        self._stream = stream
+        h = ctypes.c_void_p()
+        _check(lib.gp_graph_upload(ctypes.byref(h), self.n, self.m, _ptr(csr_off), _ptr(csr_idx), _ptr(csr_w),
+                                   _ptr(csc_off), _ptr(csc_idx), _ptr(csc_w), flags, _stream_ptr(stream)),
+               "gp_graph_upload")
+        self._h = h
+
+    @classmethod
+    def from_graphgen(cls, g, device="cuda", validate=False, normalize=False, copy=False, stream=None):
+        """Upload a graphgen.Graph (host numpy arrays): moved to CUDA tensors
+        first unless copy=True (then gp_graph_upload copies from host)."""
+        if copy:
+            return cls(g.n, g.csr_off, g.csr_idx, None if g.symmetric else g.csc_off,
+                       None if g.symmetric else g.csc_idx, g.csr_w, None if g.symmetric else g.csc_w,
+                       symmetric=g.symmetric, validate=validate, normalize=normalize, copy=True, stream=stream)
+        torch = _torch()
+        t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        csr_off, csr_idx = t(g.csr_off), t(g.csr_idx)
+        csr_w = t(g.csr_w)
+        if g.symmetric:
+            return cls(g.n, csr_off, csr_idx, None, None, csr_w, None, symmetric=True, validate=validate,
+                       normalize=normalize, stream=stream)
+        return cls(g.n, csr_off, csr_idx, t(g.csc_off), t(g.csc_idx), csr_w, t(g.csc_w), validate=validate,
+                   normalize=normalize, stream=stream)
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("graph already freed")
+        return self._h
+
+    def free(self):
+        if getattr(self, "_h", None):
+            _check(load().gp_graph_free(self._h), "gp_graph_free")
+            self._h = None
+            self._keep = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        i = gp_graph_info()
+        _check(load().gp_graph_info_get(self.handle, ctypes.byref(i)), "gp_graph_info_get")
+        return {f: getattr(i, f) for f, _ in gp_graph_info._fields_}
+
+    def options(self) -> gp_options:
+        o = gp_options()
+        _check(load().gp_graph_get_options(self.handle, ctypes.byref(o)), "gp_graph_get_options")
+        return o
+
+    def set_options(self, opt: gp_options = None, stream=None, **kw):
+        o = opt if opt is not None else self.options()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        _check(load().gp_graph_set_options(self.handle, ctypes.byref(o), _stream_ptr(stream)),
+               "gp_graph_set_options")
+
+
+def pagerank(g: Graph, mode=PULL, damping=0.85, iters=20, tol=0.0, personalization=None, x0=None, out=None,
+             stream=None, raise_not_converged=False):
+    """gp_pagerank.  Returns (ranks, stats dict).  `out` may be a CUDA tensor
+    or a host (numpy / CPU tensor) array; by default a new CUDA tensor."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    st = gp_pr_stats()
+    allow = () if raise_not_converged else (ERR_NOT_CONVERGED,)
+    _check(load().gp_pagerank(g.handle, int(mode), float(damping), int(iters), float(tol), _ptr(personalization),
+                              _ptr(x0), _ptr(out), ctypes.byref(st), _stream_ptr(stream)), "gp_pagerank", allow)
+    return out, {"iters_done": st.iters_done, "mode_used": st.mode_used, "residual": st.residual, "ms": st.ms,
+                 "converged": bool(st.converged)}
+
+
+def bfs(g: Graph, src: int, mode=AUTO, level=None, parent=None, want_parent=True, dirs=None, stream=None):
+    """gp_bfs / gp_bfs_directed.  Returns (level, parent or None, stats dict)."""
+    torch = _torch()
+    if level is None:
+        level = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    if parent is None and want_parent:
+        parent = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    st = gp_bfs_stats()
+    lib = load()
+    if dirs is None:
+        _check(lib.gp_bfs(g.handle, int(src), int(mode), _ptr(level), _ptr(parent), ctypes.byref(st),
+                          _stream_ptr(stream)), "gp_bfs")
+    else:
+        d = np.ascontiguousarray(np.asarray(dirs, dtype=np.int8))
+        _check(lib.gp_bfs_directed(g.handle, int(src), _ptr(d), int(d.shape[0]), _ptr(level), _ptr(parent),
+                                   ctypes.byref(st), _stream_ptr(stream)), "gp_bfs_directed")
+    L = min(st.levels, BFS_MAX_LEVELS)
+    stats = {"levels": st.levels, "switches": st.switches, "reached": st.reached,
+             "edges_examined": st.edges_examined, "edges_reached": st.edges_reached, "ms": st.ms,
+             "direction": list(st.direction[:L]), "frontier": list(st.frontier[:L]),
+             "examined": list(st.examined[:L])}
+    return level, parent, stats
+
+
+def profile_enable(on: bool = True):
+    _check(load().gp_profile_enable(int(on)), "gp_profile_enable")
+
+
+def profile_read(reset: bool = True) -> list:
+    """[(kernel name, launches, total ms)] sorted by total time."""
+    buf = (gp_kernel_time * 64)()
+    cnt = ctypes.c_int(0)
+    _check(load().gp_profile_read(buf, 64, ctypes.byref(cnt), int(reset)), "gp_profile_read")
+    return [(buf[i].name.decode(), buf[i].launches, buf[i].total_ms) for i in range(cnt.value)]

@@ -1,0 +1,220 @@
+// gp_internal.cuh -- shared internals of libgp: the graph handle, error and
+// allocation plumbing, launch/profiling helpers and warp/block primitives.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/gp.h"
+
+namespace gp {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int WARP = 32;
+
+// ------------------------------------------------------------------ errors
+
+int set_error(int status, const char *fmt, ...);  // records the message, returns status
+void clear_error();
+
+#define GP_CUDA(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t _e = (call);                                                               \
+        if (_e != cudaSuccess)                                                                 \
+            return ::gp::set_error(GP_ERR_CUDA, "%s failed: %s (%s:%d)", #call,              \
+                                   cudaGetErrorString(_e), __FILE__, __LINE__);                \
+    } while (0)
+
+#define GP_TRY(expr)              \
+    do {                          \
+        int _s = (expr);          \
+        if (_s != GP_OK) return _s; \
+    } while (0)
+
+// ------------------------------------------------------------------ memory
+
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    gp_free_fn free_fn = nullptr;  // nullptr = cudaFreeAsync
+    void *ctx = nullptr;
+};
+
+// Allocate `bytes` of device memory through the registered allocator.
+int dev_alloc(DevBuf &b, size_t bytes, cudaStream_t s);
+void dev_free(DevBuf &b, cudaStream_t s);
+
+// Owned allocations of a handle (freed together).
+struct Arena {
+    std::vector<DevBuf> bufs;
+    size_t total = 0;
+    template <class T>
+    int alloc(T *&out, size_t count, cudaStream_t s) {
+        DevBuf b;
+        int st = dev_alloc(b, (count ? count : 1) * sizeof(T), s);
+        if (st != GP_OK) return st;
+        bufs.push_back(b);
+        total += b.bytes;
+        out = static_cast<T *>(b.ptr);
+        return GP_OK;
+    }
+    void release(cudaStream_t s) {
+        for (auto &b : bufs) dev_free(b, s);
+        bufs.clear();
+        total = 0;
+    }
+};
+
+// Memory kind of a user pointer: true if the device can dereference it as device memory.
+bool is_device_ptr(const void *p);
+
+// ------------------------------------------------------------------ profiling
+
+// Launch bookkeeping: with profiling on, brackets a launch with CUDA events.
+struct ProfScope {
+    int slot = -1;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(const char *name, cudaStream_t s);
+    ~ProfScope();
+};
+
+#define GP_LAUNCH(name, stream, ...)                      \
+    do {                                                  \
+        ::gp::ProfScope _ps(name, stream);                \
+        __VA_ARGS__;                                      \
+    } while (0)
+
+int check_launch(const char *what);  // cudaGetLastError -> status
+
+// ------------------------------------------------------------------ graph handle
+
+// A contiguous piece of one vertex's adjacency list processed by one warp.
+struct __align__(16) Chunk {
+    int64_t beg;  // first edge slot
+    int32_t len;  // edges in the piece (<= chunk_edges)
+    int32_t v;    // vertex whose list it is
+};
+
+// Vertices whose degree exceeds the light limit, split into warp-sized chunks.
+struct BigBins {
+    int64_t nbig = 0;
+    int64_t nchunks = 0;
+    int32_t *big = nullptr;     // [nbig] ascending vertex ids
+    int64_t *cstart = nullptr;  // [nbig + 1] first chunk of each big vertex
+    Chunk *chunks = nullptr;    // [nchunks]
+    int32_t *rank = nullptr;    // [n] position of v in `big`, -1 for light vertices
+    int32_t light_max = 0;
+    int32_t chunk_edges = 0;
+    Arena mem;
+};
+
+// Cached PageRank workspace (sized for the graph; reused across calls).
+struct PrWork {
+    bool ready = false;
+    float *r1 = nullptr;           // second rank buffer
+    float *c0 = nullptr, *c1 = nullptr;  // contribution buffers x*P-scale
+    float *s_dev = nullptr;        // personalization copy (host input)
+    float *x0_dev = nullptr;       // start vector copy (host input)
+    float *out_dev = nullptr;      // output buffer when ranks_out is host memory
+    double *partials = nullptr;    // per-block residual partials
+    float *chunk_part = nullptr;   // per-chunk partial sums (pull, big vertices)
+    void *status = nullptr;        // device PrStatus
+    void *status_host = nullptr;   // pinned mirror
+    int max_blocks = 0;
+    Arena mem;
+};
+
+// Cached BFS workspace.
+struct BfsWork {
+    bool ready = false;
+    int32_t *queue[2] = {nullptr, nullptr};  // light frontier vertices
+    int32_t *hchunk[2] = {nullptr, nullptr}; // heavy frontier: indices into the push chunk table
+    uint32_t *bits[2] = {nullptr, nullptr};  // frontier bitmaps
+    int32_t *level_dev = nullptr, *parent_dev = nullptr;  // when outputs are host memory
+    void *ctr = nullptr;                     // device counters
+    void *ctr_host = nullptr;                // pinned mirror
+    Arena mem;
+};
+
+}  // namespace gp
+
+struct gp_graph {
+    int device = 0;
+    int num_sms = 0;
+    int64_t n = 0, m = 0;
+    bool symmetric = false, weighted = false, normalized = false;
+    const int64_t *csr_off = nullptr, *csc_off = nullptr;
+    const int32_t *csr_idx = nullptr, *csc_idx = nullptr;
+    const float *csr_w = nullptr, *csc_w = nullptr;
+    float *inv_deg = nullptr;  // [n]: 1/deg_out, 1/sum(w) (NORMALIZE) or 1 (weighted as given); 0 if dangling
+    int64_t max_out = 0, max_in = 0, isolated = 0;
+    gp_options opt;
+    gp::BigBins pull_bins;  // by in-degree (CSC)
+    gp::BigBins push_bins;  // by out-degree (CSR)
+    gp::PrWork pr;
+    gp::BfsWork bfs;
+    gp::Arena mem;          // copies of the arrays and degree data
+    cudaStream_t home = nullptr;
+};
+
+namespace gp {
+
+int build_bins(gp_graph *g, BigBins &b, const int64_t *off, int32_t light_max, int32_t chunk_edges,
+               cudaStream_t s);
+int grid_blocks(const gp_graph *g, int threads_per_block);
+
+// ------------------------------------------------------------------ device primitives
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        T t = __shfl_xor_sync(FULL, v, o);
+        v = t > v ? t : v;
+    }
+    return v;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T t = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Sum over the block (blockDim.x a multiple of 32, <= 1024); result valid in thread 0.
+template <class T>
+__device__ __forceinline__ T block_sum(T v, T *smem /* >= 32 entries */) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane_id() == 0) smem[w] = v;
+    __syncthreads();
+    T r = T(0);
+    if (w == 0) {
+        r = lane_id() < nw ? smem[lane_id()] : T(0);
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+}  // namespace gp

@@ -1,0 +1,133 @@
+"""BFS parity: CUDA top-down / bottom-up / switching BFS (through the C ABI)
+against the CPU oracle.  Levels must match bit for bit; parents are not unique,
+so each GPU parent is checked by rule (edge exists, one level up)."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from helpers import check_parents_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gp():
+    import torch
+
+    import paper_2010_16012_gb300 as gp
+
+    assert torch.cuda.is_available()
+    gp.load()
+    return gp
+
+
+def to_np(t):
+    return t.cpu().numpy() if hasattr(t, "cpu") else np.asarray(t)
+
+
+def check(g, O, src, level, parent):
+    ref, _ = O.bfs(src)
+    lv = to_np(level)
+    assert np.array_equal(lv, ref), (g.name, src, np.nonzero(lv != ref)[0][:10])
+    if parent is not None:
+        assert check_parents_np(g.csr_off, g.csr_idx, src, lv, to_np(parent)) == 0
+
+
+ZOO = [
+    lambda: gg.path(70),
+    lambda: gg.binary_tree(300),
+    lambda: gg.star(100),
+    lambda: gg.cycle(65),
+    lambda: gg.complete(9),
+    lambda: gg.empty(3),
+    lambda: gg.random_small(50, 0.05, seed=2),
+    lambda: gg.rmat(9, 8, seed=3, symmetrize=False),
+    lambda: gg.erdos_renyi(3000, 9000, seed=4),
+    lambda: gg.rmat(12, 16, seed=1),
+]
+OPTS = [None, {"push_light_max": 0, "pull_light_max": 0, "chunk_edges": 32},
+        {"push_light_max": 3, "chunk_edges": 32}]
+MODES = [0, 1, 2]
+
+
+@pytest.mark.parametrize("gi", range(len(ZOO)))
+@pytest.mark.parametrize("oi", range(len(OPTS)))
+def test_zoo_all_modes(gp, gi, oi):
+    g = ZOO[gi]()
+    G = gp.Graph.from_graphgen(g, validate=True)
+    if OPTS[oi]:
+        G.set_options(**OPTS[oi])
+    O = oracle.OracleGraph.from_graph(g)
+    srcs = sorted({0, g.n - 1, g.n // 2})
+    for src in srcs:
+        for mode in MODES:
+            lv, pa, st = gp.bfs(G, src, mode)
+            check(g, O, src, lv, pa)
+            assert st["reached"] == int((to_np(lv) >= 0).sum())
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_forced_direction_sequences(gp, seed):
+    """Levels do not depend on the direction chosen at each level."""
+    rng = np.random.default_rng(seed)
+    g = gg.rmat(11, 8, seed=seed, symmetrize=seed % 2 == 0)
+    G = gp.Graph.from_graphgen(g)
+    O = oracle.OracleGraph.from_graph(g)
+    src = int(gg.pick_vertices(g, 1, seed=seed)[0])
+    for dirs in ([0], [1], [0, 1], [1, 0], [0, 0, 1, 1, 0], rng.integers(0, 2, size=20).tolist()):
+        lv, pa, st = gp.bfs(G, src, dirs=dirs)
+        check(g, O, src, lv, pa)
+        L = st["levels"]
+        assert st["direction"] == [dirs[min(i, len(dirs) - 1)] for i in range(L)]
+
+
+def test_topdown_examines_every_reached_out_edge(gp):
+    """Top-down scans each reached vertex's out-edges exactly once (Section 4.3: O(m) work)."""
+    g = gg.rmat(12, 16, seed=2)
+    G = gp.Graph.from_graphgen(g)
+    lv, _, st = gp.bfs(G, 0, gp.PUSH)
+    reached = to_np(lv) >= 0
+    assert st["edges_examined"] == int(g.out_degree()[reached].sum()) == st["edges_reached"]
+    _, _, st2 = gp.bfs(G, 0, gp.PULL)
+    assert st2["reached"] == st["reached"]
+
+
+def test_auto_switches_on_rmat(gp):
+    g = gg.rmat(14, 16, seed=1)
+    G = gp.Graph.from_graphgen(g)
+    O = oracle.OracleGraph.from_graph(g)
+    lv, pa, st = gp.bfs(G, 0, gp.AUTO)
+    check(g, O, 0, lv, pa)
+    assert 1 in st["direction"] and 0 in st["direction"]
+    assert st["switches"] >= 1
+
+
+def test_isolated_source_and_no_parent(gp):
+    g = gg.rmat(10, 4, seed=5)
+    iso = int(np.nonzero((g.out_degree() == 0) & (g.in_degree() == 0))[0][0])
+    G = gp.Graph.from_graphgen(g)
+    for mode in MODES:
+        lv, pa, st = gp.bfs(G, iso, mode, want_parent=False)
+        lvn = to_np(lv)
+        assert pa is None and lvn[iso] == 0 and (lvn >= 0).sum() == 1 and st["levels"] == 1
+
+
+def test_host_outputs(gp):
+    g = gg.rmat(11, 8, seed=6)
+    G = gp.Graph.from_graphgen(g)
+    O = oracle.OracleGraph.from_graph(g)
+    lv = np.empty(g.n, dtype=np.int32)
+    pa = np.empty(g.n, dtype=np.int32)
+    gp.bfs(G, 3, gp.AUTO, level=lv, parent=pa)
+    check(g, O, 3, lv, pa)
+
+
+def test_invalid_source(gp):
+    G = gp.Graph.from_graphgen(gg.path(5))
+    for src in (-1, 5):
+        with pytest.raises(gp.GpError) as e:
+            gp.bfs(G, src)
+        assert e.value.status == gp.ERR_INVALID
+    with pytest.raises(gp.GpError):
+        gp.bfs(G, 0, dirs=[0, 2])

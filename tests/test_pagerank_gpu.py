@@ -1,0 +1,285 @@
+"""PageRank parity: CUDA push/pull/AUTO sweeps (through the C ABI) against the
+FP64 CPU oracle on the same seeded inputs.  Tolerance (from the method's
+contract): max-abs 1e-6 and L1 1e-5 against the oracle at the same sweep
+count."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+MAX_ABS, L1 = 1e-6, 1e-5
+
+
+@pytest.fixture(scope="module")
+def gp():
+    import torch
+
+    import paper_2010_16012_gb300 as gp
+
+    assert torch.cuda.is_available()
+    gp.load()
+    return gp
+
+
+def to_np(t):
+    return t.cpu().numpy() if hasattr(t, "cpu") else np.asarray(t)
+
+
+def assert_close(x, ref, what=""):
+    err = np.abs(to_np(x).astype(np.float64) - ref)
+    assert err.max() <= MAX_ABS and err.sum() <= L1, (what, float(err.max()), float(err.sum()))
+
+
+def run_and_check(gp, g, mode, iters=20, d=0.85, opts=None, weighted=True, **kw):
+    G = gp.Graph.from_graphgen(g, validate=True)
+    if opts:
+        G.set_options(**opts)
+    O = oracle.OracleGraph.from_graph(g, weighted=weighted)
+    x, st = gp.pagerank(G, mode, damping=d, iters=iters, **kw)
+    ref, k, _, _ = O.pagerank(oracle.PULL, d, iters=st["iters_done"])
+    assert st["iters_done"] == (iters if kw.get("tol", 0.0) == 0.0 else st["iters_done"])
+    assert_close(x, ref, (g.name, mode, opts))
+    return x, st
+
+
+ZOO = [
+    lambda: gg.complete(7),
+    lambda: gg.cycle(33),
+    lambda: gg.star(100),
+    lambda: gg.path(70),
+    lambda: gg.binary_tree(200),
+    lambda: gg.empty(5),
+    lambda: gg.empty(1),
+    lambda: gg.random_small(40, 0.1, seed=3),
+    lambda: gg.rmat(9, 8, seed=4, symmetrize=False),
+    lambda: gg.from_edges(6, [0, 1, 1, 2, 3, 5], [0, 1, 2, 2, 4, 5], drop_self=False, name="selfloops"),
+    lambda: gg.rmat(11, 16, seed=7),
+]
+OPTS = [None, {"pull_light_max": 0, "push_light_max": 0}, {"pull_light_max": 2, "push_light_max": 2, "chunk_edges": 32},
+        {"pull_light_max": 1 << 20, "push_light_max": 1 << 20}]
+
+
+@pytest.mark.parametrize("gi", range(len(ZOO)))
+@pytest.mark.parametrize("oi", range(len(OPTS)))
+@pytest.mark.parametrize("mode", [0, 1])
+def test_zoo(gp, gi, oi, mode):
+    run_and_check(gp, ZOO[gi](), mode, iters=13, opts=OPTS[oi])
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_rmat14_fixed_sweeps(gp, mode):
+    """The small R-MAT workload: scale 14, edge factor 16, seed 1, 20 sweeps."""
+    run_and_check(gp, gg.rmat(14, 16, seed=1), mode, iters=20)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_rmat14_to_tolerance(gp, mode):
+    g = gg.rmat(14, 16, seed=1)
+    x, st = run_and_check(gp, g, mode, iters=300, tol=1e-7)
+    assert st["converged"] and st["residual"] < 1e-7
+    O = oracle.OracleGraph.from_graph(g)
+    _, k, r, conv = O.pagerank(oracle.PULL, 0.85, iters=300, tol=1e-7)
+    assert abs(k - st["iters_done"]) <= 1
+
+
+@pytest.mark.parametrize("T", [31, 32, 33, 64, 65])
+def test_degree_at_thresholds(gp, T):
+    """A hub whose degree sits exactly at / next to the light limit and the chunk size."""
+    g = gg.star(T)
+    for opts in ({"pull_light_max": 32, "push_light_max": 32, "chunk_edges": 32},
+                 {"pull_light_max": 64, "push_light_max": 64, "chunk_edges": 64}):
+        for mode in (0, 1):
+            run_and_check(gp, g, mode, iters=9, opts=opts)
+
+
+def test_hub_spanning_many_chunks(gp):
+    g = gg.star(5000)
+    for mode in (0, 1):
+        run_and_check(gp, g, mode, iters=11, opts={"chunk_edges": 64})
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_weighted(gp, mode):
+    g = gg.rmat(10, 8, seed=5, symmetrize=False).with_weights(9)
+    run_and_check(gp, g, mode, iters=17)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_weighted_normalize_flag(gp, mode):
+    """GP_UPLOAD_NORMALIZE: P_vu = w_uv / sum of u's out-weights (computed in FP32 on the device)."""
+    g = gg.rmat(9, 8, seed=6, symmetrize=False).with_weights(10, normalize=False)
+    G = gp.Graph.from_graphgen(g, validate=True, normalize=True)
+    src, dst = g.edges()
+    w = g.csr_w.astype(np.float64)
+    rows = np.bincount(src, weights=w, minlength=g.n)
+    P = (w / rows[src]).astype(np.float32)
+    O = oracle.OracleGraph(g.n, src, dst, P)
+    x, st = gp.pagerank(G, mode, damping=0.85, iters=15)
+    ref, _, _, _ = O.pagerank(oracle.PULL, 0.85, iters=15)
+    assert_close(x, ref)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_personalization_and_x0(gp, mode):
+    import torch
+
+    g = gg.rmat(10, 8, seed=11, symmetrize=False)
+    rng = np.random.default_rng(1)
+    s = rng.random(g.n)
+    s /= s.sum()
+    x0 = rng.random(g.n)
+    x0 /= x0.sum()
+    G = gp.Graph.from_graphgen(g)
+    O = oracle.OracleGraph.from_graph(g)
+    s32, x032 = s.astype(np.float32), x0.astype(np.float32)
+    ref, _, _, _ = O.pagerank(oracle.PULL, 0.85, iters=12, personalization=s32.astype(np.float64),
+                              x0=x032.astype(np.float64))
+    # device inputs, device output
+    x, _ = gp.pagerank(G, mode, 0.85, 12, personalization=torch.from_numpy(s32).cuda(), x0=torch.from_numpy(x032).cuda())
+    assert_close(x, ref)
+    # host inputs, host output
+    out = np.zeros(g.n, dtype=np.float32)
+    gp.pagerank(G, mode, 0.85, 12, personalization=s32, x0=x032, out=out)
+    assert_close(out, ref)
+
+
+def test_one_hot_ppr(gp):
+    g = gg.rmat(10, 16, seed=2)
+    G = gp.Graph.from_graphgen(g)
+    O = oracle.OracleGraph.from_graph(g)
+    seed = int(gg.pick_vertices(g, 1, seed=6)[0])
+    e = np.zeros(g.n, dtype=np.float32)
+    e[seed] = 1.0
+    for mode in (0, 1):
+        x, st = gp.pagerank(G, mode, 0.85, 200, tol=1e-6, personalization=e)
+        ref, _, _, _ = O.pagerank(oracle.PULL, 0.85, iters=st["iters_done"], personalization=e.astype(np.float64))
+        assert_close(x, ref)
+
+
+def test_not_converged_returns_last_iterate(gp):
+    g = gg.rmat(10, 8, seed=3)
+    G = gp.Graph.from_graphgen(g)
+    O = oracle.OracleGraph.from_graph(g)
+    x, st = gp.pagerank(G, gp.PULL, 0.85, 5, tol=1e-12)
+    assert not st["converged"] and st["iters_done"] == 5
+    ref, _, _, _ = O.pagerank(oracle.PULL, 0.85, iters=5)
+    assert_close(x, ref)
+    with pytest.raises(gp.GpError) as e:
+        gp.pagerank(G, gp.PULL, 0.85, 5, tol=1e-12, raise_not_converged=True)
+    assert e.value.status == gp.ERR_NOT_CONVERGED
+
+
+@pytest.mark.parametrize("poll", [1, 3, 8])
+def test_poll_interval_and_parity_of_final_buffer(gp, poll):
+    """Convergence found at any sweep parity and any poll batch lands in ranks_out."""
+    g = gg.rmat(12, 8, seed=8)
+    G = gp.Graph.from_graphgen(g)
+    G.set_options(poll_interval=poll)
+    O = oracle.OracleGraph.from_graph(g)
+    for tol in (1e-3, 3e-4, 1e-4, 3e-5, 1e-5):
+        for mode in (0, 1):
+            x, st = gp.pagerank(G, mode, 0.85, 500, tol=tol)
+            assert st["converged"]
+            ref, _, _, _ = O.pagerank(oracle.PULL, 0.85, iters=st["iters_done"])
+            assert_close(x, ref)
+
+
+def test_pull_is_deterministic(gp):
+    g = gg.rmat(12, 16, seed=9)
+    G = gp.Graph.from_graphgen(g)
+    a, _ = gp.pagerank(G, gp.PULL, 0.85, 30)
+    b, _ = gp.pagerank(G, gp.PULL, 0.85, 30)
+    assert np.array_equal(to_np(a), to_np(b))
+
+
+def test_invalid_arguments(gp):
+    G = gp.Graph.from_graphgen(gg.path(10))
+    for kw in ({"damping": 1.0}, {"damping": 0.0}, {"iters": 0}, {"mode": 7}, {"tol": -1.0}):
+        args = dict(mode=gp.PULL, damping=0.85, iters=5, tol=0.0)
+        args.update(kw)
+        with pytest.raises(gp.GpError) as e:
+            gp.pagerank(G, **args)
+        assert e.value.status == gp.ERR_INVALID
+
+
+def test_malformed_uploads(gp):
+    import torch
+
+    def t(a):
+        return torch.from_numpy(np.asarray(a)).cuda()
+
+    off = t(np.array([0, 2, 1, 3], dtype=np.int64))  # not monotone
+    idx = t(np.array([1, 2, 0], dtype=np.int32))
+    with pytest.raises(gp.GpError) as e:
+        gp.Graph(3, off, idx, symmetric=True)
+    assert e.value.status == gp.ERR_INVALID
+    off = t(np.array([0, 1, 2, 3], dtype=np.int64))
+    bad = t(np.array([1, 2, 3], dtype=np.int32))  # index 3 >= n
+    with pytest.raises(gp.GpError):
+        gp.Graph(3, off, bad, symmetric=True)
+    short = t(np.array([0, 1, 2, 2], dtype=np.int64))  # off[n] != m
+    with pytest.raises(gp.GpError):
+        gp.Graph(3, short, idx, symmetric=True)
+    # CSR and CSC that disagree, caught by validation
+    g = gg.rmat(8, 8, seed=1, symmetrize=False)
+    csc_idx = g.csc_idx.copy()
+    csc_idx[0] = (csc_idx[0] + 1) % g.n
+    with pytest.raises(gp.GpError, match="same edges"):
+        gp.Graph(g.n, t(g.csr_off), t(g.csr_idx), t(g.csc_off), t(csc_idx), validate=True)
+    # a directed graph flagged symmetric
+    with pytest.raises(gp.GpError, match="symmetric"):
+        gp.Graph(g.n, t(g.csr_off), t(g.csr_idx), symmetric=True, validate=True)
+    # host arrays without the copy flag
+    with pytest.raises(gp.GpError):
+        gp.Graph(g.n, g.csr_off, g.csr_idx, g.csc_off, g.csc_idx, copy=False)
+
+
+def test_upload_copy_from_host(gp):
+    g = gg.rmat(10, 16, seed=12)
+    G = gp.Graph.from_graphgen(g, copy=True, validate=True)
+    O = oracle.OracleGraph.from_graph(g)
+    x, _ = gp.pagerank(G, gp.PULL, 0.85, 10)
+    ref, _, _, _ = O.pagerank(oracle.PULL, 0.85, iters=10)
+    assert_close(x, ref)
+
+
+def test_oom_from_allocator_hook(gp):
+    """A failing allocator surfaces as GP_ERR_OOM (nothing is launched)."""
+    lib = gp.load()
+    calls = []
+
+    @gp.ALLOC_FN
+    def bad_alloc(nbytes, stream, ctx):
+        calls.append(nbytes)
+        return None
+
+    @gp.FREE_FN
+    def bad_free(p, nbytes, stream, ctx):
+        pass
+
+    g = gg.path(100)
+    assert lib.gp_set_allocator(bad_alloc, bad_free, None) == gp.OK
+    try:
+        with pytest.raises(gp.GpError) as e:
+            gp.Graph.from_graphgen(g)
+        assert e.value.status == gp.ERR_OOM and calls
+    finally:
+        assert lib.gp_set_allocator(gp.ALLOC_FN(), gp.FREE_FN(), None) == gp.OK
+    gp.Graph.from_graphgen(g).free()
+
+
+def test_graph_info(gp):
+    g = gg.rmat(12, 16, seed=1)
+    G = gp.Graph.from_graphgen(g)
+    info = G.info()
+    d = g.out_degree()
+    assert info["n"] == g.n and info["m"] == g.m
+    assert info["max_out_degree"] == d.max()
+    assert info["isolated"] == int(((d == 0) & (g.in_degree() == 0)).sum())
+    lm = G.options().pull_light_max
+    assert info["pull_big_vertices"] == int((g.in_degree() > lm).sum())
