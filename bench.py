@@ -1,0 +1,503 @@
+#!/usr/bin/env python
+"""Benchmark of the push/pull sweep path on one R-MAT scale-22 graph.
+
+One step runs the whole hot path once on the graph already resident in HBM:
+  gp_graph_upload (validation + degree preparation + degree bins),
+  gp_pagerank PULL, PUSH and AUTO, each to L1 tolerance 1e-7 (cap 300 sweeps),
+  gp_bfs AUTO (direction-switching) from 64 random non-isolated sources.
+Metric: traversed edges per second (GTEPS): m per PageRank sweep, and for BFS
+the undirected edges of the reached component (Graph500 convention, the graph
+being symmetric).  One JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (FP64, all host cores) on a bounded
+sample of the same workload.  Under torchrun every rank runs the same per-GPU
+workload (weak scaling, no data-path collective); timings are the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PR/BFS GTEPS push vs pull vs auto, batched vs serial, % HBM peak, 1 GB300"
+WORKLOAD = ("R-MAT scale 22 (A/B/C/D .57/.19/.19/.05, edge factor 16, seed 1, symmetrised, no self-loops or "
+            "duplicates): PageRank PULL+PUSH+AUTO to L1 tol 1e-7 (d=0.85, cap 300) and direction-switching BFS "
+            "from 64 random non-isolated sources (seed 2)")
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--scale", type=int, default=22)
+    p.add_argument("--sources", type=int, default=64)
+    p.add_argument("--tol", type=float, default=1e-7)
+    p.add_argument("--cap", type=int, default=300)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--quiet", action="store_true")
+    return p.parse_args(argv)
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------------------ distributed plumbing
+
+class Dist:
+    """Rank bookkeeping; with WORLD_SIZE > 1 a process group used only for the
+    timing barrier and the max-over-ranks reduction."""
+
+    def __init__(self, backend=None):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group(backend=backend or "nccl")
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            if self.pg.get_backend() == "nccl":
+                import torch
+
+                self.pg.barrier(device_ids=[torch.cuda.current_device()])
+            else:
+                self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def aggregate(per_rank_units: float, per_rank_ms: float, dist: Dist) -> tuple:
+    """Whole-job throughput: units summed over ranks / slowest rank's time."""
+    total_units = dist.sum(per_rank_units)
+    ms = dist.max(per_rank_ms)
+    return total_units / (ms * 1e-3) if ms > 0 else 0.0, ms
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        loaded = [c for c in sm if c > 0.5 * (max(smax) if smax else 1)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ inputs
+
+def make_graph(scale: int):
+    import graphgen as gg
+
+    t = time.time()
+    g = gg.rmat(scale, 16, seed=1)
+    log(f"[bench] R-MAT scale {scale}: n={g.n} m={g.m} ({time.time() - t:.1f}s)")
+    return g
+
+
+def pick_sources(g, count: int):
+    import graphgen as gg
+
+    return gg.pick_vertices(g, count, seed=2)
+
+
+def measured_peak_gbs():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ algorithmic bytes per kernel launch
+
+def kernel_bytes(g, opt) -> dict:
+    """Compulsory bytes of one (working) launch of each PageRank sweep kernel;
+    random re-gathers that miss L2 are not counted."""
+    n, m = g.n, g.m
+    din, dout = g.in_degree(), g.out_degree()
+    C = opt.chunk_edges
+    big_in = din > opt.pull_light_max
+    big_out = dout > opt.push_light_max
+    e_big_in = int(din[big_in].sum())
+    ch_in = int(((din[big_in] + C - 1) // C).sum())
+    nb_in = int(big_in.sum())
+    ch_out = int(((dout[big_out] + C - 1) // C).sum())
+    return {
+        # big in-edge lists: indices + chunk table + chunk partials written
+        "pull_big": 4 * e_big_in + 16 * ch_in + 4 * ch_in,
+        # light in-edge lists + offsets + c (once) + x, inv_deg read + y, c' written + big-vertex combine
+        "pull_light": 4 * (m - e_big_in) + 8 * (n + 1) + 4 * n * 5 + 4 * ch_in + 12 * nb_in,
+        # all out-edge lists + offsets + c + y read-modify-write + chunk table
+        "push_scatter": 4 * m + 8 * (n + 1) + 4 * n + 8 * n + 16 * ch_out,
+        # y, x, inv_deg read; c and the reset buffer written
+        "push_epilogue": 20 * n,
+    }
+
+
+def bfs_level_bytes(n: int, direction: int, frontier: int, examined: int, unvisited: int, new: int) -> tuple:
+    """Compulsory bytes of one BFS level: (kernel name, bytes).  Top-down: queue
+    entries, their offsets, the scanned out-edge indices, and for each newly
+    visited vertex the level CAS, parent, offsets and queue write.  Bottom-up:
+    the level array, offsets of unvisited vertices, the scanned in-edge indices
+    and the new bitmap."""
+    if direction == 0:
+        return "bfs_topdown", 4 * frontier + 16 * frontier + 4 * examined + new * (4 + 4 + 32 + 4)
+    return "bfs_bottomup", 4 * n + 16 * unvisited + 4 * examined + n // 8 + new * 8
+
+
+def sweep_bytes(g):
+    """Compulsory bytes of one full pull sweep: 4m + 28n (+8)."""
+    return 4 * g.m + 28 * g.n + 8
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, dist: Dist):
+    import torch
+
+    import paper_2010_16012_gb300 as gp
+
+    torch.cuda.set_device(dist.local_rank)
+    gp.load()
+    g = make_graph(args.scale)
+    srcs = pick_sources(g, args.sources)
+    dev = torch.device("cuda", dist.local_rank)
+    off = torch.from_numpy(g.csr_off).to(dev)
+    idx = torch.from_numpy(g.csr_idx).to(dev)
+    n, m = g.n, g.m
+    ranks = [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(3)]
+    level = torch.empty(n, dtype=torch.int32, device=dev)
+    parent = torch.empty(n, dtype=torch.int32, device=dev)
+    modes = [(gp.PULL, "pull"), (gp.PUSH, "push"), (gp.AUTO, "auto")]
+
+    kb = kernel_bytes(g, gp.default_options())
+    pr_kernels = {gp.PULL: ("pull_big", "pull_light"), gp.PUSH: ("push_scatter", "push_epilogue")}
+
+    def step(work=None):
+        t0 = time.perf_counter()
+        G = gp.Graph(n, off, idx, symmetric=True)
+        t1 = time.perf_counter()
+        edges = 0.0
+        parts = {"upload_ms": (t1 - t0) * 1e3}
+        for i, (mode, name) in enumerate(modes):
+            ta = time.perf_counter()
+            _, st = gp.pagerank(G, mode, 0.85, args.cap, args.tol, out=ranks[i])
+            tb = time.perf_counter()
+            k = st["iters_done"]
+            edges += m * k
+            parts[f"pr_{name}"] = {"sweeps": k, "ms": (tb - ta) * 1e3, "gteps": m * k / (tb - ta) / 1e9,
+                                   "converged": st["converged"], "residual": st["residual"],
+                                   "mode_used": "push" if st["mode_used"] == gp.PUSH else "pull"}
+            if work is not None:
+                for kn in pr_kernels[st["mode_used"]]:
+                    w = work.setdefault(kn, [0.0, 0])
+                    w[0] += kb[kn] * k
+                    w[1] += k
+        bfs_ms, bfs_edges, hm, switches = 0.0, 0.0, [], 0
+        for s in srcs:
+            ta = time.perf_counter()
+            _, _, st = gp.bfs(G, int(s), gp.AUTO, level=level, parent=parent)
+            tb = time.perf_counter()
+            e = st["edges_reached"] / 2  # undirected edges of the component
+            edges += e
+            bfs_ms += (tb - ta) * 1e3
+            bfs_edges += e
+            hm.append(e / (tb - ta) / 1e9)
+            switches += st["switches"]
+            if work is not None:
+                seen = 0
+                fr = st["frontier"] + [0]
+                for L, d in enumerate(st["direction"]):
+                    seen += fr[L]
+                    kn, by = bfs_level_bytes(n, d, fr[L], st["examined"][L], n - seen, fr[L + 1])
+                    w = work.setdefault(kn, [0.0, 0])
+                    w[0] += by
+                    w[1] += 1
+        parts["bfs_auto"] = {"sources": len(srcs), "ms": bfs_ms, "gteps_total": bfs_edges / bfs_ms / 1e6,
+                             "gteps_harmonic_mean": len(hm) / sum(1.0 / max(h, 1e-12) for h in hm),
+                             "switches_per_source": switches / max(len(srcs), 1)}
+        G.free()
+        return edges, parts
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dist.local_rank)
+    clocks.start()
+    gp.profile_read(reset=True)
+    gp.profile_enable(True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    tot_edges, parts, work = 0.0, None, {}
+    for _ in range(args.steps):
+        e, parts = step(work)
+        tot_edges += e
+    e1.record()
+    torch.cuda.synchronize()
+    dist.barrier()
+    gp.profile_enable(False)
+    kt = gp.profile_read(reset=True)
+    clk = clocks.stop()
+    ms_step = e0.elapsed_time(e1) / args.steps
+    value_eps, ms_max = aggregate(tot_edges / args.steps, ms_step, dist)
+
+    # roofline of the dominant kernel (largest total device time in the timed
+    # region): compulsory bytes of its working launches / its total time
+    # (which also contains its early-exit launches after convergence)
+    peak, peak_kind = measured_peak_gbs()
+    launches = int(sum(k[1] for k in kt))
+    total_kernel_ms = sum(k[2] for k in kt)
+    kernels = [{"name": k[0], "launches": k[1], "total_ms": round(k[2], 3),
+                "share": round(k[2] / total_kernel_ms, 4) if total_kernel_ms else None} for k in kt]
+    roofline = None
+    if kt:
+        top = kt[0]
+        by, real = work.get(top[0], [0.0, 0])
+        if real:
+            ach = by / (top[2] * 1e-3) / 1e9
+            roofline = {"kernel": top[0], "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(ach / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                        "bytes_per_launch": int(by / real), "avg_launch_ms": round(top[2] / real, 5),
+                        "share": round(top[2] / total_kernel_ms, 4)}
+    # the pull sweep as a whole (both pull kernels): the benchmark spec's 40%-of-HBM figure
+    pull_sweep = None
+    if "pull_light" in work and work["pull_light"][1]:
+        tk = {k[0]: k for k in kt}
+        sweeps = work["pull_light"][1]
+        ms = (tk["pull_big"][2] + tk["pull_light"][2]) / sweeps
+        ach = sweep_bytes(g) / (ms * 1e-3) / 1e9
+        pull_sweep = {"sweeps": sweeps, "ms_per_sweep": round(ms, 5), "achieved": round(ach, 1), "peak": peak,
+                      "unit": "GB/s", "frac": round(ach / peak, 4), "bytes_per_sweep": sweep_bytes(g),
+                      "gteps": round(m / (ms * 1e-3) / 1e9, 2)}
+
+    out = {"metric": METRIC, "value": round(value_eps / 1e9, 4), "unit": "GTEPS", "n_gpus": dist.world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n": n, "m": m, "sources": int(len(srcs)),
+                      "l2": "inputs larger than L2 (CSR 0.55 GB > 129 MB); no flush between steps",
+                      "parallelism": f"replicas{dist.world}"},
+           "parts": parts, "roofline": roofline, "pull_sweep_roofline": pull_sweep,
+           "gpu_launches": launches, "kernels": kernels[:14], "clocks": clk}
+    if not args.no_e2e:
+        out["e2e"] = run_e2e(args, g, srcs, dist)
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(g, srcs, args)
+    return out
+
+
+def run_e2e(args, g, srcs, dist: Dist):
+    """Same step through the C ABI with host buffers: the CSR arrays are copied
+    from pinned host memory by gp_graph_upload (GP_UPLOAD_COPY) and every result
+    (three rank vectors, 64 level + parent vectors) is written back to pinned
+    host memory, all inside the timed region."""
+    import torch
+
+    import paper_2010_16012_gb300 as gp
+
+    n, m = g.n, g.m
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+    off_h, idx_h = pin(g.csr_off), pin(g.csr_idx)
+    ranks_h = [torch.empty(n, dtype=torch.float32).pin_memory().numpy() for _ in range(3)]
+    lv_h = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
+    pa_h = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
+    h2d = off_h.nbytes + idx_h.nbytes
+    d2h = 3 * 4 * n + len(srcs) * 8 * n
+
+    def step():
+        G = gp.Graph(n, off_h, idx_h, symmetric=True, copy=True)
+        edges = 0.0
+        for i, mode in enumerate((gp.PULL, gp.PUSH, gp.AUTO)):
+            _, st = gp.pagerank(G, mode, 0.85, args.cap, args.tol, out=ranks_h[i])
+            edges += m * st["iters_done"]
+        for s in srcs:
+            _, _, st = gp.bfs(G, int(s), gp.AUTO, level=lv_h, parent=pa_h)
+            edges += st["edges_reached"] / 2
+        G.free()
+        return edges
+
+    step()
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 3))
+    dist.barrier()
+    t0 = time.perf_counter()
+    tot = 0.0
+    for _ in range(steps):
+        tot += step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    ms = (time.perf_counter() - t0) * 1e3 / steps
+    v, _ = aggregate(tot / steps, ms, dist)
+    return {"value": round(v / 1e9, 4), "unit": "GTEPS", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": steps, "ms_per_step": round(ms, 3)}
+
+
+# ------------------------------------------------------------------ CPU oracle (baseline and reference arm)
+
+def oracle_sample(g, srcs, O, sweeps: int, nsrc: int, threads: int):
+    """One bounded sample of the workload on the CPU oracle: `sweeps` pull
+    PageRank sweeps, one push sweep, and FIFO BFS from `nsrc` sources."""
+    import oracle
+
+    t = time.perf_counter()
+    O.pagerank(oracle.PULL, 0.85, iters=sweeps, nthreads=threads)
+    O.pagerank(oracle.PUSH, 0.85, iters=1)
+    edges = g.m * (sweeps + 1)
+    for s in srcs[:nsrc]:
+        lv, _ = O.bfs(int(s))
+        edges += float(g.out_degree()[lv >= 0].sum()) / 2
+    return edges, time.perf_counter() - t
+
+
+def cpu_baseline(g, srcs, args):
+    import oracle
+
+    threads = oracle.max_threads()
+    O = oracle.OracleGraph.from_graph(g)
+    sweeps, nsrc = 8, 2
+    edges, sec = oracle_sample(g, srcs, O, sweeps, nsrc, threads)
+    return {"value": round(edges / sec / 1e9, 5), "unit": "GTEPS", "cores": threads, "kind": "oracle",
+            "sample": f"{sweeps} pull PageRank sweeps ({threads} threads) + 1 push sweep (1 thread) + FIFO BFS "
+                      f"from {nsrc} of the sources, on the full scale-{args.scale} graph; {sec:.1f} s"}
+
+
+def run_reference(args, dist: Dist):
+    import oracle
+
+    if dist.rank != 0:
+        return None
+    g = make_graph(args.scale)
+    srcs = pick_sources(g, args.sources)
+    threads = oracle.max_threads()
+    O = oracle.OracleGraph.from_graph(g)
+    sweeps, nsrc = 3, 1
+    for _ in range(args.warmup):
+        oracle_sample(g, srcs, O, 1, 0, threads)
+    tot, sec = 0.0, 0.0
+    for _ in range(args.steps):
+        e, s = oracle_sample(g, srcs, O, sweeps, nsrc, threads)
+        tot += e
+        sec += s
+    v = tot / sec / 1e9
+    sample = (f"per step {sweeps} pull PageRank sweeps ({threads} threads) + 1 push sweep + FIFO BFS from "
+              f"{nsrc} source on the full scale-{args.scale} graph")
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": "GTEPS", "n_gpus": dist.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "parallelism": "cpu oracle"},
+            "cpu_baseline": {"value": round(v, 5), "unit": "GTEPS", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(v, 5), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        dist = Dist(backend="gloo") if int(os.environ.get("WORLD_SIZE", "1")) > 1 else Dist()
+        out = run_reference(args, dist)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        dist.close()
+        return 0
+    import torch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dist = Dist()
+    out = run_ours(args, dist)
+    if dist.rank == 0:
+        print(json.dumps(out), flush=True)
+    dist.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

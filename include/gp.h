@@ -154,7 +154,9 @@ typedef struct gp_options {
     int32_t pr_auto_mode;     /* what GP_AUTO means for PageRank: GP_PUSH, GP_PULL, or -1 = rule */
     float bfs_alpha;          /* top-down -> bottom-up when m_f > m_u / alpha */
     float bfs_beta;           /* bottom-up -> top-down when n_f < n / beta (frontier shrinking) */
-    int32_t reserved[8];
+    int32_t push_fp64_accum;  /* push PageRank: 1 = accumulate the scattered updates with FP64
+                                 atomics (default; ranks stay FP32), 0 = FP32 atomics */
+    int32_t reserved[7];
 } gp_options;
 
 /* Fill *opt with the built-in defaults. */

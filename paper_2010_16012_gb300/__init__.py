@@ -41,7 +41,7 @@ class gp_options(ctypes.Structure):
                 ("chunk_edges", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("poll_interval", ctypes.c_int32), ("pr_auto_mode", ctypes.c_int32),
                 ("bfs_alpha", ctypes.c_float), ("bfs_beta", ctypes.c_float),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("push_fp64_accum", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 class gp_graph_info(ctypes.Structure):

@@ -335,7 +335,7 @@ static int bfs_run(const gp_graph *gc, int32_t src, int mode, const int8_t *dirs
     a.nxt = ctr + 0;
     a.queue_next = w.queue[0];
     a.h_next = w.hchunk[0];
-    k_bfs_seed<<<1, 32, 0, s>>>(a, src);
+    GP_LAUNCH("bfs_seed", s, (k_bfs_seed<<<1, 32, 0, s>>>(a, src)));
     GP_TRY(check_launch("bfs seed"));
     GP_CUDA(cudaMemcpyAsync(hctr, ctr, sizeof(BfsCtr), cudaMemcpyDeviceToHost, s));
     GP_CUDA(cudaStreamSynchronize(s));

@@ -124,6 +124,7 @@ struct PrWork {
     float *out_dev = nullptr;      // output buffer when ranks_out is host memory
     double *partials = nullptr;    // per-block residual partials
     float *chunk_part = nullptr;   // per-chunk partial sums (pull, big vertices)
+    double *acc64 = nullptr;       // FP64 accumulator of the push scatter
     void *status = nullptr;        // device PrStatus
     void *status_host = nullptr;   // pinned mirror
     int max_blocks = 0;

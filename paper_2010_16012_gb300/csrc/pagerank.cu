@@ -68,6 +68,7 @@ struct PrArgs {
     int32_t nprev;
     double *partials;
     float *chunk_part;
+    double *acc64;  // FP64 push accumulator (or nullptr)
     PrStatus *status;
     int32_t split_blocks;  // pull: light-tile blocks; push: big-chunk blocks
 };
@@ -108,7 +109,7 @@ __device__ bool pr_gate(const PrArgs &a, int k) {
 }
 
 __global__ void k_pr_init(int64_t n, const float *x0, const float *inv_deg, float *r0, float *c, float *r_push,
-                          const float *s, float one_minus_d, float base_uniform, PrStatus *status) {
+                          double *acc64, const float *s, float one_minus_d, float base_uniform, PrStatus *status) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const float x_uniform = 1.0f / (float)n;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
@@ -116,6 +117,7 @@ __global__ void k_pr_init(int64_t n, const float *x0, const float *inv_deg, floa
         r0[v] = x;
         c[v] = x * inv_deg[v];
         if (r_push) r_push[v] = s ? one_minus_d * s[v] : base_uniform;
+        if (acc64) acc64[v] = (double)(s ? one_minus_d * s[v] : base_uniform);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         status->done = 0;
@@ -250,13 +252,16 @@ __global__ void __launch_bounds__(256) k_pull_light(PrArgs a) {
 
 // ------------------------------------------------------------------ push
 
-template <bool W>
+// Accumulator of the scattered updates: FP32 (the paper's float atomics) or
+// FP64 (same atomic count; the order-dependent rounding of FP32 atomics at hubs
+// otherwise leaves an L1 residual floor above 1e-7 on graphs with 4M vertices).
+template <bool W, class T>
 __global__ void __launch_bounds__(256) k_push_scatter(PrArgs a) {
     if (pr_gate(a, a.k)) return;
     const int lane = lane_id();
     const int32_t *__restrict__ idx = a.idx;
     const float *__restrict__ wv = a.w;
-    float *y = a.y;
+    T *y = sizeof(T) == 8 ? (T *)a.acc64 : (T *)a.y;
     if ((int)blockIdx.x < a.split_blocks) {
         const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
         const int64_t nwarps = ((int64_t)a.split_blocks * blockDim.x) >> 5;
@@ -268,14 +273,15 @@ __global__ void __launch_bounds__(256) k_push_scatter(PrArgs a) {
             int i = lane;
             for (; i + 96 < ch.len; i += 128) {
                 const int v0 = __ldg(ip + i), v1 = __ldg(ip + i + 32), v2 = __ldg(ip + i + 64), v3 = __ldg(ip + i + 96);
-                atomicAdd(y + v0, W ? cu * __ldg(wp + i) : cu);
-                atomicAdd(y + v1, W ? cu * __ldg(wp + i + 32) : cu);
-                atomicAdd(y + v2, W ? cu * __ldg(wp + i + 64) : cu);
-                atomicAdd(y + v3, W ? cu * __ldg(wp + i + 96) : cu);
+                atomicAdd(y + v0, (T)(W ? cu * __ldg(wp + i) : cu));
+                atomicAdd(y + v1, (T)(W ? cu * __ldg(wp + i + 32) : cu));
+                atomicAdd(y + v2, (T)(W ? cu * __ldg(wp + i + 64) : cu));
+                atomicAdd(y + v3, (T)(W ? cu * __ldg(wp + i + 96) : cu));
             }
-            for (; i < ch.len; i += 32) atomicAdd(y + __ldg(ip + i), W ? cu * __ldg(wp + i) : cu);
+            for (; i < ch.len; i += 32) atomicAdd(y + __ldg(ip + i), (T)(W ? cu * __ldg(wp + i) : cu));
         }
     } else {
+        __shared__ T agg[256];
         const int64_t n = a.n;
         const int64_t warp = ((int64_t)(blockIdx.x - a.split_blocks) * blockDim.x + threadIdx.x) >> 5;
         const int64_t nwarps = ((int64_t)(gridDim.x - a.split_blocks) * blockDim.x) >> 5;
@@ -306,15 +312,38 @@ __global__ void __launch_bounds__(256) k_push_scatter(PrArgs a) {
                 const int64_t kb = __shfl_sync(FULL, b, k);
                 const int kex = __shfl_sync(FULL, excl, k);
                 const float ck = __shfl_sync(FULL, cu, k);
+                int32_t dst = -1 - lane;  // distinct dummy keys for idle lanes
+                T val = 0;
                 if (eid < E) {
                     const int64_t pos = kb + (eid - kex);
-                    atomicAdd(y + __ldg(idx + pos), W ? ck * __ldg(wv + pos) : ck);
+                    dst = __ldg(idx + pos);
+                    val = (T)(W ? ck * __ldg(wv + pos) : ck);
+                }
+                // Updates from different sources of the tile that hit the same vertex
+                // (typically a hub) are summed in the warp first, so the vertex takes one
+                // atomic per window instead of one per edge.
+                const unsigned peers = __match_any_sync(FULL, dst);
+                if (__all_sync(FULL, peers == (1u << lane))) {
+                    if (eid < E) atomicAdd(y + dst, val);
+                } else {
+                    agg[threadIdx.x] = val;
+                    __syncwarp();
+                    if (eid < E && (peers & ((1u << lane) - 1u)) == 0) {  // lowest lane of its group
+                        T sum = val;
+                        for (unsigned rest = peers & ~(1u << lane); rest; rest &= rest - 1)
+                            sum += agg[(threadIdx.x & ~31u) + (__ffs(rest) - 1)];
+                        atomicAdd(y + dst, sum);
+                    }
+                    __syncwarp();
                 }
             }
         }
     }
 }
 
+// Per vertex: the finished sum (rounded to the FP32 rank), the residual, the
+// next contribution, and the reset of the buffer the next sweep accumulates into.
+template <class T>
 __global__ void __launch_bounds__(256) k_push_epilogue(PrArgs a) {
     __shared__ double sm[32];
     if (((volatile PrStatus *)a.status)->done) return;
@@ -322,10 +351,18 @@ __global__ void __launch_bounds__(256) k_push_epilogue(PrArgs a) {
     double res = 0.0;
     float *x_reset = const_cast<float *>(a.x);
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += stride) {
-        const float y = a.y[v];
-        res += fabs((double)y - (double)a.x[v]);
-        a.c_next[v] = y * a.inv_deg[v];
-        x_reset[v] = base_term(a, v);  // the next sweep accumulates into this buffer
+        if (sizeof(T) == 8) {
+            const float y = (float)a.acc64[v];
+            res += fabs((double)y - (double)a.x[v]);
+            a.y[v] = y;
+            a.c_next[v] = y * a.inv_deg[v];
+            a.acc64[v] = (double)base_term(a, v);
+        } else {
+            const float y = a.y[v];
+            res += fabs((double)y - (double)a.x[v]);
+            a.c_next[v] = y * a.inv_deg[v];
+            x_reset[v] = base_term(a, v);  // the next sweep accumulates into this buffer
+        }
     }
     res = block_sum(res, sm);
     if (threadIdx.x == 0) a.partials[blockIdx.x] = res;
@@ -469,7 +506,11 @@ extern "C" int gp_pagerank(const gp_graph *gc, int mode, float damping, int iter
     a.split_blocks = split;
 
     const int ib = (int)std::max<int64_t>(1, std::min<int64_t>(gb, (n + 255) / 256));
-    GP_LAUNCH("pr_init", s, (k_pr_init<<<ib, 256, 0, s>>>(n, X0, g->inv_deg, R[0], C[0], push ? R[1] : nullptr, S,
+    const bool fp64 = push && g->opt.push_fp64_accum;
+    if (fp64 && !w.acc64) GP_TRY(w.mem.alloc(w.acc64, (size_t)n, s));
+    a.acc64 = fp64 ? w.acc64 : nullptr;
+    GP_LAUNCH("pr_init", s, (k_pr_init<<<ib, 256, 0, s>>>(n, X0, g->inv_deg, R[0], C[0], (push && !fp64) ? R[1] : nullptr,
+                                                          a.acc64, S,
                                                           a.one_minus_d, a.base_uniform, status)));
     GP_TRY(check_launch("pr_init"));
 
@@ -491,18 +532,26 @@ extern "C" int gp_pagerank(const gp_graph *gc, int mode, float damping, int iter
         } else {
             b.c = C[0];
             b.c_next = C[0];
-            if (W)
-                GP_LAUNCH("push_scatter", s, (k_push_scatter<true><<<g1, 256, 0, s>>>(b)));
-            else
-                GP_LAUNCH("push_scatter", s, (k_push_scatter<false><<<g1, 256, 0, s>>>(b)));
-            GP_LAUNCH("push_epilogue", s, (k_push_epilogue<<<g2, 256, 0, s>>>(b)));
+            if (fp64) {
+                if (W)
+                    GP_LAUNCH("push_scatter", s, (k_push_scatter<true, double><<<g1, 256, 0, s>>>(b)));
+                else
+                    GP_LAUNCH("push_scatter", s, (k_push_scatter<false, double><<<g1, 256, 0, s>>>(b)));
+                GP_LAUNCH("push_epilogue", s, (k_push_epilogue<double><<<g2, 256, 0, s>>>(b)));
+            } else {
+                if (W)
+                    GP_LAUNCH("push_scatter", s, (k_push_scatter<true, float><<<g1, 256, 0, s>>>(b)));
+                else
+                    GP_LAUNCH("push_scatter", s, (k_push_scatter<false, float><<<g1, 256, 0, s>>>(b)));
+                GP_LAUNCH("push_epilogue", s, (k_push_epilogue<float><<<g2, 256, 0, s>>>(b)));
+            }
         }
         return check_launch("pagerank sweep");
     };
     auto enqueue_finish = [&](int k_next, int slot) -> int {
         PrArgs b = a;
         b.k = k_next;
-        k_pr_finish<<<1, 256, 0, s>>>(b);
+        GP_LAUNCH("pr_finish", s, (k_pr_finish<<<1, 256, 0, s>>>(b)));
         GP_TRY(check_launch("pr_finish"));
         GP_CUDA(cudaMemcpyAsync((PrStatus *)w.status_host + slot, status, sizeof(PrStatus), cudaMemcpyDeviceToHost, s));
         return GP_OK;

@@ -215,15 +215,15 @@ static int exclusive_scan(const int64_t *in, int64_t *out, int64_t N, Arena &tmp
     }
     int64_t nb = (N + SCAN_TILE - 1) / SCAN_TILE;
     if (nb == 1) {
-        k_scan_tiles<<<1, SCAN_THREADS, 0, s>>>(in, out, N, nullptr);
+        GP_LAUNCH("scan_tiles", s, (k_scan_tiles<<<1, SCAN_THREADS, 0, s>>>(in, out, N, nullptr)));
         return check_launch("scan");
     }
     int64_t *sums;
     GP_TRY(tmp.alloc(sums, nb + 1, s));
-    k_tile_sums<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, N, sums);
+    GP_LAUNCH("tile_sums", s, (k_tile_sums<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, N, sums)));
     GP_TRY(check_launch("scan sums"));
     GP_TRY(exclusive_scan(sums, sums, nb, tmp, s));
-    k_scan_tiles<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, N, sums);
+    GP_LAUNCH("scan_tiles", s, (k_scan_tiles<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, N, sums)));
     return check_launch("scan tiles");
 }
 
@@ -430,7 +430,7 @@ int build_bins(gp_graph *g, BigBins &b, const int64_t *off, int32_t light_max, i
     int64_t *segc;
     int st = tmp.alloc(segc, nseg + 1, s);
     if (st != GP_OK) return st;
-    k_count_big<<<(unsigned)nseg, 256, 0, s>>>(off, n, light_max, segc);
+    GP_LAUNCH("count_big", s, (k_count_big<<<(unsigned)nseg, 256, 0, s>>>(off, n, light_max, segc)));
     st = check_launch("count_big");
     if (st == GP_OK) st = exclusive_scan(segc, segc, nseg, tmp, s);
     int64_t nbig = 0;
@@ -441,14 +441,14 @@ int build_bins(gp_graph *g, BigBins &b, const int64_t *off, int32_t light_max, i
     }
     if (st == GP_OK) st = b.mem.alloc(b.big, (size_t)std::max<int64_t>(nbig, 1), s);
     if (st == GP_OK) {
-        k_write_big<<<(unsigned)nseg, 256, 0, s>>>(off, n, light_max, segc, b.big, rank);
+        GP_LAUNCH("write_big", s, (k_write_big<<<(unsigned)nseg, 256, 0, s>>>(off, n, light_max, segc, b.big, rank)));
         st = check_launch("write_big");
     }
     if (st == GP_OK) st = b.mem.alloc(b.cstart, (size_t)nbig + 1, s);
     int64_t nchunks = 0;
     if (st == GP_OK && nbig > 0) {
         int blocks = (int)std::min<int64_t>((nbig + 255) / 256, 65535);
-        k_chunk_counts<<<blocks, 256, 0, s>>>(b.big, nbig, off, chunk_edges, b.cstart);
+        GP_LAUNCH("chunk_counts", s, (k_chunk_counts<<<blocks, 256, 0, s>>>(b.big, nbig, off, chunk_edges, b.cstart)));
         st = check_launch("chunk_counts");
         if (st == GP_OK) st = exclusive_scan(b.cstart, b.cstart, nbig, tmp, s);
         if (st == GP_OK) {
@@ -458,7 +458,7 @@ int build_bins(gp_graph *g, BigBins &b, const int64_t *off, int32_t light_max, i
         }
         if (st == GP_OK) st = b.mem.alloc(b.chunks, (size_t)std::max<int64_t>(nchunks, 1), s);
         if (st == GP_OK) {
-            k_fill_chunks<<<blocks, 256, 0, s>>>(b.big, nbig, off, b.cstart, chunk_edges, b.chunks);
+            GP_LAUNCH("fill_chunks", s, (k_fill_chunks<<<blocks, 256, 0, s>>>(b.big, nbig, off, b.cstart, chunk_edges, b.chunks)));
             st = check_launch("fill_chunks");
         }
     } else if (st == GP_OK) {
@@ -533,6 +533,7 @@ int gp_options_default(gp_options *opt) {
     opt->pr_auto_mode = -1;
     opt->bfs_alpha = 14.0f;
     opt->bfs_beta = 24.0f;
+    opt->push_fp64_accum = 1;
     return GP_OK;
 }
 
@@ -654,8 +655,9 @@ int gp_graph_upload(gp_graph **out, int64_t n, int64_t m, const int64_t *csr_off
         cudaError_t e = cudaMemsetAsync(err, 0, 4 * sizeof(unsigned), s);
         int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)g->num_sms * 8));
         if (e == cudaSuccess) {
-            k_check_offsets<<<blocks, 256, 0, s>>>(g->csr_off, n, m, err);
-            if (g->csc_off != g->csr_off) k_check_offsets<<<blocks, 256, 0, s>>>(g->csc_off, n, m, err + 1);
+            GP_LAUNCH("check_offsets", s, (k_check_offsets<<<blocks, 256, 0, s>>>(g->csr_off, n, m, err)));
+            if (g->csc_off != g->csr_off)
+                GP_LAUNCH("check_offsets", s, (k_check_offsets<<<blocks, 256, 0, s>>>(g->csc_off, n, m, err + 1)));
             e = cudaMemcpyAsync(herr, err, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s);
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -665,8 +667,9 @@ int gp_graph_upload(gp_graph **out, int64_t n, int64_t m, const int64_t *csr_off
                                                herr[0] ? "CSR" : "CSC", herr[0] ? herr[0] : herr[1]));
         int eb = (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, (int64_t)g->num_sms * 8));
         if (m > 0) {
-            k_check_indices<<<eb, 256, 0, s>>>(g->csr_idx, m, n, err + 2);
-            if (g->csc_idx != g->csr_idx) k_check_indices<<<eb, 256, 0, s>>>(g->csc_idx, m, n, err + 3);
+            GP_LAUNCH("check_indices", s, (k_check_indices<<<eb, 256, 0, s>>>(g->csr_idx, m, n, err + 2)));
+            if (g->csc_idx != g->csr_idx)
+                GP_LAUNCH("check_indices", s, (k_check_indices<<<eb, 256, 0, s>>>(g->csc_idx, m, n, err + 3)));
         }
         e = cudaMemcpyAsync(herr, err, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -682,11 +685,11 @@ int gp_graph_upload(gp_graph **out, int64_t n, int64_t m, const int64_t *csr_off
         cudaError_t e = cudaMemsetAsync(fp, 0, 2 * sizeof(unsigned long long), s);
         int blocks = grid_blocks(g, 256);
         if (e == cudaSuccess) {
-            k_edge_fingerprint<<<blocks, 256, 0, s>>>(g->csr_off, g->csr_idx, g->csr_w, n, 0, 0, fp);
+            GP_LAUNCH("edge_fingerprint", s, (k_edge_fingerprint<<<blocks, 256, 0, s>>>(g->csr_off, g->csr_idx, g->csr_w, n, 0, 0, fp)));
             if (g->csc_off != g->csr_off)
-                k_edge_fingerprint<<<blocks, 256, 0, s>>>(g->csc_off, g->csc_idx, g->csc_w, n, 1, 0, fp + 1);
+                GP_LAUNCH("edge_fingerprint", s, (k_edge_fingerprint<<<blocks, 256, 0, s>>>(g->csc_off, g->csc_idx, g->csc_w, n, 1, 0, fp + 1)));
             else  // symmetric: the reversed edge multiset must equal the edge multiset
-                k_edge_fingerprint<<<blocks, 256, 0, s>>>(g->csr_off, g->csr_idx, g->csr_w, n, 0, 1, fp + 1);
+                GP_LAUNCH("edge_fingerprint", s, (k_edge_fingerprint<<<blocks, 256, 0, s>>>(g->csr_off, g->csr_idx, g->csr_w, n, 0, 1, fp + 1)));
             e = cudaMemcpyAsync(hfp, fp, sizeof(hfp), cudaMemcpyDeviceToHost, s);
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -703,8 +706,8 @@ int gp_graph_upload(gp_graph **out, int64_t n, int64_t m, const int64_t *csr_off
         cudaError_t e = cudaMemsetAsync(dst, 0, sizeof(DegStats), s);
         int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)g->num_sms * 8));
         if (e == cudaSuccess) {
-            k_degree_prep<<<blocks, 256, 0, s>>>(g->csr_off, g->csc_off, g->csr_w, n, g->weighted, g->normalized,
-                                                 g->inv_deg, dst);
+            GP_LAUNCH("degree_prep", s, (k_degree_prep<<<blocks, 256, 0, s>>>(g->csr_off, g->csc_off, g->csr_w, n,
+                                                                             g->weighted, g->normalized, g->inv_deg, dst)));
             e = cudaMemcpyAsync(&hs, dst, sizeof(hs), cudaMemcpyDeviceToHost, s);
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -774,7 +777,8 @@ int gp_graph_set_options(gp_graph *g, const gp_options *opt, void *stream) {
     if (opt->pull_light_max < 0 || opt->push_light_max < 0 || opt->pull_light_max > (1 << 20) ||
         opt->push_light_max > (1 << 20) || opt->chunk_edges < 32 || opt->chunk_edges > (1 << 24) ||
         opt->blocks_per_sm < 1 || opt->blocks_per_sm > 32 || opt->poll_interval < 1 ||
-        !(opt->bfs_alpha > 0.f) || !(opt->bfs_beta > 0.f) || opt->pr_auto_mode < -1 || opt->pr_auto_mode > 1)
+        !(opt->bfs_alpha > 0.f) || !(opt->bfs_beta > 0.f) || opt->pr_auto_mode < -1 || opt->pr_auto_mode > 1 ||
+        (opt->push_fp64_accum != 0 && opt->push_fp64_accum != 1))
         return set_error(GP_ERR_INVALID, "gp_graph_set_options: option out of range");
     cudaStream_t s = (cudaStream_t)stream;
     const gp_options old = g->opt;

@@ -84,7 +84,26 @@ def test_rmat14_to_tolerance(gp, mode):
     assert st["converged"] and st["residual"] < 1e-7
     O = oracle.OracleGraph.from_graph(g)
     _, k, r, conv = O.pagerank(oracle.PULL, 0.85, iters=300, tol=1e-7)
-    assert abs(k - st["iters_done"]) <= 1
+    if mode == 1:  # deterministic gather: the sweep count agrees with the exact iteration
+        assert abs(k - st["iters_done"]) <= 1
+    else:  # atomics reorder the FP32 sums every sweep: the residual has a rounding floor near tol
+        assert st["iters_done"] >= k - 1
+
+
+@pytest.mark.parametrize("acc64", [0, 1])
+@pytest.mark.parametrize("gi", [2, 8, 10])
+def test_push_accumulators(gp, acc64, gi):
+    """Both push accumulators (FP32 atomics as in the paper, FP64 atomics) match the oracle."""
+    run_and_check(gp, ZOO[gi](), gp.PUSH, iters=15, opts={"push_fp64_accum": acc64})
+
+
+def test_push_fp64_converges_like_pull(gp):
+    """With FP64 accumulation the push residual follows the exact iteration."""
+    g = gg.rmat(14, 16, seed=1)
+    O = oracle.OracleGraph.from_graph(g)
+    _, k, _, _ = O.pagerank(oracle.PULL, 0.85, iters=300, tol=1e-7)
+    x, st = run_and_check(gp, g, gp.PUSH, iters=300, tol=1e-7, opts={"push_fp64_accum": 1})
+    assert st["converged"] and abs(st["iters_done"] - k) <= 1
 
 
 @pytest.mark.parametrize("T", [31, 32, 33, 64, 65])
