@@ -52,6 +52,9 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--quiet", action="store_true")
+    p.add_argument("--only", choices=["pr_pull", "pr_push", "bfs"], default=None,
+                   help="profiling case: run only this part (fixed --sweeps for PageRank), no contract line")
+    p.add_argument("--sweeps", type=int, default=4)
     return p.parse_args(argv)
 
 
@@ -479,8 +482,40 @@ def run_reference(args, dist: Dist):
             "e2e": {"value": round(v, 5), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_only(args):
+    """A reduced run for profilers: one part of the step on the same kind of
+    graph, --warmup + --steps repetitions, then a short JSON summary."""
+    import torch
+
+    import paper_2010_16012_gb300 as gp
+
+    gp.load()
+    g = make_graph(args.scale)
+    off = torch.from_numpy(g.csr_off).cuda()
+    idx = torch.from_numpy(g.csr_idx).cuda()
+    G = gp.Graph(g.n, off, idx, symmetric=True)
+    out = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    srcs = pick_sources(g, args.sources)
+    res = {}
+    for _ in range(args.warmup + args.steps):
+        if args.only == "bfs":
+            for s in srcs:
+                _, _, st = gp.bfs(G, int(s), gp.AUTO)
+            res = {"levels": st["levels"], "reached": st["reached"]}
+        else:
+            mode = gp.PULL if args.only == "pr_pull" else gp.PUSH
+            _, st = gp.pagerank(G, mode, 0.85, args.sweeps, 0.0, out=out)
+            res = {"sweeps": st["iters_done"]}
+    torch.cuda.synchronize()
+    G.free()
+    print(json.dumps({"profile_case": args.only, "scale": args.scale, "n": g.n, "m": g.m, **res}), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.only:
+        return run_only(args)
     if args.impl == "reference":
         dist = Dist(backend="gloo") if int(os.environ.get("WORLD_SIZE", "1")) > 1 else Dist()
         out = run_reference(args, dist)
