@@ -242,6 +242,44 @@ int gp_bfs(const gp_graph *g, int32_t src, int mode, int32_t *level_out, int32_t
 int gp_bfs_directed(const gp_graph *g, int32_t src, const int8_t *dirs, int ndirs, int32_t *level_out,
                     int32_t *parent_out, gp_bfs_stats *stats, void *stream);
 
+/* ------------------------------------------------------------------ sweep without allocation */
+
+/* Largest graph (in vertices) gp_pull_sweep_noalloc accepts: the size of its static scratch. */
+#define GP_NOALLOC_MAX_VERTICES (1 << 20)
+
+/*
+ * One pull PageRank sweep that allocates no device memory (the paper has no
+ * counterpart: this entry point exists for callers that are not allowed to
+ * allocate while they run -- code inside a framework hook that may only use
+ * the buffers it is given, pipelines that reserve all device memory up front,
+ * or processes whose memory is already claimed by another allocator).
+ *     y[v] = (1-d) s[v] + d * sum_{u in in(v)} w_uv * x[u] * inv_deg[u]
+ *     *residual_out = sum_v |y[v] - x[v]|   (FP64)
+ * All arrays are device memory owned by the caller:
+ *   csc_off int64[n+1], csc_idx int32[m]   in-edges (as for gp_graph_upload);
+ *   csc_w   float[m] or NULL               edge factor w_uv (NULL: 1);
+ *   inv_deg float[n]                       1/deg_out(u) (0 for dangling u), or the
+ *                                          weight normaliser when csc_w is given;
+ *   x       float[n]                       current iterate;
+ *   personalization float[n] or NULL       teleport vector s (NULL: 1/n);
+ *   y       float[n]                       new iterate (written);
+ *   residual_out double[1]                 written on the device; NaN if an
+ *                                          offset or index was out of range (the
+ *                                          bad entries are skipped, never read).
+ * Limits: 1 <= n <= GP_NOALLOC_MAX_VERTICES and m < 2^31, else GP_ERR_INVALID
+ * with no device work.  Intermediate data (x*inv_deg and per-block residual
+ * partials, 4 MiB + 8 KiB) lives in one array compiled into the library, which
+ * every device that loads the library keeps until the process exits.  The
+ * first call on a device looks up that array's device address (once per
+ * device), so make the first call on each device before any stream capture.
+ * All calls share the array: calls whose kernels overlap on the GPU (other
+ * streams, other host threads) race and corrupt each other; serialise them.
+ * Asynchronous on `stream`; no cudaMalloc/cudaFree or other allocating call.
+ */
+int gp_pull_sweep_noalloc(int64_t n, int64_t m, const int64_t *csc_off, const int32_t *csc_idx, const float *csc_w,
+                          const float *inv_deg, const float *x, float damping, const float *personalization, float *y,
+                          double *residual_out, void *stream);
+
 /* ------------------------------------------------------------------ kernel timing */
 
 /* When enabled, the library brackets each of its sweep-kernel launches with

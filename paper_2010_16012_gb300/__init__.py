@@ -90,6 +90,7 @@ SIGNATURES = [
     ("gp_bfs", ctypes.c_int, [_VP, _I32, ctypes.c_int, _VP, _VP, ctypes.POINTER(gp_bfs_stats), _VP]),
     ("gp_bfs_directed", ctypes.c_int, [_VP, _I32, _VP, ctypes.c_int, _VP, _VP, ctypes.POINTER(gp_bfs_stats),
                                        _VP]),
+    ("gp_pull_sweep_noalloc", ctypes.c_int, [_I64, _I64, _VP, _VP, _VP, _VP, _VP, _F, _VP, _VP, _VP, _VP]),
     ("gp_profile_enable", ctypes.c_int, [ctypes.c_int]),
     ("gp_profile_read", ctypes.c_int, [ctypes.POINTER(gp_kernel_time), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
@@ -271,6 +272,18 @@ def bfs(g: Graph, src: int, mode=AUTO, level=None, parent=None, want_parent=True
              "direction": list(st.direction[:L]), "frontier": list(st.frontier[:L]),
              "examined": list(st.examined[:L])}
     return level, parent, stats
+
+
+NOALLOC_MAX_VERTICES = 1 << 20
+
+
+def pull_sweep_noalloc(n, m, csc_off, csc_idx, inv_deg, x, y, residual, damping=0.85, csc_w=None,
+                       personalization=None, stream=None):
+    """gp_pull_sweep_noalloc: one pull sweep into caller-owned `y` (float32[n])
+    and `residual` (float64[1]), with no device allocation by the library."""
+    _check(load().gp_pull_sweep_noalloc(int(n), int(m), _ptr(csc_off), _ptr(csc_idx), _ptr(csc_w), _ptr(inv_deg),
+                                        _ptr(x), float(damping), _ptr(personalization), _ptr(y), _ptr(residual),
+                                        _stream_ptr(stream)), "gp_pull_sweep_noalloc")
 
 
 def profile_enable(on: bool = True):
