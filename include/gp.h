@@ -156,7 +156,9 @@ typedef struct gp_options {
     float bfs_beta;           /* bottom-up -> top-down when n_f < n / beta (frontier shrinking) */
     int32_t push_fp64_accum;  /* push PageRank: 1 = accumulate the scattered updates with FP64
                                  atomics (default; ranks stay FP32), 0 = FP32 atomics */
-    int32_t reserved[7];
+    int32_t pull_hot_slots;   /* pull PageRank: contributions of this many highest out-degree
+                                 vertices are served from shared memory (0 = off, <= 49152) */
+    int32_t reserved[6];
 } gp_options;
 
 /* Fill *opt with the built-in defaults. */

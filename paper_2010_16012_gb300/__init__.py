@@ -41,7 +41,8 @@ class gp_options(ctypes.Structure):
                 ("chunk_edges", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("poll_interval", ctypes.c_int32), ("pr_auto_mode", ctypes.c_int32),
                 ("bfs_alpha", ctypes.c_float), ("bfs_beta", ctypes.c_float),
-                ("push_fp64_accum", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("push_fp64_accum", ctypes.c_int32), ("pull_hot_slots", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class gp_graph_info(ctypes.Structure):

@@ -114,6 +114,19 @@ struct BigBins {
     Arena mem;
 };
 
+// Contributions of the H most gathered vertices (largest out-degree), kept in
+// shared memory by the pull kernels: enc_idx is the CSC index array with each
+// such vertex u replaced by HOT_BIT | slot(u); c_hot[slot] mirrors c[u].
+constexpr uint32_t HOT_BIT = 0x80000000u;
+struct HotSet {
+    int32_t slots = 0;  // requested H (0 = off)
+    int64_t nhot = 0;
+    int32_t *hot_id = nullptr;   // [nhot] vertex of each slot
+    float *c_hot = nullptr;      // [nhot]
+    int32_t *enc_idx = nullptr;  // [m]
+    Arena mem;
+};
+
 // Cached PageRank workspace (sized for the graph; reused across calls).
 struct PrWork {
     bool ready = false;
@@ -158,6 +171,7 @@ struct gp_graph {
     gp_options opt;
     gp::BigBins pull_bins;  // by in-degree (CSC)
     gp::BigBins push_bins;  // by out-degree (CSR)
+    gp::HotSet pull_hot;    // shared-memory contribution cache of the pull sweep
     gp::PrWork pr;
     gp::BfsWork bfs;
     gp::Arena mem;          // copies of the arrays and degree data
@@ -168,6 +182,9 @@ namespace gp {
 
 int build_bins(gp_graph *g, BigBins &b, const int64_t *off, int32_t light_max, int32_t chunk_edges,
                cudaStream_t s);
+int build_pull_hot(gp_graph *g, int32_t slots, cudaStream_t s);
+int select_by_degree(const int64_t *off, int64_t n, int64_t lo, int64_t hi, Arena &mem, int32_t *&list,
+                     int64_t &count, int64_t cap, int32_t *rank, cudaStream_t s);
 int grid_blocks(const gp_graph *g, int threads_per_block);
 
 // ------------------------------------------------------------------ device primitives

@@ -69,6 +69,8 @@ struct PrArgs {
     double *partials;
     float *chunk_part;
     double *acc64;  // FP64 push accumulator (or nullptr)
+    const float *c_hot;  // hot contributions (pull, HOT kernels)
+    int64_t nhot;
     PrStatus *status;
     int32_t split_blocks;  // pull: light-tile blocks; push: big-chunk blocks
 };
@@ -132,9 +134,32 @@ __global__ void k_pr_finish(PrArgs a) { pr_gate(a, a.k); }
 
 // ------------------------------------------------------------------ pull
 
-template <bool W>
-__global__ void __launch_bounds__(256) k_pull_big(PrArgs a) {
+// Shared-memory copy of the hot contributions (see HotSet): loaded once per
+// block, then every gather of a hot vertex is a shared-memory read.
+template <bool HOT>
+__device__ __forceinline__ void load_hot(const PrArgs &a, float *sh) {
+    if (!HOT) return;
+    const int64_t nh = a.nhot;
+    const float4 *src = reinterpret_cast<const float4 *>(a.c_hot);
+    float4 *dst = reinterpret_cast<float4 *>(sh);
+    for (int64_t i = threadIdx.x; i < nh / 4; i += blockDim.x) dst[i] = __ldg(src + i);
+    for (int64_t i = (nh & ~int64_t(3)) + threadIdx.x; i < nh; i += blockDim.x) sh[i] = __ldg(a.c_hot + i);
+    __syncthreads();
+}
+
+template <bool HOT>
+__device__ __forceinline__ float gather_c(const float *__restrict__ c, const float *sh, int32_t u) {
+    if (HOT && u < 0) return sh[u & 0x7fffffff];
+    return __ldg(c + u);
+}
+
+constexpr int BIG_UNROLL = 8;
+
+template <bool W, bool HOT>
+__global__ void __launch_bounds__(1024) k_pull_big(PrArgs a) {
+    extern __shared__ float sh_hot[];
     if (pr_gate(a, a.k)) return;
+    load_hot<HOT>(a, sh_hot);
     const int lane = lane_id();
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -146,36 +171,42 @@ __global__ void __launch_bounds__(256) k_pull_big(PrArgs a) {
         const int32_t *ip = idx + ch.beg;
         const float *wp = W ? w + ch.beg : nullptr;
         float acc = 0.f;
-        int i = lane;
-        for (; i + 96 < ch.len; i += 128) {
-            const int u0 = __ldg(ip + i), u1 = __ldg(ip + i + 32), u2 = __ldg(ip + i + 64), u3 = __ldg(ip + i + 96);
-            float f0 = __ldg(c + u0), f1 = __ldg(c + u1), f2 = __ldg(c + u2), f3 = __ldg(c + u3);
-            if (W) {
-                f0 *= __ldg(wp + i);
-                f1 *= __ldg(wp + i + 32);
-                f2 *= __ldg(wp + i + 64);
-                f3 *= __ldg(wp + i + 96);
+        for (int i0 = 0; i0 < ch.len; i0 += 32 * BIG_UNROLL) {
+            // all index loads of the window first, then all gathers: BIG_UNROLL in flight per lane
+            int32_t u[BIG_UNROLL];
+#pragma unroll
+            for (int q = 0; q < BIG_UNROLL; ++q) {
+                const int i = i0 + q * 32 + lane;
+                u[q] = i < ch.len ? __ldg(ip + i) : 0;
             }
-            acc += (f0 + f1) + (f2 + f3);
-        }
-        for (; i < ch.len; i += 32) {
-            float f = __ldg(c + __ldg(ip + i));
-            if (W) f *= __ldg(wp + i);
-            acc += f;
+            float f[BIG_UNROLL];
+#pragma unroll
+            for (int q = 0; q < BIG_UNROLL; ++q) {
+                const int i = i0 + q * 32 + lane;
+                f[q] = 0.f;
+                if (i < ch.len) {
+                    f[q] = gather_c<HOT>(c, sh_hot, u[q]);
+                    if (W) f[q] *= __ldg(wp + i);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < BIG_UNROLL; ++q) acc += f[q];
         }
         acc = warp_sum(acc);
         if (lane == 0) a.chunk_part[j] = acc;
     }
 }
 
-template <bool W>
-__global__ void __launch_bounds__(256) k_pull_light(PrArgs a) {
+template <bool W, bool HOT>
+__global__ void __launch_bounds__(512) k_pull_light(PrArgs a) {
+    extern __shared__ float sh_hot[];
     __shared__ double sm[32];
     if (((volatile PrStatus *)a.status)->done) return;
     const int lane = lane_id();
     double res = 0.0;
     const int64_t n = a.n;
     if ((int)blockIdx.x < a.split_blocks) {
+        load_hot<HOT>(a, sh_hot);
         const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
         const int64_t nwarps = ((int64_t)a.split_blocks * blockDim.x) >> 5;
         const int64_t ntiles = (n + 31) >> 5;
@@ -211,7 +242,7 @@ __global__ void __launch_bounds__(256) k_pull_light(PrArgs a) {
                 float val = 0.f;
                 if (eid < E) {
                     const int64_t pos = kb + (eid - kex);
-                    val = __ldg(c + __ldg(idx + pos));
+                    val = gather_c<HOT>(c, sh_hot, __ldg(idx + pos));
                     if (W) val *= __ldg(wv + pos);
                 }
                 // segmented inclusive scan over the lanes owned by the same vertex
@@ -248,6 +279,12 @@ __global__ void __launch_bounds__(256) k_pull_light(PrArgs a) {
     }
     res = block_sum(res, sm);
     if (threadIdx.x == 0) a.partials[blockIdx.x] = res;
+}
+
+// c_hot[slot] = c[hot_id[slot]] for the sweep that reads c next.
+__global__ void k_hot_gather(const int32_t *hot_id, int64_t nhot, const float *c, float *c_hot) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nhot; i += stride) c_hot[i] = c[hot_id[i]];
 }
 
 // ------------------------------------------------------------------ push
@@ -381,13 +418,22 @@ void release_pr_work(gp_graph *g, cudaStream_t s) {
     g->pr = PrWork();
 }
 
+// Resident blocks per SM of `kernel` (raising its dynamic shared-memory limit first).
+static int occupancy(const void *kernel, int threads, size_t smem, int &blocks) {
+    if (smem > 48 * 1024)
+        GP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, threads, smem));
+    if (blocks < 1) return set_error(GP_ERR_UNSUPPORTED, "kernel does not fit on an SM (%zu B shared memory)", smem);
+    return GP_OK;
+}
+
 static int ensure_pr_work(gp_graph *g, cudaStream_t s) {
     PrWork &w = g->pr;
     if (w.ready) return GP_OK;
     const size_t n = (size_t)std::max<int64_t>(g->n, 1);
-    const int gb = grid_blocks(g, 256);
     const int64_t epi = (g->pull_bins.nbig + 255) / 256;
-    w.max_blocks = (int)(gb + epi + 2 * gb + 64);
+    // covers any grid: at most 32 resident blocks per SM, plus the epilogue blocks
+    w.max_blocks = (int)(std::max(g->num_sms * 32, grid_blocks(g, 256)) + epi + 64);
     GP_TRY(w.mem.alloc(w.r1, n, s));
     GP_TRY(w.mem.alloc(w.c0, n, s));
     GP_TRY(w.mem.alloc(w.c1, n, s));
@@ -490,12 +536,37 @@ extern "C" int gp_pagerank(const gp_graph *gc, int mode, float damping, int iter
 
     const int gb = grid_blocks(g, 256);
     const int64_t ntiles = (n + 31) / 32;
+    // pull: hot-contribution cache in shared memory (built once per graph)
+    bool hot = false;
+    int tbp = 256, tbl = 256;  // threads per block of pull_big / pull_light
+    size_t smem = 0;
+    if (!push) {
+        if (g->pull_hot.slots != g->opt.pull_hot_slots) GP_TRY(build_pull_hot(g, g->opt.pull_hot_slots, s));
+        hot = g->pull_hot.nhot > 0;
+        if (hot) {
+            tbp = 1024;
+            tbl = 512;
+            smem = (size_t)((g->pull_hot.nhot + 3) & ~int64_t(3)) * sizeof(float);
+            a.c_hot = g->pull_hot.c_hot;
+            a.nhot = g->pull_hot.nhot;
+            a.idx = g->pull_hot.enc_idx;
+        }
+    }
     // grids
     int g1, g2, split;
     if (!push) {
-        g1 = (int)std::max<int64_t>(1, std::min<int64_t>(gb, (bins.nchunks + 7) / 8));
-        split = (int)std::max<int64_t>(1, std::min<int64_t>(gb, (ntiles + 7) / 8));
-        g2 = split + (int)((bins.nbig + 255) / 256);
+        int ob = 0, ol = 0;
+        if (W) {
+            GP_TRY(occupancy(hot ? (const void *)k_pull_big<true, true> : (const void *)k_pull_big<true, false>, tbp, smem, ob));
+            GP_TRY(occupancy(hot ? (const void *)k_pull_light<true, true> : (const void *)k_pull_light<true, false>, tbl, smem, ol));
+        } else {
+            GP_TRY(occupancy(hot ? (const void *)k_pull_big<false, true> : (const void *)k_pull_big<false, false>, tbp, smem, ob));
+            GP_TRY(occupancy(hot ? (const void *)k_pull_light<false, true> : (const void *)k_pull_light<false, false>, tbl, smem, ol));
+        }
+        const int wpb = tbp / 32, wpl = tbl / 32;
+        g1 = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ob * g->num_sms, (bins.nchunks + wpb - 1) / wpb));
+        split = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ol * g->num_sms, (ntiles + wpl - 1) / wpl));
+        g2 = split + (int)((bins.nbig + tbl - 1) / tbl);
     } else {
         split = (int)std::min<int64_t>(gb, (bins.nchunks + 7) / 8);
         g1 = split + (int)std::max<int64_t>(1, std::min<int64_t>(gb, (ntiles + 7) / 8));
@@ -513,6 +584,13 @@ extern "C" int gp_pagerank(const gp_graph *gc, int mode, float damping, int iter
                                                           a.acc64, S,
                                                           a.one_minus_d, a.base_uniform, status)));
     GP_TRY(check_launch("pr_init"));
+    auto enqueue_hot_gather = [&](const float *c_src) -> int {
+        const int hb = (int)std::max<int64_t>(1, std::min<int64_t>((g->pull_hot.nhot + 255) / 256, 4096));
+        GP_LAUNCH("hot_gather", s, (k_hot_gather<<<hb, 256, 0, s>>>(g->pull_hot.hot_id, g->pull_hot.nhot, c_src,
+                                                                    g->pull_hot.c_hot)));
+        return check_launch("hot_gather");
+    };
+    if (hot) GP_TRY(enqueue_hot_gather(C[0]));
 
     auto enqueue_sweep = [&](int k) -> int {
         PrArgs b = a;
@@ -522,13 +600,20 @@ extern "C" int gp_pagerank(const gp_graph *gc, int mode, float damping, int iter
         if (!push) {
             b.c = C[(k - 1) & 1];
             b.c_next = C[k & 1];
-            if (W) {
-                GP_LAUNCH("pull_big", s, (k_pull_big<true><<<g1, 256, 0, s>>>(b)));
-                GP_LAUNCH("pull_light", s, (k_pull_light<true><<<g2, 256, 0, s>>>(b)));
+            if (W && hot) {
+                GP_LAUNCH("pull_big", s, (k_pull_big<true, true><<<g1, tbp, smem, s>>>(b)));
+                GP_LAUNCH("pull_light", s, (k_pull_light<true, true><<<g2, tbl, smem, s>>>(b)));
+            } else if (W) {
+                GP_LAUNCH("pull_big", s, (k_pull_big<true, false><<<g1, tbp, 0, s>>>(b)));
+                GP_LAUNCH("pull_light", s, (k_pull_light<true, false><<<g2, tbl, 0, s>>>(b)));
+            } else if (hot) {
+                GP_LAUNCH("pull_big", s, (k_pull_big<false, true><<<g1, tbp, smem, s>>>(b)));
+                GP_LAUNCH("pull_light", s, (k_pull_light<false, true><<<g2, tbl, smem, s>>>(b)));
             } else {
-                GP_LAUNCH("pull_big", s, (k_pull_big<false><<<g1, 256, 0, s>>>(b)));
-                GP_LAUNCH("pull_light", s, (k_pull_light<false><<<g2, 256, 0, s>>>(b)));
+                GP_LAUNCH("pull_big", s, (k_pull_big<false, false><<<g1, tbp, 0, s>>>(b)));
+                GP_LAUNCH("pull_light", s, (k_pull_light<false, false><<<g2, tbl, 0, s>>>(b)));
             }
+            if (hot) GP_TRY(enqueue_hot_gather(b.c_next));
         } else {
             b.c = C[0];
             b.c_next = C[0];

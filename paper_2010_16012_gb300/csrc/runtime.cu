@@ -336,22 +336,25 @@ __global__ void k_degree_prep(const int64_t *csr_off, const int64_t *csc_off, co
 
 constexpr int BIN_SEG = 2048;  // vertices per block segment in the selection kernels
 
-__global__ void k_count_big(const int64_t *off, int64_t n, int32_t light_max, int64_t *counts) {
+// Vertices v with lo <= off[v+1] - off[v] <= hi, per block segment: count, then
+// write them in ascending order (and rank[v], -1 for the others, if given).
+__global__ void k_count_deg(const int64_t *off, int64_t n, int64_t lo, int64_t hi, int64_t *counts) {
     __shared__ int64_t sm[33];
     const int64_t base = (int64_t)blockIdx.x * BIN_SEG;
     int64_t c = 0;
     for (int i = threadIdx.x; i < BIN_SEG; i += blockDim.x) {
         int64_t v = base + i;
-        if (v < n && off[v + 1] - off[v] > light_max) ++c;
+        if (v < n) {
+            const int64_t d = off[v + 1] - off[v];
+            c += (d >= lo && d <= hi);
+        }
     }
     c = block_sum(c, sm);
     if (threadIdx.x == 0) counts[blockIdx.x] = c;
 }
 
-// Writes the big vertices of each segment in ascending order at the segment's
-// offset, and rank[v] (position in the big list, -1 for light vertices).
-__global__ void k_write_big(const int64_t *off, int64_t n, int32_t light_max, const int64_t *seg_off,
-                            int32_t *big, int32_t *rank) {
+__global__ void k_write_deg(const int64_t *off, int64_t n, int64_t lo, int64_t hi, const int64_t *seg_off, int64_t cap,
+                            int32_t *list, int32_t *rank) {
     __shared__ int32_t warp_cnt[32];
     __shared__ int64_t running;
     const int64_t base = (int64_t)blockIdx.x * BIN_SEG;
@@ -360,15 +363,19 @@ __global__ void k_write_big(const int64_t *off, int64_t n, int32_t light_max, co
     __syncthreads();
     for (int i0 = 0; i0 < BIN_SEG; i0 += blockDim.x) {
         int64_t v = base + i0 + threadIdx.x;
-        bool isbig = v < n && off[v + 1] - off[v] > light_max;
-        unsigned bal = __ballot_sync(FULL, isbig);
+        bool sel = false;
+        if (v < n) {
+            const int64_t d = off[v + 1] - off[v];
+            sel = d >= lo && d <= hi;
+        }
+        unsigned bal = __ballot_sync(FULL, sel);
         if (lane == 0) warp_cnt[w] = __popc(bal);
         __syncthreads();
         int64_t pos = running;
         for (int k = 0; k < w; ++k) pos += warp_cnt[k];
         pos += __popc(bal & ((1u << lane) - 1u));
-        if (v < n) rank[v] = isbig ? (int32_t)pos : -1;
-        if (isbig) big[pos] = (int32_t)v;
+        if (rank && v < n) rank[v] = sel ? (int32_t)pos : -1;
+        if (sel && pos < cap) list[pos] = (int32_t)v;
         __syncthreads();
         if (threadIdx.x == 0) {
             int64_t t = 0;
@@ -377,6 +384,37 @@ __global__ void k_write_big(const int64_t *off, int64_t n, int32_t light_max, co
         }
         __syncthreads();
     }
+}
+
+int select_by_degree(const int64_t *off, int64_t n, int64_t lo, int64_t hi, Arena &mem, int32_t *&list,
+                     int64_t &count, int64_t cap, int32_t *rank, cudaStream_t s) {
+    count = 0;
+    list = nullptr;
+    if (n == 0) return GP_OK;
+    const int64_t nseg = (n + BIN_SEG - 1) / BIN_SEG;
+    Arena tmp;
+    int64_t *segc;
+    int st = tmp.alloc(segc, nseg + 1, s);
+    if (st == GP_OK) {
+        GP_LAUNCH("count_deg", s, (k_count_deg<<<(unsigned)nseg, 256, 0, s>>>(off, n, lo, hi, segc)));
+        st = check_launch("count_deg");
+    }
+    if (st == GP_OK) st = exclusive_scan(segc, segc, nseg, tmp, s);
+    int64_t total = 0;
+    if (st == GP_OK) {
+        cudaError_t e = cudaMemcpyAsync(&total, segc + nseg, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = set_error(GP_ERR_CUDA, "selection count read-back: %s", cudaGetErrorString(e));
+    }
+    const int64_t keep = std::min(total, cap);
+    if (st == GP_OK) st = mem.alloc(list, (size_t)std::max<int64_t>(keep, 1), s);
+    if (st == GP_OK) {
+        GP_LAUNCH("write_deg", s, (k_write_deg<<<(unsigned)nseg, 256, 0, s>>>(off, n, lo, hi, segc, keep, list, rank)));
+        st = check_launch("write_deg");
+    }
+    tmp.release(s);
+    count = keep;
+    return st;
 }
 
 __global__ void k_chunk_counts(const int32_t *big, int64_t nbig, const int64_t *off, int32_t C, int64_t *cnt) {
@@ -405,6 +443,109 @@ __global__ void k_fill_chunks(const int32_t *big, int64_t nbig, const int64_t *o
     }
 }
 
+constexpr int HOT_HIST = 65536;  // out-degree histogram buckets (the last one collects all larger degrees)
+
+__global__ void k_deg_hist(const int64_t *off, int64_t n, unsigned long long *hist) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int64_t d = off[v + 1] - off[v];
+        if (d > 0) atomicAdd(hist + (d < HOT_HIST - 1 ? d : HOT_HIST - 1), 1ull);
+    }
+}
+
+__global__ void k_fill_slots(const int32_t *hot_id, int64_t nhot, int32_t *slot) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nhot; i += stride) slot[hot_id[i]] = (int32_t)i;
+}
+
+__global__ void k_encode_hot(const int32_t *idx, int64_t m, const int32_t *slot, int32_t *enc) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const int32_t u = idx[e];
+        const int32_t sl = slot[u];
+        enc[e] = sl >= 0 ? (int32_t)(HOT_BIT | (uint32_t)sl) : u;
+    }
+}
+
+// Picks the `slots` vertices with the largest out-degree (ties: lowest ids),
+// builds the encoded copy of the CSC indices and the slot -> vertex table.
+int build_pull_hot(gp_graph *g, int32_t slots, cudaStream_t s) {
+    HotSet &h = g->pull_hot;
+    h.mem.release(s);
+    h = HotSet();
+    h.slots = slots;
+    const int64_t n = g->n, m = g->m;
+    if (slots <= 0 || n == 0 || m == 0) return GP_OK;
+    Arena tmp;
+    unsigned long long *hist = nullptr;
+    int st = tmp.alloc(hist, HOT_HIST, s);
+    std::vector<unsigned long long> hh(HOT_HIST);
+    if (st == GP_OK) {
+        cudaError_t e = cudaMemsetAsync(hist, 0, HOT_HIST * sizeof(unsigned long long), s);
+        int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)g->num_sms * 8));
+        if (e == cudaSuccess) {
+            GP_LAUNCH("deg_hist", s, (k_deg_hist<<<blocks, 256, 0, s>>>(g->csr_off, n, hist)));
+            e = cudaMemcpyAsync(hh.data(), hist, HOT_HIST * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = set_error(GP_ERR_CUDA, "hot-set histogram: %s", cudaGetErrorString(e));
+    }
+    // bucket B: every vertex above B is taken, then the lowest ids of bucket B until `slots`
+    int64_t above = 0;
+    int B = 0;
+    if (st == GP_OK) {
+        for (int b = HOT_HIST - 1; b >= 1; --b) {
+            if (above + (int64_t)hh[b] > slots) {
+                B = b;
+                break;
+            }
+            above += (int64_t)hh[b];
+        }
+    }
+    int32_t *list1 = nullptr, *list2 = nullptr;
+    int64_t c1 = 0, c2 = 0;
+    const int64_t top_lo = B > 0 ? (int64_t)B + 1 : 1;
+    if (st == GP_OK && top_lo <= HOT_HIST - 1)
+        st = select_by_degree(g->csr_off, n, top_lo, INT64_MAX, tmp, list1, c1, slots, nullptr, s);
+    if (st == GP_OK && B > 0) {
+        const int64_t hi = B == HOT_HIST - 1 ? INT64_MAX : (int64_t)B;
+        st = select_by_degree(g->csr_off, n, B, hi, tmp, list2, c2, slots - c1, nullptr, s);
+    }
+    const int64_t nhot = c1 + c2;
+    int32_t *slot = nullptr;
+    if (st == GP_OK) st = h.mem.alloc(h.hot_id, (size_t)std::max<int64_t>(nhot, 1), s);
+    if (st == GP_OK) st = h.mem.alloc(h.c_hot, (size_t)std::max<int64_t>(nhot, 4), s);
+    if (st == GP_OK) st = h.mem.alloc(h.enc_idx, (size_t)m, s);
+    if (st == GP_OK) st = tmp.alloc(slot, (size_t)n, s);
+    if (st == GP_OK) {
+        cudaError_t e = cudaSuccess;
+        if (c1) e = cudaMemcpyAsync(h.hot_id, list1, c1 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess && c2)
+            e = cudaMemcpyAsync(h.hot_id + c1, list2, c2 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(slot, 0xff, (size_t)n * sizeof(int32_t), s);
+        if (e != cudaSuccess) st = set_error(GP_ERR_CUDA, "hot-set copy: %s", cudaGetErrorString(e));
+    }
+    if (st == GP_OK && nhot > 0) {
+        int b1 = (int)std::max<int64_t>(1, std::min<int64_t>((nhot + 255) / 256, 65535));
+        GP_LAUNCH("fill_slots", s, (k_fill_slots<<<b1, 256, 0, s>>>(h.hot_id, nhot, slot)));
+        int b2 = (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, (int64_t)g->num_sms * 8));
+        GP_LAUNCH("encode_hot", s, (k_encode_hot<<<b2, 256, 0, s>>>(g->csc_idx, m, slot, h.enc_idx)));
+        st = check_launch("encode_hot");
+    }
+    if (st == GP_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = set_error(GP_ERR_CUDA, "hot-set build: %s", cudaGetErrorString(e));
+    }
+    tmp.release(s);
+    if (st != GP_OK) {
+        h.mem.release(s);
+        h = HotSet();
+        return st;
+    }
+    h.nhot = nhot;
+    return GP_OK;
+}
+
 int grid_blocks(const gp_graph *g, int threads_per_block) {
     int per_sm = std::max(1, g->opt.blocks_per_sm * 256 / std::max(32, threads_per_block));
     return std::max(1, g->num_sms * per_sm);
@@ -425,26 +566,10 @@ int build_bins(gp_graph *g, BigBins &b, const int64_t *off, int32_t light_max, i
     GP_TRY(b.mem.alloc(rank, (size_t)std::max<int64_t>(n, 1), s));
     b.rank = rank;
     if (n == 0) return GP_OK;
-    const int64_t nseg = (n + BIN_SEG - 1) / BIN_SEG;
-    Arena tmp;
-    int64_t *segc;
-    int st = tmp.alloc(segc, nseg + 1, s);
-    if (st != GP_OK) return st;
-    GP_LAUNCH("count_big", s, (k_count_big<<<(unsigned)nseg, 256, 0, s>>>(off, n, light_max, segc)));
-    st = check_launch("count_big");
-    if (st == GP_OK) st = exclusive_scan(segc, segc, nseg, tmp, s);
     int64_t nbig = 0;
-    if (st == GP_OK) {
-        cudaError_t e = cudaMemcpyAsync(&nbig, segc + nseg, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) st = set_error(GP_ERR_CUDA, "bin count read-back: %s", cudaGetErrorString(e));
-    }
-    if (st == GP_OK) st = b.mem.alloc(b.big, (size_t)std::max<int64_t>(nbig, 1), s);
-    if (st == GP_OK) {
-        GP_LAUNCH("write_big", s, (k_write_big<<<(unsigned)nseg, 256, 0, s>>>(off, n, light_max, segc, b.big, rank)));
-        st = check_launch("write_big");
-    }
-    if (st == GP_OK) st = b.mem.alloc(b.cstart, (size_t)nbig + 1, s);
+    GP_TRY(select_by_degree(off, n, (int64_t)light_max + 1, INT64_MAX, b.mem, b.big, nbig, INT64_MAX, rank, s));
+    Arena tmp;
+    int st = b.mem.alloc(b.cstart, (size_t)nbig + 1, s);
     int64_t nchunks = 0;
     if (st == GP_OK && nbig > 0) {
         int blocks = (int)std::min<int64_t>((nbig + 255) / 256, 65535);
@@ -534,6 +659,7 @@ int gp_options_default(gp_options *opt) {
     opt->bfs_alpha = 14.0f;
     opt->bfs_beta = 24.0f;
     opt->push_fp64_accum = 1;
+    opt->pull_hot_slots = 16384;
     return GP_OK;
 }
 
@@ -580,6 +706,7 @@ int gp_profile_read(gp_kernel_time *out, int cap, int *count, int reset) {
 static int upload_fail(gp_graph *g, cudaStream_t s, int st) {
     g->pull_bins.mem.release(s);
     g->push_bins.mem.release(s);
+    g->pull_hot.mem.release(s);
     g->mem.release(s);
     delete g;
     return st;
@@ -736,6 +863,7 @@ int gp_graph_free(gp_graph *g) {
     release_bfs_work(g, s);
     g->pull_bins.mem.release(s);
     g->push_bins.mem.release(s);
+    g->pull_hot.mem.release(s);
     g->mem.release(s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (dev != g->device && dev >= 0) cudaSetDevice(dev);
@@ -778,7 +906,8 @@ int gp_graph_set_options(gp_graph *g, const gp_options *opt, void *stream) {
         opt->push_light_max > (1 << 20) || opt->chunk_edges < 32 || opt->chunk_edges > (1 << 24) ||
         opt->blocks_per_sm < 1 || opt->blocks_per_sm > 32 || opt->poll_interval < 1 ||
         !(opt->bfs_alpha > 0.f) || !(opt->bfs_beta > 0.f) || opt->pr_auto_mode < -1 || opt->pr_auto_mode > 1 ||
-        (opt->push_fp64_accum != 0 && opt->push_fp64_accum != 1))
+        (opt->push_fp64_accum != 0 && opt->push_fp64_accum != 1) || opt->pull_hot_slots < 0 ||
+        opt->pull_hot_slots > 49152)
         return set_error(GP_ERR_INVALID, "gp_graph_set_options: option out of range");
     cudaStream_t s = (cudaStream_t)stream;
     const gp_options old = g->opt;

@@ -61,7 +61,9 @@ ZOO = [
     lambda: gg.rmat(11, 16, seed=7),
 ]
 OPTS = [None, {"pull_light_max": 0, "push_light_max": 0}, {"pull_light_max": 2, "push_light_max": 2, "chunk_edges": 32},
-        {"pull_light_max": 1 << 20, "push_light_max": 1 << 20}]
+        {"pull_light_max": 1 << 20, "push_light_max": 1 << 20},
+        {"pull_hot_slots": 0},                            # no shared-memory contribution cache
+        {"pull_hot_slots": 3, "pull_light_max": 4}]       # cache cut inside a degree tie
 
 
 @pytest.mark.parametrize("gi", range(len(ZOO)))
@@ -290,6 +292,13 @@ def test_oom_from_allocator_hook(gp):
     finally:
         assert lib.gp_set_allocator(gp.ALLOC_FN(), gp.FREE_FN(), None) == gp.OK
     gp.Graph.from_graphgen(g).free()
+
+
+@pytest.mark.parametrize("slots", [0, 1, 7, 100, 4096, 49152])
+def test_hot_slot_counts(gp, slots):
+    """Any number of cached hot contributions gives the same iterate."""
+    g = gg.rmat(12, 16, seed=13, symmetrize=False)
+    run_and_check(gp, g, gp.PULL, iters=12, opts={"pull_hot_slots": slots})
 
 
 def test_graph_info(gp):
