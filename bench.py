@@ -55,6 +55,8 @@ def parse_args(argv=None):
     p.add_argument("--only", choices=["pr_pull", "pr_push", "bfs"], default=None,
                    help="profiling case: run only this part (fixed --sweeps for PageRank), no contract line")
     p.add_argument("--sweeps", type=int, default=4)
+    p.add_argument("--opt", action="append", default=[], metavar="KEY=VALUE",
+                   help="gp_options override for the profiling case (repeatable)")
     return p.parse_args(argv)
 
 
@@ -494,10 +496,20 @@ def run_only(args):
     off = torch.from_numpy(g.csr_off).cuda()
     idx = torch.from_numpy(g.csr_idx).cuda()
     G = gp.Graph(g.n, off, idx, symmetric=True)
+    opts = {}
+    for kv in args.opt:
+        k, v = kv.split("=")
+        opts[k] = float(v) if k.startswith("bfs_") else int(v)
+    if opts:
+        G.set_options(**opts)
     out = torch.empty(g.n, dtype=torch.float32, device="cuda")
     srcs = pick_sources(g, args.sources)
     res = {}
-    for _ in range(args.warmup + args.steps):
+    for i in range(args.warmup + args.steps):
+        if i == args.warmup:
+            torch.cuda.synchronize()
+            gp.profile_read(reset=True)
+            gp.profile_enable(True)
         if args.only == "bfs":
             for s in srcs:
                 _, _, st = gp.bfs(G, int(s), gp.AUTO)
@@ -507,8 +519,12 @@ def run_only(args):
             _, st = gp.pagerank(G, mode, 0.85, args.sweeps, 0.0, out=out)
             res = {"sweeps": st["iters_done"]}
     torch.cuda.synchronize()
+    gp.profile_enable(False)
+    kt = gp.profile_read(reset=True)
     G.free()
-    print(json.dumps({"profile_case": args.only, "scale": args.scale, "n": g.n, "m": g.m, **res}), flush=True)
+    per = {k[0]: round(k[2] / max(k[1], 1), 4) for k in kt}
+    print(json.dumps({"profile_case": args.only, "scale": args.scale, "n": g.n, "m": g.m, "opts": opts,
+                      "avg_launch_ms": per, **res}), flush=True)
     return 0
 
 

@@ -155,6 +155,19 @@ __device__ __forceinline__ float gather_c(const float *__restrict__ c, const flo
 
 constexpr int BIG_UNROLL = 8;
 
+// Index arrays are streamed once per sweep: loaded with the evict-first hint so
+// they do not push the gathered contribution vector out of L2.
+#ifndef GP_IDX_STREAMING
+#define GP_IDX_STREAMING 1
+#endif
+__device__ __forceinline__ int32_t ld_idx(const int32_t *p) {
+#if GP_IDX_STREAMING
+    return __ldcs(p);
+#else
+    return __ldg(p);
+#endif
+}
+
 template <bool W, bool HOT>
 __global__ void __launch_bounds__(1024) k_pull_big(PrArgs a) {
     extern __shared__ float sh_hot[];
@@ -177,7 +190,7 @@ __global__ void __launch_bounds__(1024) k_pull_big(PrArgs a) {
 #pragma unroll
             for (int q = 0; q < BIG_UNROLL; ++q) {
                 const int i = i0 + q * 32 + lane;
-                u[q] = i < ch.len ? __ldg(ip + i) : 0;
+                u[q] = i < ch.len ? ld_idx(ip + i) : 0;
             }
             float f[BIG_UNROLL];
 #pragma unroll
@@ -197,8 +210,44 @@ __global__ void __launch_bounds__(1024) k_pull_big(PrArgs a) {
     }
 }
 
+// Owner lane of virtual edge `eid` in a tile: the last lane k with excl[k] <= eid
+// (zero-degree lanes share their successor's excl, so the last one is non-empty).
+__device__ __forceinline__ int tile_owner(int excl, int eid) {
+    int k = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        const int ex = __shfl_sync(FULL, excl, k + s);
+        if (ex <= eid) k += s;
+    }
+    return k;
+}
+
+// Sum of the lanes of `val` that belong to the same vertex in this 32-edge
+// window, delivered to that vertex's own lane (segmented warp scan).
+__device__ __forceinline__ float window_segment_sum(float val, int kex, int base, int deg, int excl, int incl) {
+    const int lane = lane_id();
+    const int head = max(kex, base) - base;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        const float tv = __shfl_up_sync(FULL, val, s);
+        if (lane - s >= head) val += tv;
+    }
+    const bool has = deg > 0 && excl < base + 32 && incl > base;
+    const int tail = has ? min(incl, base + 32) - base - 1 : 0;
+    const float seg = __shfl_sync(FULL, val, tail);
+    return has ? seg : 0.f;
+}
+
+#ifndef GP_LIGHT_WINDOWS
+#define GP_LIGHT_WINDOWS 4
+#endif
+#ifndef GP_LIGHT_MIN_BLOCKS
+#define GP_LIGHT_MIN_BLOCKS 3
+#endif
+constexpr int LW = GP_LIGHT_WINDOWS;  // 32-edge windows in flight per step of the light tiles
+
 template <bool W, bool HOT>
-__global__ void __launch_bounds__(512) k_pull_light(PrArgs a) {
+__global__ void __launch_bounds__(512, GP_LIGHT_MIN_BLOCKS) k_pull_light(PrArgs a) {
     extern __shared__ float sh_hot[];
     __shared__ double sm[32];
     if (((volatile PrStatus *)a.status)->done) return;
@@ -213,12 +262,28 @@ __global__ void __launch_bounds__(512) k_pull_light(PrArgs a) {
         const int32_t *__restrict__ idx = a.idx;
         const float *__restrict__ c = a.c;
         const float *__restrict__ wv = a.w;
-        for (int64_t t = warp; t < ntiles; t += nwarps) {
+        // offsets of the first tile; inside the loop the next tile's are fetched early
+        int64_t t = warp;
+        int64_t nb = 0, ne = 0;
+        if (t < ntiles && t * 32 + lane < n) {
+            nb = a.off[t * 32 + lane];
+            ne = a.off[t * 32 + lane + 1];
+        }
+        for (; t < ntiles; t += nwarps) {
             const int64_t v = t * 32 + lane;
-            int64_t b = 0, e = 0;
+            const int64_t b = nb, e = ne;
+            // per-vertex operands, independent of the edges: issued now
+            float xv = 0.f, inv = 0.f, base_v = 0.f;
             if (v < n) {
-                b = a.off[v];
-                e = a.off[v + 1];
+                xv = a.x[v];
+                inv = a.inv_deg[v];
+                base_v = base_term(a, v);
+            }
+            const int64_t tn = t + nwarps, vn = tn * 32 + lane;
+            nb = ne = 0;
+            if (tn < ntiles && vn < n) {
+                nb = a.off[vn];
+                ne = a.off[vn + 1];
             }
             const int64_t dd = e - b;
             const bool big = dd > a.light_max;
@@ -227,42 +292,38 @@ __global__ void __launch_bounds__(512) k_pull_light(PrArgs a) {
             const int excl = incl - deg;
             const int E = __shfl_sync(FULL, incl, 31);
             float acc = 0.f;
-            for (int base = 0; base < E; base += 32) {
-                const int eid = base + lane;
-                // owner: the last lane k with excl[k] <= eid (zero-degree lanes share
-                // their successor's excl, so the last one is the non-empty owner)
-                int k = 0;
+            for (int base = 0; base < E; base += 32 * LW) {
+                // LW 32-edge windows per step: all index loads, then all gathers, then the sums
+                int kx[LW];
+                int64_t p[LW];
+                int32_t u[LW];
 #pragma unroll
-                for (int s = 16; s > 0; s >>= 1) {
-                    const int ex = __shfl_sync(FULL, excl, k + s);
-                    if (ex <= eid) k += s;
+                for (int q = 0; q < LW; ++q) {
+                    const int eq = base + 32 * q + lane;
+                    const int k = tile_owner(excl, eq);
+                    kx[q] = __shfl_sync(FULL, excl, k);
+                    p[q] = __shfl_sync(FULL, b, k) + (eq - kx[q]);
                 }
-                const int64_t kb = __shfl_sync(FULL, b, k);
-                const int kex = __shfl_sync(FULL, excl, k);
-                float val = 0.f;
-                if (eid < E) {
-                    const int64_t pos = kb + (eid - kex);
-                    val = gather_c<HOT>(c, sh_hot, __ldg(idx + pos));
-                    if (W) val *= __ldg(wv + pos);
-                }
-                // segmented inclusive scan over the lanes owned by the same vertex
-                const int head = max(kex, base) - base;
 #pragma unroll
-                for (int s = 1; s < 32; s <<= 1) {
-                    const float tv = __shfl_up_sync(FULL, val, s);
-                    if (lane - s >= head) val += tv;
+                for (int q = 0; q < LW; ++q) u[q] = base + 32 * q + lane < E ? ld_idx(idx + p[q]) : 0;
+                float f[LW];
+#pragma unroll
+                for (int q = 0; q < LW; ++q) {
+                    f[q] = 0.f;
+                    if (base + 32 * q + lane < E) {
+                        f[q] = gather_c<HOT>(c, sh_hot, u[q]);
+                        if (W) f[q] *= __ldg(wv + p[q]);
+                    }
                 }
-                // each vertex collects the tail of its segment in this 32-edge window
-                const bool has = deg > 0 && excl < base + 32 && incl > base;
-                const int tail = has ? min(incl, base + 32) - base - 1 : 0;
-                const float segsum = __shfl_sync(FULL, val, tail);
-                if (has) acc += segsum;
+#pragma unroll
+                for (int q = 0; q < LW; ++q)
+                    if (base + 32 * q < E) acc += window_segment_sum(f[q], kx[q], base + 32 * q, deg, excl, incl);
             }
             if (v < n && !big) {
-                const float y = base_term(a, v) + a.d * acc;
-                res += fabs((double)y - (double)a.x[v]);
+                const float y = base_v + a.d * acc;
+                res += fabs((double)y - (double)xv);
                 a.y[v] = y;
-                a.c_next[v] = y * a.inv_deg[v];
+                a.c_next[v] = y * inv;
             }
         }
     } else {
@@ -420,8 +481,8 @@ void release_pr_work(gp_graph *g, cudaStream_t s) {
 
 // Resident blocks per SM of `kernel` (raising its dynamic shared-memory limit first).
 static int occupancy(const void *kernel, int threads, size_t smem, int &blocks) {
-    if (smem > 48 * 1024)
-        GP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // the opt-in is needed whenever dynamic + static shared memory exceeds 48 KiB; set it for any size
+    if (smem > 0) GP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, threads, smem));
     if (blocks < 1) return set_error(GP_ERR_UNSUPPORTED, "kernel does not fit on an SM (%zu B shared memory)", smem);
     return GP_OK;

@@ -650,9 +650,9 @@ int gp_set_allocator(gp_alloc_fn alloc, gp_free_fn free_fn, void *ctx) {
 int gp_options_default(gp_options *opt) {
     if (!opt) return set_error(GP_ERR_INVALID, "gp_options_default: NULL");
     memset(opt, 0, sizeof(*opt));
-    opt->pull_light_max = 32;
+    opt->pull_light_max = 16;
     opt->push_light_max = 32;
-    opt->chunk_edges = 1024;
+    opt->chunk_edges = 256;
     opt->blocks_per_sm = 4;
     opt->poll_interval = 8;
     opt->pr_auto_mode = -1;

@@ -294,7 +294,7 @@ def test_oom_from_allocator_hook(gp):
     gp.Graph.from_graphgen(g).free()
 
 
-@pytest.mark.parametrize("slots", [0, 1, 7, 100, 4096, 49152])
+@pytest.mark.parametrize("slots", [0, 1, 7, 100, 4096, 12288, 12289, 49152])
 def test_hot_slot_counts(gp, slots):
     """Any number of cached hot contributions gives the same iterate."""
     g = gg.rmat(12, 16, seed=13, symmetrize=False)
