@@ -192,6 +192,39 @@ def pick_sources(g, count: int):
     return gg.pick_vertices(g, count, seed=2)
 
 
+KERNEL_SOURCE = {"pull_big": "pagerank.cu", "pull_light": "pagerank.cu", "push_scatter": "pagerank.cu",
+                 "push_epilogue": "pagerank.cu", "bfs_topdown": "bfs.cu", "bfs_bottomup": "bfs.cu"}
+
+
+def source_key(cu_name: str) -> str:
+    """First 16 hex digits of sha256 over the kernel's .cu file and the shared header."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for p in (os.path.join(ROOT, "paper_2010_16012_gb300", "csrc", cu_name),
+              os.path.join(ROOT, "paper_2010_16012_gb300", "csrc", "gp_internal.cuh")):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from profiles/traffic.md, or None when
+    no capture exists or the kernel's source changed since it was taken."""
+    cu = KERNEL_SOURCE.get(kernel)
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not cu or not os.path.exists(path):
+        return None
+    key = source_key(cu)
+    for line in open(path):
+        f = [x.strip() for x in line.strip().strip("|").split("|")]
+        if len(f) >= 6 and f[0] == kernel and f[2] == key:
+            try:
+                return int(f[5])
+            except ValueError:
+                return None
+    return None
+
+
 def measured_peak_gbs():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -351,7 +384,7 @@ def run_ours(args, dist: Dist):
         if real:
             ach = by / (top[2] * 1e-3) / 1e9
             roofline = {"kernel": top[0], "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                        "frac": round(ach / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                        "frac": round(ach / peak, 4), "traffic": captured_traffic(top[0]), "peak_kind": peak_kind,
                         "bytes_per_launch": int(by / real), "avg_launch_ms": round(top[2] / real, 5),
                         "share": round(top[2] / total_kernel_ms, 4)}
     # the pull sweep as a whole (both pull kernels): the benchmark spec's 40%-of-HBM figure
