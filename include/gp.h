@@ -201,6 +201,38 @@ typedef struct gp_pr_stats {
 int gp_pagerank(const gp_graph *g, int mode, float damping, int iters, double tol, const float *personalization,
                 const float *x0, float *ranks_out, gp_pr_stats *stats, void *stream);
 
+/*
+ * Gradient of a loss on the PageRank fixed point (not in the paper: implicit
+ * differentiation of x = (1-d) s + d P x, so no iterate is stored).  For
+ * L with dL/dx = grad_ranks, the adjoint lambda solves
+ *     (I - d P^T) lambda = grad_ranks
+ * by the transposed sweep -- the pull sweep run over out-edges (CSR) for
+ * GP_PULL, the push sweep run over in-edges (CSC) for GP_PUSH -- with the same
+ * on-device convergence test as gp_pagerank (L1 change of lambda < tol, or
+ * `iters` sweeps).  Then
+ *     grad_personalization[v] = (1-d) lambda_v
+ *     grad_weights[e]          = d lambda_v x_u            for CSR edge e = (u -> v)
+ * i.e. dL/dP_vu for the stored transition entries (unweighted graphs: the
+ * entries 1/deg_out(u); weighted: the weights as given).  For a graph uploaded
+ * with GP_UPLOAD_NORMALIZE (P_vu = w_uv / S_u) grad_weights is the gradient
+ * with respect to the raw weights: (x_u / S_u)(d lambda_v - lambda_u + g_u).
+ *   ranks                 float[n] "any": the fixed point x the gradient is taken at.
+ *   grad_ranks            float[n] "any": dL/dx.
+ *   grad_weights          float[m] "any" or NULL, CSR edge order.
+ *   grad_personalization  float[n] "any" or NULL.
+ * Returns GP_ERR_NOT_CONVERGED (gradients still written) when tol > 0 is not met.
+ */
+int gp_pagerank_backward(const gp_graph *g, int mode, float damping, const float *ranks, const float *grad_ranks,
+                         float *grad_weights, float *grad_personalization, int iters, double tol, gp_pr_stats *stats,
+                         void *stream);
+
+/* Replace the edge weights of a weighted graph (device arrays, caller-owned,
+ * kept alive until the next call or gp_graph_free; csc_w may be NULL for a
+ * symmetric graph whose CSC shares the CSR arrays).  The per-source normaliser
+ * of a GP_UPLOAD_NORMALIZE graph is recomputed on `stream`.  Used by training
+ * loops that update weights between forward passes. */
+int gp_graph_set_weights(gp_graph *g, const float *csr_w, const float *csc_w, void *stream);
+
 /* ------------------------------------------------------------------ BFS */
 
 #define GP_BFS_MAX_LEVELS 512

@@ -74,7 +74,7 @@ def _ptr(a):
 
 class OracleGraph:
     """The oracle's own adjacency, rebuilt from an edge list (src[e] -> dst[e],
-    optional per-edge weight w[e] = P_{dst,src})."""
+    optional per-edge weight w[e] = P_{dst,src}, taken in double precision)."""
 
     def __init__(self, n: int, src, dst, w=None):
         self._lib = _get()
@@ -85,7 +85,8 @@ class OracleGraph:
         if self.m and (self._src.min() < 0 or self._src.max() >= n or self._dst.min() < 0
                        or self._dst.max() >= n):
             raise ValueError("edge endpoint outside [0, n)")
-        self._w = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+        # weights in double precision (float32 inputs convert exactly)
+        self._w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
         self._h = self._lib.or_graph_new(self.n, self.m, _ptr(self._src), _ptr(self._dst), _ptr(self._w))
 
     @classmethod

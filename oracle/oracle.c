@@ -70,7 +70,7 @@ static void or_set_threads(int nthreads) {
 
 /* Adjacency arrays of Section 2.2 built by a counting sort of the edge list;
  * within a vertex the neighbours keep the order of the input list. */
-or_graph *or_graph_new(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const float *w) {
+or_graph *or_graph_new(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const double *w) {
     or_graph *g = (or_graph *)calloc(1, sizeof(or_graph));
     g->n = n;
     g->m = m;
@@ -84,7 +84,7 @@ or_graph *or_graph_new(int64_t n, int64_t m, const int32_t *src, const int32_t *
     g->w = NULL;
     if (w) {
         g->w = (double *)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
-        for (int64_t e = 0; e < m; ++e) g->w[e] = (double)w[e];
+        for (int64_t e = 0; e < m; ++e) g->w[e] = w[e];
     }
     for (int64_t e = 0; e < m; ++e) {
         g->out_off[src[e] + 1]++;

@@ -88,6 +88,9 @@ SIGNATURES = [
     ("gp_graph_get_options", ctypes.c_int, [_VP, ctypes.POINTER(gp_options)]),
     ("gp_pagerank", ctypes.c_int, [_VP, ctypes.c_int, _F, ctypes.c_int, _D, _VP, _VP, _VP,
                                    ctypes.POINTER(gp_pr_stats), _VP]),
+    ("gp_pagerank_backward", ctypes.c_int, [_VP, ctypes.c_int, _F, _VP, _VP, _VP, _VP, ctypes.c_int, _D,
+                                            ctypes.POINTER(gp_pr_stats), _VP]),
+    ("gp_graph_set_weights", ctypes.c_int, [_VP, _VP, _VP, _VP]),
     ("gp_bfs", ctypes.c_int, [_VP, _I32, ctypes.c_int, _VP, _VP, ctypes.POINTER(gp_bfs_stats), _VP]),
     ("gp_bfs_directed", ctypes.c_int, [_VP, _I32, _VP, ctypes.c_int, _VP, _VP, ctypes.POINTER(gp_bfs_stats),
                                        _VP]),
@@ -186,15 +189,18 @@ class Graph:
     def from_graphgen(cls, g, device="cuda", validate=False, normalize=False, copy=False, stream=None):
         """Upload a graphgen.Graph (host numpy arrays): moved to CUDA tensors
         first unless copy=True (then gp_graph_upload copies from host)."""
+        # a symmetric structure with per-source weights is not a symmetric graph:
+        # its CSC weights differ, so it is uploaded with both directions
+        sym = g.symmetric and g.csr_w is None
         if copy:
-            return cls(g.n, g.csr_off, g.csr_idx, None if g.symmetric else g.csc_off,
-                       None if g.symmetric else g.csc_idx, g.csr_w, None if g.symmetric else g.csc_w,
-                       symmetric=g.symmetric, validate=validate, normalize=normalize, copy=True, stream=stream)
+            return cls(g.n, g.csr_off, g.csr_idx, None if sym else g.csc_off, None if sym else g.csc_idx, g.csr_w,
+                       None if sym else g.csc_w, symmetric=sym, validate=validate, normalize=normalize, copy=True,
+                       stream=stream)
         torch = _torch()
         t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(device)
         csr_off, csr_idx = t(g.csr_off), t(g.csr_idx)
         csr_w = t(g.csr_w)
-        if g.symmetric:
+        if sym:
             return cls(g.n, csr_off, csr_idx, None, None, csr_w, None, symmetric=True, validate=validate,
                        normalize=normalize, stream=stream)
         return cls(g.n, csr_off, csr_idx, t(g.csc_off), t(g.csc_idx), csr_w, t(g.csc_w), validate=validate,
@@ -228,6 +234,12 @@ class Graph:
         _check(load().gp_graph_get_options(self.handle, ctypes.byref(o)), "gp_graph_get_options")
         return o
 
+    def set_weights(self, csr_w, csc_w=None, stream=None):
+        """gp_graph_set_weights: point the graph at new (device) weight arrays."""
+        self._wkeep = (csr_w, csc_w)
+        _check(load().gp_graph_set_weights(self.handle, _ptr(csr_w), _ptr(csc_w), _stream_ptr(stream)),
+               "gp_graph_set_weights")
+
     def set_options(self, opt: gp_options = None, stream=None, **kw):
         o = opt if opt is not None else self.options()
         for k, v in kw.items():
@@ -249,6 +261,68 @@ def pagerank(g: Graph, mode=PULL, damping=0.85, iters=20, tol=0.0, personalizati
                               _ptr(x0), _ptr(out), ctypes.byref(st), _stream_ptr(stream)), "gp_pagerank", allow)
     return out, {"iters_done": st.iters_done, "mode_used": st.mode_used, "residual": st.residual, "ms": st.ms,
                  "converged": bool(st.converged)}
+
+
+def pagerank_backward(g: Graph, ranks, grad_ranks, mode=PULL, damping=0.85, iters=1000, tol=1e-7,
+                      want_weights=True, want_personalization=True, stream=None, raise_not_converged=False):
+    """gp_pagerank_backward.  Returns (grad_weights [CSR order] or None,
+    grad_personalization or None, stats dict)."""
+    torch = _torch()
+    gw = torch.empty(g.m, dtype=torch.float32, device="cuda") if want_weights else None
+    gs = torch.empty(g.n, dtype=torch.float32, device="cuda") if want_personalization else None
+    st = gp_pr_stats()
+    allow = () if raise_not_converged else (ERR_NOT_CONVERGED,)
+    _check(load().gp_pagerank_backward(g.handle, int(mode), float(damping), _ptr(ranks), _ptr(grad_ranks), _ptr(gw),
+                                       _ptr(gs), int(iters), float(tol), ctypes.byref(st), _stream_ptr(stream)),
+           "gp_pagerank_backward", allow)
+    return gw, gs, {"iters_done": st.iters_done, "residual": st.residual, "ms": st.ms,
+                    "converged": bool(st.converged)}
+
+
+def _autograd_function():
+    torch = _torch()
+
+    class PageRankFunction(torch.autograd.Function):
+        """x = PageRank(csr_w, s) with gradients by the adjoint kernels (implicit
+        differentiation of the fixed point; nothing is checkpointed)."""
+
+        @staticmethod
+        def forward(ctx, csr_w, personalization, graph, csc_perm, damping, iters, tol, mode, adj_iters, adj_tol):
+            if csr_w is not None:
+                csc_w = None if csc_perm is None else csr_w.detach().index_select(0, csc_perm).contiguous()
+                graph.set_weights(csr_w.detach().contiguous(), csc_w)
+            s = None if personalization is None else personalization.detach().contiguous()
+            x, _ = pagerank(graph, mode, damping, iters, tol, personalization=s)
+            ctx.graph = graph
+            ctx.cfg = (damping, mode, adj_iters, adj_tol)
+            ctx.has_w = csr_w is not None
+            ctx.has_s = personalization is not None
+            ctx.save_for_backward(x)
+            return x
+
+        @staticmethod
+        def backward(ctx, grad_x):
+            (x,) = ctx.saved_tensors
+            damping, mode, adj_iters, adj_tol = ctx.cfg
+            gw, gs, _ = pagerank_backward(ctx.graph, x, grad_x.contiguous().float(), mode, damping, adj_iters, adj_tol,
+                                          want_weights=ctx.has_w, want_personalization=ctx.has_s)
+            return gw, gs, None, None, None, None, None, None, None, None
+
+    return PageRankFunction
+
+
+def pagerank_autograd(graph: Graph, csr_w=None, personalization=None, csc_perm=None, damping=0.85, iters=1000,
+                      tol=1e-7, mode=PULL, adj_iters=1000, adj_tol=1e-7):
+    """Differentiable PageRank: gradients flow to the CSR edge weights `csr_w`
+    (the graph's weights are replaced by them; `csc_perm[j]` = CSR position of
+    CSC slot j for non-symmetric graphs) and to the personalization vector."""
+    global _PRF
+    if _PRF is None:
+        _PRF = _autograd_function()
+    return _PRF.apply(csr_w, personalization, graph, csc_perm, damping, iters, tol, mode, adj_iters, adj_tol)
+
+
+_PRF = None
 
 
 def bfs(g: Graph, src: int, mode=AUTO, level=None, parent=None, want_parent=True, dirs=None, stream=None):

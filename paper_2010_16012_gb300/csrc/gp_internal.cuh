@@ -138,6 +138,8 @@ struct PrWork {
     double *partials = nullptr;    // per-block residual partials
     float *chunk_part = nullptr;   // per-chunk partial sums (pull, big vertices)
     double *acc64 = nullptr;       // FP64 accumulator of the push scatter
+    float *lam = nullptr;          // adjoint solution
+    float *gw_dev = nullptr;       // weight gradient when the output is host memory
     void *status = nullptr;        // device PrStatus
     void *status_host = nullptr;   // pinned mirror
     int max_blocks = 0;

@@ -60,8 +60,11 @@ struct PrArgs {
     float *y;        // new iterate
     const float *c;  // contributions of x
     float *c_next;   // contributions of y (pull)
-    const float *s;  // personalization or nullptr
-    float base_uniform;  // (1-d)/n
+    const float *s;  // teleport vector (forward) or dL/dx (adjoint), or nullptr
+    float s_scale;       // factor of s in the base term: 1-d (forward), 1 (adjoint)
+    float base_uniform;  // base term when s is nullptr: (1-d)/n
+    const float *post_scale;  // factor of the gathered sum per owner (adjoint: inv_deg), or nullptr
+    const float *cmul;        // c_next = y * cmul (forward: inv_deg), or nullptr (c_next = y)
     float one_minus_d, d;
     double tol;
     int32_t k;  // sweep number, 1-based
@@ -76,8 +79,10 @@ struct PrArgs {
 };
 
 __device__ __forceinline__ float base_term(const PrArgs &a, int64_t v) {
-    return a.s ? a.one_minus_d * a.s[v] : a.base_uniform;
+    return a.s ? a.s_scale * a.s[v] : a.base_uniform;
 }
+__device__ __forceinline__ float post_factor(const PrArgs &a, int64_t v) { return a.post_scale ? a.post_scale[v] : 1.f; }
+__device__ __forceinline__ float c_factor(const PrArgs &a, int64_t v) { return a.cmul ? a.cmul[v] : 1.f; }
 
 // Convergence gate at the start of sweep k: every block reduces the residual
 // partials of sweep k-1 in the same order, so all blocks take the same
@@ -110,16 +115,17 @@ __device__ bool pr_gate(const PrArgs &a, int k) {
     return stop != 0;
 }
 
-__global__ void k_pr_init(int64_t n, const float *x0, const float *inv_deg, float *r0, float *c, float *r_push,
-                          double *acc64, const float *s, float one_minus_d, float base_uniform, PrStatus *status) {
+// x = x0 (or 1/n), c = x * cmul, and the push accumulators zeroed.
+__global__ void k_pr_init(int64_t n, const float *x0, const float *cmul, float *r0, float *c, float *r_push,
+                          double *acc64, PrStatus *status) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const float x_uniform = 1.0f / (float)n;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         const float x = x0 ? x0[v] : x_uniform;
         r0[v] = x;
-        c[v] = x * inv_deg[v];
-        if (r_push) r_push[v] = s ? one_minus_d * s[v] : base_uniform;
-        if (acc64) acc64[v] = (double)(s ? one_minus_d * s[v] : base_uniform);
+        c[v] = cmul ? x * cmul[v] : x;
+        if (r_push) r_push[v] = 0.f;
+        if (acc64) acc64[v] = 0.0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         status->done = 0;
@@ -273,10 +279,11 @@ __global__ void __launch_bounds__(512, GP_LIGHT_MIN_BLOCKS) k_pull_light(PrArgs 
             const int64_t v = t * 32 + lane;
             const int64_t b = nb, e = ne;
             // per-vertex operands, independent of the edges: issued now
-            float xv = 0.f, inv = 0.f, base_v = 0.f;
+            float xv = 0.f, cm = 0.f, ps = 0.f, base_v = 0.f;
             if (v < n) {
                 xv = a.x[v];
-                inv = a.inv_deg[v];
+                cm = c_factor(a, v);
+                ps = post_factor(a, v);
                 base_v = base_term(a, v);
             }
             const int64_t tn = t + nwarps, vn = tn * 32 + lane;
@@ -320,10 +327,10 @@ __global__ void __launch_bounds__(512, GP_LIGHT_MIN_BLOCKS) k_pull_light(PrArgs 
                     if (base + 32 * q < E) acc += window_segment_sum(f[q], kx[q], base + 32 * q, deg, excl, incl);
             }
             if (v < n && !big) {
-                const float y = base_v + a.d * acc;
+                const float y = base_v + a.d * (ps * acc);
                 res += fabs((double)y - (double)xv);
                 a.y[v] = y;
-                a.c_next[v] = y * inv;
+                a.c_next[v] = y * cm;
             }
         }
     } else {
@@ -332,10 +339,10 @@ __global__ void __launch_bounds__(512, GP_LIGHT_MIN_BLOCKS) k_pull_light(PrArgs 
             const int32_t v = a.big[r];
             float acc = 0.f;
             for (int64_t j = a.cstart[r]; j < a.cstart[r + 1]; ++j) acc += a.chunk_part[j];
-            const float y = base_term(a, v) + a.d * acc;
+            const float y = base_term(a, v) + a.d * (post_factor(a, v) * acc);
             res += fabs((double)y - (double)a.x[v]);
             a.y[v] = y;
-            a.c_next[v] = y * a.inv_deg[v];
+            a.c_next[v] = y * c_factor(a, v);
         }
     }
     res = block_sum(res, sm);
@@ -439,8 +446,9 @@ __global__ void __launch_bounds__(256) k_push_scatter(PrArgs a) {
     }
 }
 
-// Per vertex: the finished sum (rounded to the FP32 rank), the residual, the
-// next contribution, and the reset of the buffer the next sweep accumulates into.
+// Per vertex: y = base + post_scale * (scattered sum), rounded to the FP32 rank;
+// the residual, the next contribution, and the zeroing of the buffer the next
+// sweep accumulates into.
 template <class T>
 __global__ void __launch_bounds__(256) k_push_epilogue(PrArgs a) {
     __shared__ double sm[32];
@@ -449,28 +457,104 @@ __global__ void __launch_bounds__(256) k_push_epilogue(PrArgs a) {
     double res = 0.0;
     float *x_reset = const_cast<float *>(a.x);
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += stride) {
+        const float base = base_term(a, v), ps = post_factor(a, v);
+        float y;
         if (sizeof(T) == 8) {
-            const float y = (float)a.acc64[v];
-            res += fabs((double)y - (double)a.x[v]);
-            a.y[v] = y;
-            a.c_next[v] = y * a.inv_deg[v];
-            a.acc64[v] = (double)base_term(a, v);
+            y = (float)((double)base + (double)ps * a.acc64[v]);
+            a.acc64[v] = 0.0;
         } else {
-            const float y = a.y[v];
-            res += fabs((double)y - (double)a.x[v]);
-            a.c_next[v] = y * a.inv_deg[v];
-            x_reset[v] = base_term(a, v);  // the next sweep accumulates into this buffer
+            y = base + ps * a.y[v];
         }
+        res += fabs((double)y - (double)a.x[v]);
+        a.y[v] = y;
+        a.c_next[v] = y * c_factor(a, v);
+        if (sizeof(T) != 8) x_reset[v] = 0.f;  // the next sweep accumulates into this buffer
     }
     res = block_sum(res, sm);
     if (threadIdx.x == 0) a.partials[blockIdx.x] = res;
 }
 
-// ------------------------------------------------------------------ driver
+// ------------------------------------------------------------------ adjoint gradients
 
-struct PrGrids {
-    int big, light, epi_big, total2;
+// grad_s[v] = (1-d) lambda_v
+__global__ void k_grad_s(int64_t n, float one_minus_d, const float *lam, float *grad_s) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) grad_s[v] = one_minus_d * lam[v];
+}
+
+struct GradArgs {
+    int64_t n;
+    const int64_t *off;  // CSR
+    const int32_t *idx;
+    const float *x, *lam, *g, *inv_deg;
+    const Chunk *chunks;
+    int64_t nchunks;
+    int32_t light_max;
+    float d;
+    int normalized;
+    float *grad_w;
+    int32_t split_blocks;
 };
+
+// dL/dP_vu = d lambda_v x_u for the CSR edge e = (u -> v); with per-source
+// normalisation P_vu = w_uv / S_u the raw-weight gradient is
+// (x_u / S_u) (d lambda_v - lambda_u + g_u), using lambda_u = g_u + d (P^T lambda)_u.
+__device__ __forceinline__ float edge_grad(const GradArgs &a, int32_t u, int32_t v, float xu_or_coef, float lam_u_term) {
+    return a.normalized ? xu_or_coef * (a.d * a.lam[v] - lam_u_term) : a.d * a.lam[v] * xu_or_coef;
+}
+
+__global__ void __launch_bounds__(256) k_grad_w(GradArgs a) {
+    const int lane = lane_id();
+    if ((int)blockIdx.x < a.split_blocks) {
+        const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        const int64_t nwarps = ((int64_t)a.split_blocks * blockDim.x) >> 5;
+        for (int64_t j = warp; j < a.nchunks; j += nwarps) {
+            const Chunk ch = a.chunks[j];
+            const int32_t u = ch.v;
+            const float coef = a.normalized ? a.x[u] * a.inv_deg[u] : a.x[u];
+            const float lt = a.normalized ? a.lam[u] - a.g[u] : 0.f;
+            for (int i = lane; i < ch.len; i += 32) {
+                const int64_t pos = ch.beg + i;
+                a.grad_w[pos] = edge_grad(a, u, a.idx[pos], coef, lt);
+            }
+        }
+    } else {
+        const int64_t warp = ((int64_t)(blockIdx.x - a.split_blocks) * blockDim.x + threadIdx.x) >> 5;
+        const int64_t nwarps = ((int64_t)(gridDim.x - a.split_blocks) * blockDim.x) >> 5;
+        const int64_t ntiles = (a.n + 31) >> 5;
+        for (int64_t t = warp; t < ntiles; t += nwarps) {
+            const int64_t u = t * 32 + lane;
+            int64_t b = 0, e = 0;
+            float coef = 0.f, lt = 0.f;
+            if (u < a.n) {
+                b = a.off[u];
+                e = a.off[u + 1];
+                coef = a.normalized ? a.x[u] * a.inv_deg[u] : a.x[u];
+                lt = a.normalized ? a.lam[u] - a.g[u] : 0.f;
+            }
+            const int64_t dd = e - b;
+            const int deg = dd > a.light_max ? 0 : (int)dd;
+            const int incl = warp_incl_scan(deg);
+            const int excl = incl - deg;
+            const int E = __shfl_sync(FULL, incl, 31);
+            for (int base = 0; base < E; base += 32) {
+                const int eid = base + lane;
+                const int k = tile_owner(excl, eid);
+                const int64_t kb = __shfl_sync(FULL, b, k);
+                const int kex = __shfl_sync(FULL, excl, k);
+                const float kc = __shfl_sync(FULL, coef, k);
+                const float kl = __shfl_sync(FULL, lt, k);
+                const int32_t ku = (int32_t)(t * 32 + k);
+                if (eid < E) {
+                    const int64_t pos = kb + (eid - kex);
+                    a.grad_w[pos] = edge_grad(a, ku, a.idx[pos], kc, kl);
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ driver
 
 void release_pr_work(gp_graph *g, cudaStream_t s) {
     if (g->pr.status_host) cudaFreeHost(g->pr.status_host);
@@ -492,14 +576,15 @@ static int ensure_pr_work(gp_graph *g, cudaStream_t s) {
     PrWork &w = g->pr;
     if (w.ready) return GP_OK;
     const size_t n = (size_t)std::max<int64_t>(g->n, 1);
-    const int64_t epi = (g->pull_bins.nbig + 255) / 256;
+    const int64_t nbig = std::max(g->pull_bins.nbig, g->push_bins.nbig);
+    const int64_t epi = (nbig + 255) / 256;
     // covers any grid: at most 32 resident blocks per SM, plus the epilogue blocks
     w.max_blocks = (int)(std::max(g->num_sms * 32, grid_blocks(g, 256)) + epi + 64);
     GP_TRY(w.mem.alloc(w.r1, n, s));
     GP_TRY(w.mem.alloc(w.c0, n, s));
     GP_TRY(w.mem.alloc(w.c1, n, s));
     GP_TRY(w.mem.alloc(w.partials, (size_t)w.max_blocks, s));
-    GP_TRY(w.mem.alloc(w.chunk_part, (size_t)std::max<int64_t>(g->pull_bins.nchunks, 1), s));
+    GP_TRY(w.mem.alloc(w.chunk_part, (size_t)std::max<int64_t>(std::max(g->pull_bins.nchunks, g->push_bins.nchunks), 1), s));
     PrStatus *st = nullptr;
     GP_TRY(w.mem.alloc(st, 1, s));
     w.status = st;
@@ -513,95 +598,64 @@ static int ensure_vec(gp_graph *g, float *&slot, cudaStream_t s) {
     return g->pr.mem.alloc(slot, (size_t)std::max<int64_t>(g->n, 1), s);
 }
 
-}  // namespace gp
+// One power iteration y = base + d * post_scale * (gather or scatter over the
+// given adjacency) of a PageRank-type linear system, with on-device
+// convergence; used for the forward pass and for the adjoint.
+struct IterSpec {
+    bool push;        // scatter with atomics (else gather, owner-only writes)
+    bool hot;         // use the pull hot-contribution cache (forward pull only)
+    const int64_t *off;
+    const int32_t *idx;
+    const float *w;
+    const BigBins *bins;
+    const float *s;   // base vector (nullable: uniform base_uniform)
+    float s_scale, base_uniform, d;
+    const float *x0;  // start vector (nullable: 1/n)
+    const float *post_scale, *cmul;
+    int iters;
+    double tol;
+};
 
-using namespace gp;
-
-extern "C" int gp_pagerank(const gp_graph *gc, int mode, float damping, int iters, double tol,
-                           const float *personalization, const float *x0, float *ranks_out, gp_pr_stats *stats,
-                           void *stream) {
-    clear_error();
-    gp_graph *g = const_cast<gp_graph *>(gc);
-    if (!g) return set_error(GP_ERR_INVALID, "gp_pagerank: graph is NULL");
-    if (!ranks_out) return set_error(GP_ERR_INVALID, "gp_pagerank: ranks_out is NULL");
-    if (!(damping > 0.f && damping < 1.f)) return set_error(GP_ERR_INVALID, "damping %g outside (0, 1)", (double)damping);
-    if (iters < 1) return set_error(GP_ERR_INVALID, "iters = %d < 1", iters);
-    if (!(tol >= 0.0)) return set_error(GP_ERR_INVALID, "tol must be >= 0");
-    if (mode != GP_PUSH && mode != GP_PULL && mode != GP_AUTO) return set_error(GP_ERR_INVALID, "bad mode %d", mode);
-    cudaStream_t s = (cudaStream_t)stream;
-    if (mode == GP_AUTO) mode = g->opt.pr_auto_mode >= 0 ? g->opt.pr_auto_mode : GP_PULL;
+static int pr_iterate(gp_graph *g, const IterSpec &sp, float *out, PrStatus &fin, cudaStream_t s) {
     const int64_t n = g->n;
-    if (stats) memset(stats, 0, sizeof(*stats));
-    if (n == 0) {
-        if (stats) {
-            stats->mode_used = mode;
-            stats->converged = 1;
-        }
-        return GP_OK;
-    }
-    GP_TRY(ensure_pr_work(g, s));
     PrWork &w = g->pr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    if (stats) {
-        GP_CUDA(cudaEventCreate(&ev0));
-        GP_CUDA(cudaEventCreate(&ev1));
-        GP_CUDA(cudaEventRecord(ev0, s));
-    }
-    // inputs and outputs that live in host memory go through library buffers
-    const bool out_dev = is_device_ptr(ranks_out);
-    float *R0 = ranks_out;
-    if (!out_dev) {
-        GP_TRY(ensure_vec(g, w.out_dev, s));
-        R0 = w.out_dev;
-    }
-    const float *S = personalization;
-    if (S && !is_device_ptr(S)) {
-        GP_TRY(ensure_vec(g, w.s_dev, s));
-        GP_CUDA(cudaMemcpyAsync(w.s_dev, S, n * sizeof(float), cudaMemcpyHostToDevice, s));
-        S = w.s_dev;
-    }
-    const float *X0 = x0;
-    if (X0 && !is_device_ptr(X0)) {
-        GP_TRY(ensure_vec(g, w.x0_dev, s));
-        GP_CUDA(cudaMemcpyAsync(w.x0_dev, X0, n * sizeof(float), cudaMemcpyHostToDevice, s));
-        X0 = w.x0_dev;
-    }
-    float *R[2] = {R0, w.r1};
+    float *R[2] = {out, w.r1};
     float *C[2] = {w.c0, w.c1};
     PrStatus *status = (PrStatus *)w.status;
-    const bool push = mode == GP_PUSH;
-    const bool W = g->weighted;
+    const bool push = sp.push;
+    const bool W = sp.w != nullptr;
+    const BigBins &bins = *sp.bins;
 
     PrArgs a;
     memset(&a, 0, sizeof(a));
     a.n = n;
-    a.off = push ? g->csr_off : g->csc_off;
-    a.idx = push ? g->csr_idx : g->csc_idx;
-    a.w = W ? (push ? g->csr_w : g->csc_w) : nullptr;
-    a.inv_deg = g->inv_deg;
-    const BigBins &bins = push ? g->push_bins : g->pull_bins;
+    a.off = sp.off;
+    a.idx = sp.idx;
+    a.w = sp.w;
     a.big = bins.big;
     a.cstart = bins.cstart;
     a.chunks = bins.chunks;
     a.nbig = bins.nbig;
     a.nchunks = bins.nchunks;
     a.light_max = bins.light_max;
-    a.s = S;
-    a.one_minus_d = 1.0f - damping;
-    a.d = damping;
-    a.base_uniform = (float)((1.0 - (double)damping) / (double)n);
-    a.tol = tol;
+    a.s = sp.s;
+    a.s_scale = sp.s_scale;
+    a.base_uniform = sp.base_uniform;
+    a.post_scale = sp.post_scale;
+    a.cmul = sp.cmul;
+    a.one_minus_d = 1.0f - sp.d;
+    a.d = sp.d;
+    a.tol = sp.tol;
     a.partials = w.partials;
     a.chunk_part = w.chunk_part;
     a.status = status;
 
     const int gb = grid_blocks(g, 256);
     const int64_t ntiles = (n + 31) / 32;
-    // pull: hot-contribution cache in shared memory (built once per graph)
     bool hot = false;
     int tbp = 256, tbl = 256;  // threads per block of pull_big / pull_light
     size_t smem = 0;
-    if (!push) {
+    if (!push && sp.hot) {
         if (g->pull_hot.slots != g->opt.pull_hot_slots) GP_TRY(build_pull_hot(g, g->opt.pull_hot_slots, s));
         hot = g->pull_hot.nhot > 0;
         if (hot) {
@@ -613,17 +667,19 @@ extern "C" int gp_pagerank(const gp_graph *gc, int mode, float damping, int iter
             a.idx = g->pull_hot.enc_idx;
         }
     }
-    // grids
+    if (!push && !hot) {
+        tbp = 1024;
+        tbl = 512;
+    }
     int g1, g2, split;
     if (!push) {
         int ob = 0, ol = 0;
-        if (W) {
-            GP_TRY(occupancy(hot ? (const void *)k_pull_big<true, true> : (const void *)k_pull_big<true, false>, tbp, smem, ob));
-            GP_TRY(occupancy(hot ? (const void *)k_pull_light<true, true> : (const void *)k_pull_light<true, false>, tbl, smem, ol));
-        } else {
-            GP_TRY(occupancy(hot ? (const void *)k_pull_big<false, true> : (const void *)k_pull_big<false, false>, tbp, smem, ob));
-            GP_TRY(occupancy(hot ? (const void *)k_pull_light<false, true> : (const void *)k_pull_light<false, false>, tbl, smem, ol));
-        }
+        const void *kb_ = W ? (hot ? (const void *)k_pull_big<true, true> : (const void *)k_pull_big<true, false>)
+                            : (hot ? (const void *)k_pull_big<false, true> : (const void *)k_pull_big<false, false>);
+        const void *kl_ = W ? (hot ? (const void *)k_pull_light<true, true> : (const void *)k_pull_light<true, false>)
+                            : (hot ? (const void *)k_pull_light<false, true> : (const void *)k_pull_light<false, false>);
+        GP_TRY(occupancy(kb_, tbp, smem, ob));
+        GP_TRY(occupancy(kl_, tbl, smem, ol));
         const int wpb = tbp / 32, wpl = tbl / 32;
         g1 = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ob * g->num_sms, (bins.nchunks + wpb - 1) / wpb));
         split = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ol * g->num_sms, (ntiles + wpl - 1) / wpl));
@@ -641,9 +697,8 @@ extern "C" int gp_pagerank(const gp_graph *gc, int mode, float damping, int iter
     const bool fp64 = push && g->opt.push_fp64_accum;
     if (fp64 && !w.acc64) GP_TRY(w.mem.alloc(w.acc64, (size_t)n, s));
     a.acc64 = fp64 ? w.acc64 : nullptr;
-    GP_LAUNCH("pr_init", s, (k_pr_init<<<ib, 256, 0, s>>>(n, X0, g->inv_deg, R[0], C[0], (push && !fp64) ? R[1] : nullptr,
-                                                          a.acc64, S,
-                                                          a.one_minus_d, a.base_uniform, status)));
+    GP_LAUNCH("pr_init", s, (k_pr_init<<<ib, 256, 0, s>>>(n, sp.x0, sp.cmul, R[0], C[0], (push && !fp64) ? R[1] : nullptr,
+                                                          a.acc64, status)));
     GP_TRY(check_launch("pr_init"));
     auto enqueue_hot_gather = [&](const float *c_src) -> int {
         const int hb = (int)std::max<int64_t>(1, std::min<int64_t>((g->pull_hot.nhot + 255) / 256, 4096));
@@ -704,6 +759,7 @@ extern "C" int gp_pagerank(const gp_graph *gc, int mode, float damping, int iter
     };
 
     const int poll = std::max(1, g->opt.poll_interval);
+    const int iters = sp.iters;
     int issued = 0;
     cudaEvent_t evs[2] = {nullptr, nullptr};
     GP_CUDA(cudaEventCreateWithFlags(&evs[0], cudaEventDisableTiming));
@@ -712,7 +768,7 @@ extern "C" int gp_pagerank(const gp_graph *gc, int mode, float damping, int iter
     int batch = 0, oldest = 0;
     bool stop = false;
     int st = GP_OK;
-    if (tol <= 0.0) {
+    if (sp.tol <= 0.0) {
         for (int k = 1; k <= iters && st == GP_OK; ++k) st = enqueue_sweep(k);
         if (st == GP_OK) st = enqueue_finish(iters + 1, 0);
         issued = iters;
@@ -748,13 +804,110 @@ extern "C" int gp_pagerank(const gp_graph *gc, int mode, float damping, int iter
     cudaEventDestroy(evs[0]);
     cudaEventDestroy(evs[1]);
     if (st != GP_OK) return st;
-    if (e != cudaSuccess) return set_error(GP_ERR_CUDA, "gp_pagerank: %s", cudaGetErrorString(e));
-    // authoritative final status
+    if (e != cudaSuccess) return set_error(GP_ERR_CUDA, "pagerank iteration: %s", cudaGetErrorString(e));
+    GP_CUDA(cudaMemcpyAsync(&fin, status, sizeof(PrStatus), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    if ((fin.iters_done & 1) && fin.iters_done > 0)
+        GP_CUDA(cudaMemcpyAsync(out, R[1], n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return GP_OK;
+}
+
+// Device pointer for a caller array of n floats that may live in host memory.
+static int device_input(gp_graph *g, const float *p, float *&slot, const float *&dev, cudaStream_t s) {
+    dev = p;
+    if (p && !is_device_ptr(p)) {
+        GP_TRY(ensure_vec(g, slot, s));
+        GP_CUDA(cudaMemcpyAsync(slot, p, g->n * sizeof(float), cudaMemcpyHostToDevice, s));
+        dev = slot;
+    }
+    return GP_OK;
+}
+
+static int pr_validate(const gp_graph *g, int mode, float damping, int iters, double tol) {
+    if (!g) return set_error(GP_ERR_INVALID, "graph is NULL");
+    if (!(damping > 0.f && damping < 1.f)) return set_error(GP_ERR_INVALID, "damping %g outside (0, 1)", (double)damping);
+    if (iters < 1) return set_error(GP_ERR_INVALID, "iters = %d < 1", iters);
+    if (!(tol >= 0.0)) return set_error(GP_ERR_INVALID, "tol must be >= 0");
+    if (mode != GP_PUSH && mode != GP_PULL && mode != GP_AUTO) return set_error(GP_ERR_INVALID, "bad mode %d", mode);
+    return GP_OK;
+}
+
+__global__ void k_recompute_inv(const int64_t *csr_off, const float *csr_w, int64_t n, int normalize, float *inv_deg) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+        const int64_t b = csr_off[u], e = csr_off[u + 1];
+        float inv = 0.f;
+        if (e > b) {
+            if (normalize) {
+                double sw = 0.0;
+                for (int64_t j = b; j < e; ++j) sw += (double)csr_w[j];
+                inv = sw > 0.0 ? (float)(1.0 / sw) : 0.f;
+            } else {
+                inv = 1.f;
+            }
+        }
+        inv_deg[u] = inv;
+    }
+}
+
+}  // namespace gp
+
+using namespace gp;
+
+extern "C" int gp_pagerank(const gp_graph *gc, int mode, float damping, int iters, double tol,
+                           const float *personalization, const float *x0, float *ranks_out, gp_pr_stats *stats,
+                           void *stream) {
+    clear_error();
+    gp_graph *g = const_cast<gp_graph *>(gc);
+    GP_TRY(pr_validate(g, mode, damping, iters, tol));
+    if (!ranks_out) return set_error(GP_ERR_INVALID, "gp_pagerank: ranks_out is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (mode == GP_AUTO) mode = g->opt.pr_auto_mode >= 0 ? g->opt.pr_auto_mode : GP_PULL;
+    const int64_t n = g->n;
+    if (stats) memset(stats, 0, sizeof(*stats));
+    if (n == 0) {
+        if (stats) {
+            stats->mode_used = mode;
+            stats->converged = 1;
+        }
+        return GP_OK;
+    }
+    GP_TRY(ensure_pr_work(g, s));
+    PrWork &w = g->pr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (stats) {
+        GP_CUDA(cudaEventCreate(&ev0));
+        GP_CUDA(cudaEventCreate(&ev1));
+        GP_CUDA(cudaEventRecord(ev0, s));
+    }
+    const bool out_dev = is_device_ptr(ranks_out);
+    float *R0 = ranks_out;
+    if (!out_dev) {
+        GP_TRY(ensure_vec(g, w.out_dev, s));
+        R0 = w.out_dev;
+    }
+    const float *S = nullptr, *X0 = nullptr;
+    GP_TRY(device_input(g, personalization, w.s_dev, S, s));
+    GP_TRY(device_input(g, x0, w.x0_dev, X0, s));
+    const bool push = mode == GP_PUSH;
+    IterSpec sp;
+    sp.push = push;
+    sp.hot = !push;
+    sp.off = push ? g->csr_off : g->csc_off;
+    sp.idx = push ? g->csr_idx : g->csc_idx;
+    sp.w = g->weighted ? (push ? g->csr_w : g->csc_w) : nullptr;
+    sp.bins = push ? &g->push_bins : &g->pull_bins;
+    sp.s = S;
+    sp.s_scale = 1.0f - damping;
+    sp.base_uniform = (float)((1.0 - (double)damping) / (double)n);
+    sp.d = damping;
+    sp.x0 = X0;
+    sp.post_scale = nullptr;
+    sp.cmul = g->inv_deg;
+    sp.iters = iters;
+    sp.tol = tol;
     PrStatus fin;
-    GP_CUDA(cudaMemcpy(&fin, status, sizeof(PrStatus), cudaMemcpyDeviceToHost));
-    const int kdone = fin.iters_done;
-    if ((kdone & 1) && kdone > 0)
-        GP_CUDA(cudaMemcpyAsync(R0, R[1], n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    GP_TRY(pr_iterate(g, sp, R0, fin, s));
     if (!out_dev) GP_CUDA(cudaMemcpyAsync(ranks_out, R0, n * sizeof(float), cudaMemcpyDeviceToHost, s));
     if (stats) {
         GP_CUDA(cudaEventRecord(ev1, s));
@@ -763,7 +916,7 @@ extern "C" int gp_pagerank(const gp_graph *gc, int mode, float damping, int iter
         cudaEventElapsedTime(&ms, ev0, ev1);
         cudaEventDestroy(ev0);
         cudaEventDestroy(ev1);
-        stats->iters_done = kdone;
+        stats->iters_done = fin.iters_done;
         stats->mode_used = mode;
         stats->residual = fin.residual;
         stats->ms = ms;
@@ -772,6 +925,133 @@ extern "C" int gp_pagerank(const gp_graph *gc, int mode, float damping, int iter
         GP_CUDA(cudaStreamSynchronize(s));
     }
     if (tol > 0.0 && !fin.converged)
-        return set_error(GP_ERR_NOT_CONVERGED, "residual %.3e >= tol %.3e after %d sweeps", fin.residual, tol, kdone);
+        return set_error(GP_ERR_NOT_CONVERGED, "residual %.3e >= tol %.3e after %d sweeps", fin.residual, tol,
+                         fin.iters_done);
+    return GP_OK;
+}
+
+extern "C" int gp_pagerank_backward(const gp_graph *gc, int mode, float damping, const float *ranks,
+                                    const float *grad_ranks, float *grad_weights, float *grad_personalization,
+                                    int iters, double tol, gp_pr_stats *stats, void *stream) {
+    clear_error();
+    gp_graph *g = const_cast<gp_graph *>(gc);
+    GP_TRY(pr_validate(g, mode, damping, iters, tol));
+    if (!ranks || !grad_ranks) return set_error(GP_ERR_INVALID, "gp_pagerank_backward: ranks and grad_ranks are required");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (mode == GP_AUTO) mode = GP_PULL;
+    const int64_t n = g->n, m = g->m;
+    if (stats) memset(stats, 0, sizeof(*stats));
+    if (n == 0) return GP_OK;
+    GP_TRY(ensure_pr_work(g, s));
+    PrWork &w = g->pr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (stats) {
+        GP_CUDA(cudaEventCreate(&ev0));
+        GP_CUDA(cudaEventCreate(&ev1));
+        GP_CUDA(cudaEventRecord(ev0, s));
+    }
+    const float *X = nullptr, *G = nullptr;
+    GP_TRY(device_input(g, ranks, w.x0_dev, X, s));
+    GP_TRY(device_input(g, grad_ranks, w.s_dev, G, s));
+    GP_TRY(ensure_vec(g, w.lam, s));
+    // (I - d P^T) lambda = g: the transposed sweep.  Pull gathers lambda over the
+    // out-edges (CSR) of every vertex; push scatters lambda_v over the in-edges (CSC).
+    const bool push = mode == GP_PUSH;
+    IterSpec sp;
+    sp.push = push;
+    sp.hot = false;
+    sp.off = push ? g->csc_off : g->csr_off;
+    sp.idx = push ? g->csc_idx : g->csr_idx;
+    sp.w = g->weighted ? (push ? g->csc_w : g->csr_w) : nullptr;
+    sp.bins = push ? &g->pull_bins : &g->push_bins;
+    sp.s = G;
+    sp.s_scale = 1.0f;
+    sp.base_uniform = 0.f;
+    sp.d = damping;
+    sp.x0 = G;
+    sp.post_scale = g->inv_deg;
+    sp.cmul = nullptr;
+    sp.iters = iters;
+    sp.tol = tol;
+    PrStatus fin;
+    GP_TRY(pr_iterate(g, sp, w.lam, fin, s));
+    const int gb = grid_blocks(g, 256);
+    if (grad_personalization) {
+        const bool dev = is_device_ptr(grad_personalization);
+        float *dst = grad_personalization;
+        if (!dev) {
+            GP_TRY(ensure_vec(g, w.out_dev, s));
+            dst = w.out_dev;
+        }
+        const int b = (int)std::max<int64_t>(1, std::min<int64_t>(gb, (n + 255) / 256));
+        GP_LAUNCH("grad_s", s, (k_grad_s<<<b, 256, 0, s>>>(n, 1.0f - damping, w.lam, dst)));
+        GP_TRY(check_launch("grad_s"));
+        if (!dev) GP_CUDA(cudaMemcpyAsync(grad_personalization, dst, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    }
+    if (grad_weights && m > 0) {
+        const bool dev = is_device_ptr(grad_weights);
+        float *dst = grad_weights;
+        if (!dev) {
+            if (!w.gw_dev) GP_TRY(w.mem.alloc(w.gw_dev, (size_t)m, s));
+            dst = w.gw_dev;
+        }
+        GradArgs ga;
+        ga.n = n;
+        ga.off = g->csr_off;
+        ga.idx = g->csr_idx;
+        ga.x = X;
+        ga.lam = w.lam;
+        ga.g = G;
+        ga.inv_deg = g->inv_deg;
+        ga.chunks = g->push_bins.chunks;
+        ga.nchunks = g->push_bins.nchunks;
+        ga.light_max = g->push_bins.light_max;
+        ga.d = damping;
+        ga.normalized = g->normalized ? 1 : 0;
+        ga.grad_w = dst;
+        const int64_t ntiles = (n + 31) / 32;
+        ga.split_blocks = (int)std::min<int64_t>(gb, (ga.nchunks + 7) / 8);
+        const int b = ga.split_blocks + (int)std::max<int64_t>(1, std::min<int64_t>(gb, (ntiles + 7) / 8));
+        GP_LAUNCH("grad_w", s, (k_grad_w<<<b, 256, 0, s>>>(ga)));
+        GP_TRY(check_launch("grad_w"));
+        if (!dev) GP_CUDA(cudaMemcpyAsync(grad_weights, dst, m * sizeof(float), cudaMemcpyDeviceToHost, s));
+    }
+    if (stats) {
+        GP_CUDA(cudaEventRecord(ev1, s));
+        GP_CUDA(cudaEventSynchronize(ev1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+        stats->iters_done = fin.iters_done;
+        stats->mode_used = mode;
+        stats->residual = fin.residual;
+        stats->ms = ms;
+        stats->converged = (tol <= 0.0) ? 1 : fin.converged;
+    }
+    GP_CUDA(cudaStreamSynchronize(s));
+    if (tol > 0.0 && !fin.converged)
+        return set_error(GP_ERR_NOT_CONVERGED, "adjoint residual %.3e >= tol %.3e after %d sweeps", fin.residual, tol,
+                         fin.iters_done);
+    return GP_OK;
+}
+
+extern "C" int gp_graph_set_weights(gp_graph *g, const float *csr_w, const float *csc_w, void *stream) {
+    clear_error();
+    if (!g) return set_error(GP_ERR_INVALID, "gp_graph_set_weights: graph is NULL");
+    if (!g->weighted) return set_error(GP_ERR_UNSUPPORTED, "gp_graph_set_weights: the graph was uploaded without weights");
+    if (!csr_w || !is_device_ptr(csr_w)) return set_error(GP_ERR_INVALID, "gp_graph_set_weights: csr_w must be device memory");
+    const bool shared = g->csc_idx == g->csr_idx;
+    if (!shared && (!csc_w || !is_device_ptr(csc_w)))
+        return set_error(GP_ERR_INVALID, "gp_graph_set_weights: csc_w must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    g->csr_w = csr_w;
+    g->csc_w = shared ? csr_w : csc_w;
+    const int64_t n = g->n;
+    if (n > 0) {
+        const int b = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)g->num_sms * 8));
+        GP_LAUNCH("recompute_inv", s, (k_recompute_inv<<<b, 256, 0, s>>>(g->csr_off, g->csr_w, n, g->normalized, g->inv_deg)));
+        GP_TRY(check_launch("recompute_inv"));
+    }
     return GP_OK;
 }
