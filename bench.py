@@ -52,7 +52,8 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--quiet", action="store_true")
-    p.add_argument("--only", choices=["pr_pull", "pr_push", "bfs"], default=None,
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--only", choices=["pr_pull", "pr_push", "bfs", "batched"], default=None,
                    help="profiling case: run only this part (fixed --sweeps for PageRank), no contract line")
     p.add_argument("--sweeps", type=int, default=4)
     p.add_argument("--opt", action="append", default=[], metavar="KEY=VALUE",
@@ -408,6 +409,8 @@ def run_ours(args, dist: Dist):
            "gpu_launches": launches, "kernels": kernels[:14], "clocks": clk}
     if not args.no_e2e:
         out["e2e"] = run_e2e(args, g, srcs, dist)
+    if not args.no_batched:
+        out["batched"] = run_batched(args)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(g, srcs, args)
     return out
@@ -517,6 +520,84 @@ def run_reference(args, dist: Dist):
             "e2e": {"value": round(v, 5), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def batched_workload(nscale_lo=12, nscale_hi=18, ngraphs=32):
+    """32 R-MAT graphs, scales uniform in [12, 18] (seed 5), graph i with seed 100 + i."""
+    import graphgen as gg
+
+    scales = [nscale_lo + int(gg.draw(5, i) % (nscale_hi - nscale_lo + 1)) for i in range(ngraphs)]
+    return [gg.rmat(s, 16, seed=100 + i) for i, s in enumerate(scales)], scales
+
+
+def run_batched(args, graphs_scales=None):
+    """Batched personalised PageRank (256 one-hot vectors per graph, tol 1e-6) and
+    64-source BFS over 32 graphs in one persistent launch each, against
+    one-at-a-time gp_pagerank / gp_bfs calls on the same stream (timed on a
+    sample of vectors and sources per graph, scaled to all of them; CUDA-graph
+    capture is excluded from the batched side, launch overheads are included on
+    both sides)."""
+    import torch
+
+    import graphgen as gg
+    import paper_2010_16012_gb300 as gp
+
+    K, NSRC, SAMPLE = 256, 64, 4
+    graphs, scales = graphs_scales or batched_workload()
+    G = [gp.Graph.from_graphgen(g) for g in graphs]
+    B = gp.Batch(G, k_ppr=K)
+    seeds = np.stack([np.resize(gg.pick_vertices(g, K, seed=6 + 1000 * i), K) for i, g in enumerate(graphs)])
+    srcs = np.stack([np.resize(gg.pick_vertices(g, NSRC, seed=7 + 1000 * i), NSRC) for i, g in enumerate(graphs)])
+    B.ppr(seeds, iters=1000, tol=1e-6)  # captures the CUDA graph
+    B.msbfs(srcs)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    outs, done, st = B.ppr(seeds, iters=1000, tol=1e-6)
+    ppr_batched_s = time.perf_counter() - t
+    t = time.perf_counter()
+    louts, bst = B.msbfs(srcs)
+    bfs_batched_s = time.perf_counter() - t
+    # one at a time, on a sample
+    e = [torch.zeros(g.n, device="cuda") for g in graphs]
+    x = [torch.empty(g.n, device="cuda") for g in graphs]
+    lv = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in graphs]
+    for i in range(len(graphs)):  # warm-up of the per-graph workspaces
+        gp.pagerank(G[i], gp.PULL, 0.85, 5, 0.0, out=x[i])
+        gp.bfs(G[i], int(srcs[i, 0]), gp.AUTO, level=lv[i], want_parent=False)
+    torch.cuda.synchronize()
+    ev = [[torch.zeros(g.n, device="cuda") for _ in range(SAMPLE)] for g in graphs]
+    xs = [[torch.empty(g.n, device="cuda") for _ in range(SAMPLE)] for g in graphs]
+    for i in range(len(graphs)):
+        for j in range(SAMPLE):
+            ev[i][j][int(seeds[i, j])] = 1.0
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for i in range(len(graphs)):
+        for j in range(SAMPLE):
+            gp.pagerank(G[i], gp.PULL, 0.85, 1000, 1e-6, personalization=ev[i][j], out=xs[i][j])
+    torch.cuda.synchronize()
+    ppr_serial_s = (time.perf_counter() - t) * K / SAMPLE
+    max_err = max(float((xs[i][j] - outs[i][:, j]).abs().max()) for i in range(len(graphs)) for j in range(SAMPLE))
+    t = time.perf_counter()
+    for i in range(len(graphs)):
+        for j in range(SAMPLE):
+            gp.bfs(G[i], int(srcs[i, j]), gp.AUTO, level=lv[i], want_parent=False)
+    torch.cuda.synchronize()
+    bfs_serial_s = (time.perf_counter() - t) * NSRC / SAMPLE
+    nvec = len(graphs) * K
+    edges = sum(g.m * int(done[i].sum()) for i, g in enumerate(graphs))
+    B.free()
+    return {"graphs": len(graphs), "scales": scales, "n_total": int(sum(g.n for g in graphs)),
+            "m_total": int(sum(g.m for g in graphs)), "ppr_vectors": nvec,
+            "ppr_batched_ms": round(ppr_batched_s * 1e3, 2), "ppr_batched_sweeps": st["sweeps"],
+            "ppr_serial_ms_extrapolated": round(ppr_serial_s * 1e3, 1),
+            "ppr_speedup": round(ppr_serial_s / ppr_batched_s, 2),
+            "ppr_batched_gteps": round(edges / ppr_batched_s / 1e9, 2),
+            "ppr_max_abs_diff_vs_serial": max_err,
+            "bfs_sources": len(graphs) * NSRC, "bfs_batched_ms": round(bfs_batched_s * 1e3, 2),
+            "bfs_serial_ms_extrapolated": round(bfs_serial_s * 1e3, 1),
+            "bfs_speedup": round(bfs_serial_s / bfs_batched_s, 2), "bfs_levels": bst["levels"],
+            "serial_sample_per_graph": SAMPLE}
+
+
 def run_only(args):
     """A reduced run for profilers: one part of the step on the same kind of
     graph, --warmup + --steps repetitions, then a short JSON summary."""
@@ -525,6 +606,9 @@ def run_only(args):
     import paper_2010_16012_gb300 as gp
 
     gp.load()
+    if args.only == "batched":
+        print(json.dumps({"profile_case": "batched", **run_batched(args)}), flush=True)
+        return 0
     g = make_graph(args.scale)
     off = torch.from_numpy(g.csr_off).cuda()
     idx = torch.from_numpy(g.csr_idx).cuda()

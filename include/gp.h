@@ -276,6 +276,56 @@ int gp_bfs(const gp_graph *g, int32_t src, int mode, int32_t *level_out, int32_t
 int gp_bfs_directed(const gp_graph *g, int32_t src, const int8_t *dirs, int ndirs, int32_t *level_out,
                     int32_t *parent_out, gp_bfs_stats *stats, void *stream);
 
+/* ------------------------------------------------------------------ batches of graphs */
+
+typedef struct gp_batch gp_batch; /* opaque: a work plan over several uploaded graphs */
+
+typedef struct gp_batch_stats {
+    int32_t sweeps;  /* PageRank: sweeps run (the slowest vector's count) */
+    int32_t levels;  /* BFS: levels explored by the deepest search */
+    float ms;        /* device time of the persistent launch (CUDA events) */
+    int32_t blocks;  /* resident blocks of the cooperative launch */
+} gp_batch_stats;
+
+/*
+ * Prepare batched runs over `ngraphs` uploaded graphs (the handles stay owned
+ * by the caller and must outlive the batch).  k_ppr in {32, 64, 128, 256} is the
+ * number of personalised PageRank vectors per graph.  Reads the in-degrees once
+ * to lay out the work (vertex tiles per graph, warp chunks of in-edge lists
+ * longer than 256) and allocates, per graph, two n x k_ppr iterates and the
+ * n x 64 BFS level array.  Synchronises the stream.
+ */
+int gp_batch_create(gp_batch **out, gp_graph *const *graphs, int ngraphs, int k_ppr, void *stream);
+int gp_batch_free(gp_batch *b);
+
+/*
+ * Personalised PageRank for every graph and every one-hot seed (Section 3.1
+ * formula with s = e_seed), all graphs and vectors in one persistent
+ * cooperative launch replayed from a CUDA graph (captured on first use and
+ * whenever damping, iters or tol change).
+ *   seeds       int32[ngraphs][k_ppr] host: the seed vertex of every vector.
+ *   out         ngraphs pointers ("any", or NULL entries to skip) to float[n_i][k_ppr]
+ *               (vertex-major: column j of graph i is out[i][v * k_ppr + j]).
+ *   iters_done  int32[ngraphs][k_ppr] "any" or NULL: sweeps each vector ran.
+ * Each vector starts from 1/n and stops at its first sweep with L1 change < tol
+ * (or after `iters`), exactly as gp_pagerank with that personalization would.
+ * Returns GP_ERR_TIMEOUT if a grid barrier wait ran out.  Synchronises.
+ */
+int gp_ppr_batched(gp_batch *b, const int32_t *seeds, float damping, int iters, double tol, float *const *out,
+                   int32_t *iters_done, gp_batch_stats *stats, void *stream);
+
+/*
+ * Multi-source BFS: nsrc <= 64 searches per graph (sources: host
+ * int32[ngraphs][nsrc]) advanced together as 64-bit masks, pull levels with early
+ * exit (Section 3.3, Algorithm 3 pulling), one persistent launch from a CUDA graph.
+ *   levels_out  ngraphs pointers ("any", or NULL) to int32[n_i][64]: level of
+ *               vertex v in search j at [v * 64 + j], -1 if unreached (columns
+ *               >= nsrc stay -1).
+ * Returns GP_ERR_TIMEOUT if a grid barrier wait ran out.  Synchronises.
+ */
+int gp_msbfs_batched(gp_batch *b, const int32_t *sources, int nsrc, int32_t *const *levels_out, gp_batch_stats *stats,
+                     void *stream);
+
 /* ------------------------------------------------------------------ sweep without allocation */
 
 /* Largest graph (in vertices) gp_pull_sweep_noalloc accepts: the size of its static scratch. */

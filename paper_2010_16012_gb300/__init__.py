@@ -66,6 +66,11 @@ class gp_bfs_stats(ctypes.Structure):
                 ("examined", ctypes.c_int64 * BFS_MAX_LEVELS)]
 
 
+class gp_batch_stats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int32), ("levels", ctypes.c_int32), ("ms", ctypes.c_float),
+                ("blocks", ctypes.c_int32)]
+
+
 class gp_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -94,6 +99,12 @@ SIGNATURES = [
     ("gp_bfs", ctypes.c_int, [_VP, _I32, ctypes.c_int, _VP, _VP, ctypes.POINTER(gp_bfs_stats), _VP]),
     ("gp_bfs_directed", ctypes.c_int, [_VP, _I32, _VP, ctypes.c_int, _VP, _VP, ctypes.POINTER(gp_bfs_stats),
                                        _VP]),
+    ("gp_batch_create", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _VP]),
+    ("gp_batch_free", ctypes.c_int, [_VP]),
+    ("gp_ppr_batched", ctypes.c_int, [_VP, _VP, _F, ctypes.c_int, _D, ctypes.POINTER(_VP), _VP,
+                                      ctypes.POINTER(gp_batch_stats), _VP]),
+    ("gp_msbfs_batched", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(gp_batch_stats),
+                                        _VP]),
     ("gp_pull_sweep_noalloc", ctypes.c_int, [_I64, _I64, _VP, _VP, _VP, _VP, _VP, _F, _VP, _VP, _VP, _VP]),
     ("gp_profile_enable", ctypes.c_int, [ctypes.c_int]),
     ("gp_profile_read", ctypes.c_int, [ctypes.POINTER(gp_kernel_time), ctypes.c_int,
@@ -347,6 +358,57 @@ def bfs(g: Graph, src: int, mode=AUTO, level=None, parent=None, want_parent=True
              "direction": list(st.direction[:L]), "frontier": list(st.frontier[:L]),
              "examined": list(st.examined[:L])}
     return level, parent, stats
+
+
+class Batch:
+    """gp_batch: batched personalised PageRank and multi-source BFS over several graphs."""
+
+    def __init__(self, graphs, k_ppr=256, stream=None):
+        lib = load()
+        self.graphs = list(graphs)
+        self.k = int(k_ppr)
+        arr = (ctypes.c_void_p * len(self.graphs))(*[g.handle.value for g in self.graphs])
+        h = ctypes.c_void_p()
+        _check(lib.gp_batch_create(ctypes.byref(h), arr, len(self.graphs), self.k, _stream_ptr(stream)),
+               "gp_batch_create")
+        self._h = h
+
+    def free(self):
+        if getattr(self, "_h", None):
+            _check(load().gp_batch_free(self._h), "gp_batch_free")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def ppr(self, seeds, damping=0.85, iters=1000, tol=1e-6, outs=None, stream=None):
+        """seeds: int array [ngraphs][k].  Returns (list of [n_i, k] tensors, iters_done [ngraphs, k], stats)."""
+        torch = _torch()
+        seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.int32).reshape(len(self.graphs), self.k))
+        if outs is None:
+            outs = [torch.empty((g.n, self.k), dtype=torch.float32, device="cuda") for g in self.graphs]
+        optr = (ctypes.c_void_p * len(outs))(*[o.data_ptr() if hasattr(o, "data_ptr") else o.ctypes.data for o in outs])
+        done = np.zeros((len(self.graphs), self.k), dtype=np.int32)
+        st = gp_batch_stats()
+        _check(load().gp_ppr_batched(self._h, _ptr(seeds), float(damping), int(iters), float(tol), optr, _ptr(done),
+                                     ctypes.byref(st), _stream_ptr(stream)), "gp_ppr_batched")
+        return outs, done, {"sweeps": st.sweeps, "ms": st.ms, "blocks": st.blocks}
+
+    def msbfs(self, sources, outs=None, stream=None):
+        """sources: int array [ngraphs][nsrc] (nsrc <= 64).  Returns (list of [n_i, 64] int32 tensors, stats)."""
+        torch = _torch()
+        sources = np.ascontiguousarray(np.asarray(sources, dtype=np.int32))
+        nsrc = sources.shape[1]
+        if outs is None:
+            outs = [torch.empty((g.n, 64), dtype=torch.int32, device="cuda") for g in self.graphs]
+        optr = (ctypes.c_void_p * len(outs))(*[o.data_ptr() if hasattr(o, "data_ptr") else o.ctypes.data for o in outs])
+        st = gp_batch_stats()
+        _check(load().gp_msbfs_batched(self._h, _ptr(sources), int(nsrc), optr, ctypes.byref(st), _stream_ptr(stream)),
+               "gp_msbfs_batched")
+        return outs, {"levels": st.levels, "ms": st.ms, "blocks": st.blocks}
 
 
 NOALLOC_MAX_VERTICES = 1 << 20

@@ -1,0 +1,129 @@
+"""Batched personalised PageRank and multi-source BFS (one persistent launch
+over several graphs, replayed from a CUDA graph) against the CPU oracle and
+against the one-at-a-time entry points: every PPR vector within max-abs 1e-6 /
+L1 1e-5 of the oracle at its own sweep count, every BFS level bit-exact."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+MAX_ABS, L1 = 1e-6, 1e-5
+
+
+@pytest.fixture(scope="module")
+def gp():
+    import torch
+
+    import paper_2010_16012_gb300 as gp
+
+    assert torch.cuda.is_available()
+    gp.load()
+    return gp
+
+
+def uneven_graphs():
+    return [gg.rmat(9, 16, seed=41), gg.rmat(11, 8, seed=42, symmetrize=False),
+            gg.rmat(12, 16, seed=43).with_weights(44), gg.star(300), gg.path(77)]
+
+
+def seeds_for(g, k, seed):
+    s = gg.pick_vertices(g, min(k, int((g.out_degree() > 0).sum())), seed=seed)
+    return np.resize(s, k).astype(np.int32)
+
+
+@pytest.mark.parametrize("k", [32, 256])
+def test_ppr_batched_matches_oracle(gp, k):
+    graphs = uneven_graphs()
+    G = [gp.Graph.from_graphgen(g) for g in graphs]
+    B = gp.Batch(G, k_ppr=k)
+    seeds = np.stack([seeds_for(g, k, 50 + i) for i, g in enumerate(graphs)])
+    outs, done, st = B.ppr(seeds, damping=0.85, iters=500, tol=1e-6)
+    assert st["sweeps"] == done.max() and done.min() >= 1
+    rng = np.random.default_rng(0)
+    for i, g in enumerate(graphs):
+        X = outs[i].cpu().numpy()
+        O = oracle.OracleGraph.from_graph(g)
+        for j in sorted(set(rng.choice(k, size=min(k, 12), replace=False).tolist()) | {0, k - 1}):
+            e = np.zeros(g.n)
+            e[seeds[i, j]] = 1.0
+            ref, kk, r, _ = O.pagerank(oracle.PULL, 0.85, iters=int(done[i, j]), personalization=e)
+            err = np.abs(X[:, j].astype(np.float64) - ref)
+            assert err.max() <= MAX_ABS and err.sum() <= L1, (i, j, err.max(), err.sum())
+            # it stopped at the first sweep where the change fell below tol (within FP32 rounding)
+            _, k_exact, _, _ = O.pagerank(oracle.PULL, 0.85, iters=500, tol=1e-6, personalization=e)
+            assert abs(int(done[i, j]) - k_exact) <= 1
+    B.free()
+
+
+@pytest.mark.parametrize("k", [64, 128])
+def test_ppr_batched_matches_serial(gp, k):
+    import torch
+
+    graphs = [gg.rmat(10, 16, seed=61), gg.rmat(8, 16, seed=62)]
+    G = [gp.Graph.from_graphgen(g) for g in graphs]
+    B = gp.Batch(G, k_ppr=k)
+    seeds = np.stack([seeds_for(g, k, 70 + i) for i, g in enumerate(graphs)])
+    outs, done, _ = B.ppr(seeds, iters=500, tol=1e-6)
+    for i, g in enumerate(graphs):
+        for j in (0, 7, k - 1):
+            e = torch.zeros(g.n, device="cuda")
+            e[int(seeds[i, j])] = 1.0
+            x, st = gp.pagerank(G[i], gp.PULL, 0.85, int(done[i, j]), 0.0, personalization=e)
+            err = (outs[i][:, j] - x).abs()
+            assert float(err.max()) <= MAX_ABS, (i, j)
+
+
+def test_ppr_batched_replay_with_new_seeds(gp):
+    graphs = [gg.rmat(9, 8, seed=81), gg.rmat(10, 8, seed=82)]
+    G = [gp.Graph.from_graphgen(g) for g in graphs]
+    B = gp.Batch(G, k_ppr=32)
+    for rep in range(3):
+        seeds = np.stack([seeds_for(g, 32, 90 + 10 * rep + i) for i, g in enumerate(graphs)])
+        outs, done, _ = B.ppr(seeds, iters=300, tol=1e-6)
+        for i, g in enumerate(graphs):
+            O = oracle.OracleGraph.from_graph(g)
+            j = rep * 5
+            e = np.zeros(g.n)
+            e[seeds[i, j]] = 1.0
+            ref, _, _, _ = O.pagerank(oracle.PULL, 0.85, iters=int(done[i, j]), personalization=e)
+            assert np.abs(outs[i][:, j].cpu().numpy() - ref).max() <= MAX_ABS
+
+
+@pytest.mark.parametrize("nsrc", [64, 5])
+def test_msbfs_batched_matches_oracle(gp, nsrc):
+    graphs = uneven_graphs() + [gg.erdos_renyi(2000, 6000, seed=91), gg.empty(3)]
+    G = [gp.Graph.from_graphgen(g) for g in graphs]
+    B = gp.Batch(G, k_ppr=32)
+    srcs = []
+    for i, g in enumerate(graphs):
+        s = gg.pick_vertices(g, nsrc, seed=100 + i, min_out_degree=0)
+        srcs.append(np.resize(s, nsrc))
+    srcs = np.stack(srcs).astype(np.int32)
+    outs, st = B.msbfs(srcs)
+    for i, g in enumerate(graphs):
+        L = outs[i].cpu().numpy()
+        O = oracle.OracleGraph.from_graph(g)
+        for j in range(nsrc):
+            ref, _ = O.bfs(int(srcs[i, j]))
+            assert np.array_equal(L[:, j], ref), (i, j)
+        assert (L[:, nsrc:] == -1).all()
+    # replay through the captured graph with other sources
+    outs2, _ = B.msbfs(srcs[:, ::-1].copy())
+    for i, g in enumerate(graphs):
+        O = oracle.OracleGraph.from_graph(g)
+        ref, _ = O.bfs(int(srcs[i, -1]))
+        assert np.array_equal(outs2[i].cpu().numpy()[:, 0], ref)
+
+
+def test_batched_rejects_bad_input(gp):
+    G = [gp.Graph.from_graphgen(gg.path(10))]
+    with pytest.raises(gp.GpError):
+        gp.Batch(G, k_ppr=48)
+    B = gp.Batch(G, k_ppr=32)
+    with pytest.raises(gp.GpError):
+        B.ppr(np.full((1, 32), 10, dtype=np.int32))
+    with pytest.raises(gp.GpError):
+        B.msbfs(np.full((1, 3), -1, dtype=np.int32))
