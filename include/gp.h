@@ -170,6 +170,31 @@ int gp_graph_set_options(gp_graph *g, const gp_options *opt, void *stream);
 
 int gp_graph_get_options(const gp_graph *g, gp_options *opt);
 
+/* ------------------------------------------------------------------ autotuning */
+
+#define GP_TUNE_PULL 0x1u /* pull_light_max, chunk_edges, pull_hot_slots */
+#define GP_TUNE_PUSH 0x2u /* push_light_max, blocks_per_sm */
+#define GP_TUNE_AUTO 0x4u /* pr_auto_mode: the faster of pull and push for this graph */
+#define GP_TUNE_BFS 0x8u  /* bfs_alpha, bfs_beta */
+#define GP_TUNE_ALL 0xFu
+
+typedef struct gp_tune_result {
+    gp_options best;         /* the options left set on the graph */
+    float pull_ms_per_sweep; /* best measured, 0 if not tuned */
+    float push_ms_per_sweep;
+    float bfs_ms;            /* all given sources, direction-switching */
+    int32_t evaluated;       /* candidates timed */
+} gp_tune_result;
+
+/*
+ * Pick options for this graph by timing candidates on the device (coordinate
+ * descent over small sets, CUDA events on `stream`; a few PageRank sweeps or
+ * the given BFS sources per candidate).  Results never depend on the options,
+ * only speed does.  sources (host int32[nsources]) are needed for GP_TUNE_BFS.
+ * Leaves the best options set on the graph.  Synchronises the stream.
+ */
+int gp_autotune(gp_graph *g, unsigned what, const int32_t *sources, int nsources, gp_tune_result *res, void *stream);
+
 /* ------------------------------------------------------------------ PageRank */
 
 typedef struct gp_pr_stats {

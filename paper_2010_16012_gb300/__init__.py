@@ -22,6 +22,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgp.so")
 
 PUSH, PULL, AUTO = 0, 1, 2
+TUNE_PULL, TUNE_PUSH, TUNE_AUTO, TUNE_BFS, TUNE_ALL = 0x1, 0x2, 0x4, 0x8, 0xF
 UPLOAD_VALIDATE, UPLOAD_SYMMETRIC, UPLOAD_COPY, UPLOAD_NORMALIZE = 0x1, 0x2, 0x4, 0x8
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 BFS_MAX_LEVELS = 512
@@ -71,6 +72,11 @@ class gp_batch_stats(ctypes.Structure):
                 ("blocks", ctypes.c_int32)]
 
 
+class gp_tune_result(ctypes.Structure):
+    _fields_ = [("best", gp_options), ("pull_ms_per_sweep", ctypes.c_float), ("push_ms_per_sweep", ctypes.c_float),
+                ("bfs_ms", ctypes.c_float), ("evaluated", ctypes.c_int32)]
+
+
 class gp_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -106,6 +112,7 @@ SIGNATURES = [
     ("gp_msbfs_batched", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(gp_batch_stats),
                                         _VP]),
     ("gp_pull_sweep_noalloc", ctypes.c_int, [_I64, _I64, _VP, _VP, _VP, _VP, _VP, _F, _VP, _VP, _VP, _VP]),
+    ("gp_autotune", ctypes.c_int, [_VP, _U, _VP, ctypes.c_int, ctypes.POINTER(gp_tune_result), _VP]),
     ("gp_profile_enable", ctypes.c_int, [ctypes.c_int]),
     ("gp_profile_read", ctypes.c_int, [ctypes.POINTER(gp_kernel_time), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
@@ -409,6 +416,74 @@ class Batch:
         _check(load().gp_msbfs_batched(self._h, _ptr(sources), int(nsrc), optr, ctypes.byref(st), _stream_ptr(stream)),
                "gp_msbfs_batched")
         return outs, {"levels": st.levels, "ms": st.ms, "blocks": st.blocks}
+
+
+OPTION_FIELDS = ["pull_light_max", "push_light_max", "chunk_edges", "blocks_per_sm", "poll_interval", "pr_auto_mode",
+                 "bfs_alpha", "bfs_beta", "push_fp64_accum", "pull_hot_slots"]
+
+
+def options_dict(o: gp_options) -> dict:
+    return {f: getattr(o, f) for f in OPTION_FIELDS}
+
+
+def tune_key(info: dict, what: int, device_name: str = "") -> str:
+    """Cache key of a tuning result: the graph's shape statistics, what was tuned
+    and the GPU model."""
+    return "|".join(str(x) for x in (device_name, info["n"], info["m"], info["max_out_degree"], info["max_in_degree"],
+                                     info["isolated"], info["symmetric"], info["weighted"], what))
+
+
+def tune_cache_path(path=None) -> str:
+    """The JSON cache file: `path`, else $GP_TUNE_CACHE, else ~/.cache/gp_tune.json."""
+    return path or os.environ.get("GP_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "gp_tune.json")
+
+
+def tune_cache_load(path) -> dict:
+    import json
+
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def tune_cache_store(path, key: str, entry: dict):
+    import json
+
+    data = tune_cache_load(path)
+    data[key] = entry
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def autotune(g: Graph, what: int = TUNE_ALL, sources=None, cache=None, use_cache: bool = True, stream=None) -> dict:
+    """gp_autotune with a JSON cache keyed by graph statistics and GPU model.
+    Returns {"options": {...}, "cached": bool, ...timings}."""
+    torch = _torch()
+    path = tune_cache_path(cache)
+    key = tune_key(g.info(), what, torch.cuda.get_device_name())
+    if use_cache:
+        hit = tune_cache_load(path).get(key)
+        if hit:
+            g.set_options(stream=stream, **hit["options"])
+            return dict(hit, cached=True)
+    src = None
+    n_src = 0
+    if what & TUNE_BFS:
+        src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32))
+        n_src = int(src.shape[0])
+    res = gp_tune_result()
+    _check(load().gp_autotune(g.handle, int(what), _ptr(src), n_src, ctypes.byref(res), _stream_ptr(stream)),
+           "gp_autotune")
+    entry = {"options": options_dict(res.best), "pull_ms_per_sweep": res.pull_ms_per_sweep,
+             "push_ms_per_sweep": res.push_ms_per_sweep, "bfs_ms": res.bfs_ms, "evaluated": res.evaluated}
+    if use_cache:
+        tune_cache_store(path, key, entry)
+    return dict(entry, cached=False)
 
 
 NOALLOC_MAX_VERTICES = 1 << 20
