@@ -194,7 +194,7 @@ def pick_sources(g, count: int):
 
 
 KERNEL_SOURCE = {"pull_big": "pagerank.cu", "pull_light": "pagerank.cu", "push_scatter": "pagerank.cu",
-                 "push_epilogue": "pagerank.cu", "bfs_topdown": "bfs.cu", "bfs_bottomup": "bfs.cu"}
+                 "push_epilogue": "pagerank.cu", "bfs_persistent": "bfs.cu"}
 
 
 def source_key(cu_name: str) -> str:
@@ -338,15 +338,15 @@ def run_ours(args, dist: Dist):
             bfs_edges += e
             hm.append(e / (tb - ta) / 1e9)
             switches += st["switches"]
-            if work is not None:
-                seen = 0
+            if work is not None:  # one launch per search: the sum of its levels' bytes
+                seen, by = 0, 0
                 fr = st["frontier"] + [0]
                 for L, d in enumerate(st["direction"]):
                     seen += fr[L]
-                    kn, by = bfs_level_bytes(n, d, fr[L], st["examined"][L], n - seen, fr[L + 1])
-                    w = work.setdefault(kn, [0.0, 0])
-                    w[0] += by
-                    w[1] += 1
+                    by += bfs_level_bytes(n, d, fr[L], st["examined"][L], n - seen, fr[L + 1])[1]
+                w = work.setdefault("bfs_persistent", [0.0, 0])
+                w[0] += by
+                w[1] += 1
         parts["bfs_auto"] = {"sources": len(srcs), "ms": bfs_ms, "gteps_total": bfs_edges / bfs_ms / 1e6,
                              "gteps_harmonic_mean": len(hm) / sum(1.0 / max(h, 1e-12) for h in hm),
                              "switches_per_source": switches / max(len(srcs), 1)}

@@ -34,46 +34,6 @@ constexpr int BT_TILE = 1024;       // vertices per block tile
 constexpr int BT_THREADS = 512;     // threads per block of the persistent kernels
 constexpr int BT_BIG = 256;         // in-degree above which a vertex is split into chunks
 constexpr int BT_CHUNK = 256;       // edges per chunk
-constexpr unsigned long long BT_SPIN_LIMIT = 1ull << 24;  // ~2 s of 128 ns sleeps
-
-struct GridSync {
-    unsigned count;
-    unsigned gen;
-    int err;
-    int pad;
-};
-
-// Grid-wide barrier for a cooperative launch.  Returns false if any block gave
-// up waiting (iteration limit) -- every block then leaves its loop.
-__device__ bool grid_sync(GridSync *gs, unsigned nblocks) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned *vgen = &gs->gen;
-        volatile int *verr = &gs->err;
-        const unsigned g0 = *vgen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(&gs->count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(&gs->count, 0u);
-            __threadfence();
-            atomicAdd(&gs->gen, 1u);
-        } else {
-            unsigned long long spins = 0;
-            while (*vgen == g0) {
-                if (*verr || ++spins > BT_SPIN_LIMIT) {
-                    atomicExch(&gs->err, 1);
-                    break;
-                }
-                __nanosleep(128);
-            }
-        }
-        __threadfence();
-        s_ok = *verr == 0;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
 
 struct BGraph {  // per-graph device descriptor
     int64_t n;

@@ -110,13 +110,17 @@ __device__ void flush_counters(const BfsArgs &a, unsigned long long nf, unsigned
     }
 }
 
-__global__ void __launch_bounds__(256) k_bfs_topdown(BfsArgs a) {
+// ------------------------------------------------------------------ level steps (device functions)
+
+// Top-down level: heavy frontier vertices (chunk ids) one warp per chunk, light
+// ones 32 queue entries per warp with a merged edge stream.
+__device__ void bfs_topdown_step(const BfsArgs &a) {
     const int lane = lane_id();
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t h_len = (int64_t)a.cur->h_len, q_len = (int64_t)a.cur->q_len;
+    const int64_t h_len = (int64_t)((volatile BfsCtr *)a.cur)->h_len;
+    const int64_t q_len = (int64_t)((volatile BfsCtr *)a.cur)->q_len;
     unsigned long long nf = 0, mf = 0, mu = 0, ex = 0;
-    // heavy frontier vertices: one warp per chunk of out-edges
     for (int64_t j = warp; j < h_len; j += nwarps) {
         const Chunk ch = a.push_chunks[a.h_cur[j]];
         for (int i0 = 0; i0 < ch.len; i0 += 32) {
@@ -131,7 +135,6 @@ __global__ void __launch_bounds__(256) k_bfs_topdown(BfsArgs a) {
             frontier_append(a, take, w, nf, mf, mu);
         }
     }
-    // light frontier vertices: 32 queue entries per warp, one merged edge stream
     const int64_t ntiles = (q_len + 31) >> 5;
     for (int64_t t = warp; t < ntiles; t += nwarps) {
         const int64_t qi = t * 32 + lane;
@@ -170,7 +173,8 @@ __global__ void __launch_bounds__(256) k_bfs_topdown(BfsArgs a) {
     flush_counters(a, nf, mf, mu, ex);
 }
 
-__global__ void __launch_bounds__(256) k_bfs_bottomup(BfsArgs a) {
+// Bottom-up level: warp per 32-vertex bitmap word, lane per vertex, early exit.
+__device__ void bfs_bottomup_step(const BfsArgs &a) {
     const int lane = lane_id();
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -203,11 +207,11 @@ __global__ void __launch_bounds__(256) k_bfs_bottomup(BfsArgs a) {
     flush_counters(a, nf, mf, mu, ex);
 }
 
-// Frontier queue (+ heavy chunk ids) -> bitmap (bits must be zeroed first).
-__global__ void k_queue_to_bits(const BfsCtr *cur, const int32_t *queue, const int32_t *h, const Chunk *chunks,
-                                uint32_t *bits) {
+// Frontier queue (+ heavy chunk ids) -> bitmap; the bitmap must be zero.
+__device__ void queue_to_bits_step(const BfsCtr *cur, const int32_t *queue, const int32_t *h, const Chunk *chunks,
+                                   uint32_t *bits) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t q_len = (int64_t)cur->q_len, h_len = (int64_t)cur->h_len;
+    const int64_t q_len = (int64_t)((volatile BfsCtr *)cur)->q_len, h_len = (int64_t)((volatile BfsCtr *)cur)->h_len;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < q_len + h_len; i += stride) {
         const int32_t v = i < q_len ? queue[i] : chunks[h[i - q_len]].v;
         atomicOr(bits + (v >> 5), 1u << (v & 31));
@@ -215,11 +219,11 @@ __global__ void k_queue_to_bits(const BfsCtr *cur, const int32_t *queue, const i
 }
 
 // Bitmap -> queue + heavy chunk ids (the counters' q_len/h_len must be zero).
-__global__ void k_bits_to_queue(BfsArgs a) {
+__device__ void bits_to_queue_step(const BfsArgs &a) {
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nwords = (a.n + 31) >> 5;
-    unsigned long long nf = 0, mf = 0, mu = 0;  // already known to the host: discarded
+    unsigned long long nf = 0, mf = 0, mu = 0;  // already counted by the level that made the bitmap
     for (int64_t wd = warp; wd < nwords; wd += nwarps) {
         const uint32_t word = a.bits_cur[wd];
         if (!word) continue;  // uniform across the warp
@@ -229,27 +233,145 @@ __global__ void k_bits_to_queue(BfsArgs a) {
     }
 }
 
-__global__ void k_bfs_init(int64_t n, int32_t *level, int32_t *parent) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        level[v] = -1;
-        if (parent) parent[v] = -1;
-    }
-}
+// ------------------------------------------------------------------ the whole search in one launch
 
-// Seeds the frontier {src} in queue form and its counters.
-__global__ void k_bfs_seed(BfsArgs a, int32_t src) {
-    unsigned long long nf = 0, mf = 0, mu = 0;
-    const bool take = lane_id() == 0;
-    if (take) {
-        a.level[src] = 0;
-        if (a.parent) a.parent[src] = src;
+struct BfsLevelStat {
+    int32_t direction;
+    int32_t pad;
+    int64_t frontier;
+    int64_t examined;
+};
+
+struct BfsSummary {
+    int64_t levels, reached, examined, edges_reached, switches;
+};
+
+struct BfsRun {
+    BfsArgs base;  // graph arrays, level/parent, chunk table
+    int32_t *queue[2];
+    int32_t *hchunk[2];
+    uint32_t *bits[2];
+    BfsCtr *ctr;  // [2]
+    const int8_t *dirs;  // forced directions (device) or nullptr
+    int32_t ndirs;
+    int32_t mode;
+    float alpha, beta;
+    int64_t m;
+    int32_t src;
+    BfsLevelStat *stats;  // [GP_BFS_MAX_LEVELS]
+    BfsSummary *summary;
+    GridSync *sync;
+};
+
+// Every block keeps identical copies of the frontier statistics (read from the
+// counters after each barrier), so all blocks take the same direction decision
+// without a host round trip.
+__global__ void __launch_bounds__(256) k_bfs_persistent(BfsRun R) {
+    const int64_t n = R.base.n;
+    const int64_t gthread = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t nwords = (n + 31) >> 5;
+    for (int64_t v = gthread; v < n; v += nthreads) {
+        R.base.level[v] = -1;
+        if (R.base.parent) R.base.parent[v] = -1;
     }
-    frontier_append(a, take, src, nf, mf, mu);
-    if (take) {
-        a.nxt->nf = nf;
-        a.nxt->mf = mf;
-        a.nxt->mu_dec = mu;
+    if (gthread < 2 * (int64_t)(sizeof(BfsCtr) / sizeof(unsigned long long)))
+        ((unsigned long long *)R.ctr)[gthread] = 0;
+    if (!grid_sync(R.sync, gridDim.x)) return;
+    BfsArgs a = R.base;
+    // frontier 0 = {src}, in queue form, counters in ctr[0]
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        a.nxt = R.ctr;
+        a.queue_next = R.queue[0];
+        a.h_next = R.hchunk[0];
+        unsigned long long nf = 0, mf = 0, mu = 0;
+        const bool take = threadIdx.x == 0;
+        if (take) {
+            a.level[R.src] = 0;
+            if (a.parent) a.parent[R.src] = R.src;
+        }
+        frontier_append(a, take, R.src, nf, mf, mu);
+        if (take) {
+            R.ctr[0].nf = nf;
+            R.ctr[0].mf = mf;
+            R.ctr[0].mu_dec = mu;
+        }
+    }
+    if (!grid_sync(R.sync, gridDim.x)) return;
+    volatile BfsCtr *vc = (volatile BfsCtr *)R.ctr;
+    unsigned long long nf = vc[0].nf, mf = vc[0].mf;
+    long long mu = (long long)R.m - (long long)vc[0].mu_dec;
+    unsigned long long prev_nf = 0;
+    int cur = 0, prev_dir = GP_PUSH, L = 0, switches = 0;
+    bool in_queue = true;
+    long long reached = 1, examined = 0, edges_reached = (long long)mf;
+    while (nf > 0) {
+        int dir;
+        if (R.dirs) {
+            dir = R.dirs[L < R.ndirs ? L : R.ndirs - 1];
+        } else if (R.mode == GP_PUSH || R.mode == GP_PULL) {
+            dir = R.mode;
+        } else if (prev_dir == GP_PUSH) {
+            dir = ((double)mf > (double)(mu > 0 ? mu : 0) / R.alpha) ? GP_PULL : GP_PUSH;
+        } else {
+            dir = ((double)nf < (double)n / R.beta && nf < prev_nf) ? GP_PUSH : GP_PULL;
+        }
+        if (L > 0 && dir != prev_dir) ++switches;
+        const int nxt = cur ^ 1;
+        a.L = L;
+        a.cur = R.ctr + cur;
+        a.nxt = R.ctr + nxt;
+        a.queue_cur = R.queue[cur];
+        a.h_cur = R.hchunk[cur];
+        a.bits_cur = R.bits[cur];
+        a.queue_next = R.queue[nxt];
+        a.h_next = R.hchunk[nxt];
+        a.bits_next = R.bits[nxt];
+        if (dir == GP_PUSH && !in_queue) {
+            BfsArgs c = a;  // the queue form is written in place of the bitmap's slot
+            c.nxt = a.cur;
+            c.queue_next = R.queue[cur];
+            c.h_next = R.hchunk[cur];
+            bits_to_queue_step(c);
+        } else if (dir == GP_PULL && in_queue) {
+            for (int64_t i = gthread; i < nwords; i += nthreads) R.bits[cur][i] = 0u;
+            if (!grid_sync(R.sync, gridDim.x)) return;
+            queue_to_bits_step(R.ctr + cur, R.queue[cur], R.hchunk[cur], a.push_chunks, R.bits[cur]);
+        }
+        if (gthread < (int64_t)(sizeof(BfsCtr) / sizeof(unsigned long long)))
+            ((unsigned long long *)(R.ctr + nxt))[gthread] = 0;
+        if (!grid_sync(R.sync, gridDim.x)) return;
+        if (dir == GP_PUSH) {
+            bfs_topdown_step(a);
+            in_queue = true;
+        } else {
+            bfs_bottomup_step(a);
+            in_queue = false;
+        }
+        if (!grid_sync(R.sync, gridDim.x)) return;
+        const unsigned long long nf2 = vc[nxt].nf, mf2 = vc[nxt].mf, mud = vc[nxt].mu_dec, ex = vc[nxt].examined;
+        if (gthread == 0 && L < GP_BFS_MAX_LEVELS) {
+            R.stats[L].direction = dir;
+            R.stats[L].frontier = (int64_t)nf;
+            R.stats[L].examined = (int64_t)ex;
+        }
+        examined += (long long)ex;
+        reached += (long long)nf2;
+        edges_reached += (long long)mf2;
+        prev_nf = nf;
+        nf = nf2;
+        mf = mf2;
+        mu -= (long long)mud;
+        prev_dir = dir;
+        cur = nxt;
+        ++L;
+    }
+    if (gthread == 0) {
+        R.summary->levels = L;
+        R.summary->reached = reached;
+        R.summary->examined = examined;
+        R.summary->edges_reached = edges_reached;
+        R.summary->switches = switches;
     }
 }
 
@@ -276,7 +398,23 @@ static int ensure_bfs_work(gp_graph *g, cudaStream_t s) {
     BfsCtr *c = nullptr;
     GP_TRY(w.mem.alloc(c, 2, s));
     w.ctr = c;
-    GP_CUDA(cudaMallocHost(&w.ctr_host, 2 * sizeof(BfsCtr)));
+    BfsLevelStat *st = nullptr;
+    GP_TRY(w.mem.alloc(st, GP_BFS_MAX_LEVELS, s));
+    w.stats = st;
+    BfsSummary *sum = nullptr;
+    GP_TRY(w.mem.alloc(sum, 1, s));
+    w.summary = sum;
+    GridSync *sync = nullptr;
+    GP_TRY(w.mem.alloc(sync, 1, s));
+    w.sync = sync;
+    int8_t *d = nullptr;
+    GP_TRY(w.mem.alloc(d, GP_BFS_MAX_LEVELS, s));
+    w.dirs = d;
+    int per_sm = 0;
+    GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs_persistent, 256, 0));
+    if (per_sm < 1) return set_error(GP_ERR_UNSUPPORTED, "BFS kernel does not fit on an SM");
+    w.grid = per_sm * g->num_sms;
+    GP_CUDA(cudaMallocHost(&w.ctr_host, sizeof(BfsSummary) + GP_BFS_MAX_LEVELS * sizeof(BfsLevelStat) + sizeof(GridSync)));
     w.ready = true;
     return GP_OK;
 }
@@ -307,128 +445,75 @@ static int bfs_run(const gp_graph *gc, int32_t src, int mode, const int8_t *dirs
         if (!w.parent_dev) GP_TRY(w.mem.alloc(w.parent_dev, (size_t)n, s));
         parent = w.parent_dev;
     }
-    BfsCtr *ctr = (BfsCtr *)w.ctr;
-    BfsCtr *hctr = (BfsCtr *)w.ctr_host;
-    const int gb = grid_blocks(g, 256);
-    const int ib = (int)std::max<int64_t>(1, std::min<int64_t>(gb, (n + 255) / 256));
-    const int64_t nwords = (n + 31) / 32;
-    const int wb = (int)std::max<int64_t>(1, std::min<int64_t>(gb, (nwords + 7) / 8));
-
-    BfsArgs a;
-    memset(&a, 0, sizeof(a));
-    a.n = n;
-    a.csr_off = g->csr_off;
-    a.csc_off = g->csc_off;
-    a.csr_idx = g->csr_idx;
-    a.csc_idx = g->csc_idx;
-    a.push_rank = g->push_bins.rank;
-    a.push_cstart = g->push_bins.cstart;
-    a.push_chunks = g->push_bins.chunks;
-    a.level = level;
-    a.parent = parent;
-
-    GP_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(BfsCtr), s));
-    GP_LAUNCH("bfs_init", s, (k_bfs_init<<<ib, 256, 0, s>>>(n, level, parent)));
-    // frontier 0 = {src} in queue form, counters in ctr[0]
-    int cur = 0;
-    a.cur = ctr + 1;
-    a.nxt = ctr + 0;
-    a.queue_next = w.queue[0];
-    a.h_next = w.hchunk[0];
-    GP_LAUNCH("bfs_seed", s, (k_bfs_seed<<<1, 32, 0, s>>>(a, src)));
-    GP_TRY(check_launch("bfs seed"));
-    GP_CUDA(cudaMemcpyAsync(hctr, ctr, sizeof(BfsCtr), cudaMemcpyDeviceToHost, s));
-    GP_CUDA(cudaStreamSynchronize(s));
-    unsigned long long nf = hctr[0].nf, mf = hctr[0].mf;
-    long long mu = (long long)g->m - (long long)hctr[0].mu_dec;
-    bool in_queue = true;  // frontier form
-    int prev_dir = GP_PUSH;
-    unsigned long long prev_nf = 0;
-    int L = 0;
-    int64_t reached = 1, examined = 0, edges_reached = (int64_t)mf;
-    int switches = 0;
-    const float alpha = g->opt.bfs_alpha, beta = g->opt.bfs_beta;
-    while (nf > 0) {
-        int dir;
-        if (dirs) {
-            dir = dirs[std::min(L, ndirs - 1)];
-        } else if (mode == GP_PUSH || mode == GP_PULL) {
-            dir = mode;
-        } else if (prev_dir == GP_PUSH) {
-            dir = ((double)mf > (double)std::max(mu, 0LL) / alpha) ? GP_PULL : GP_PUSH;
-        } else {
-            dir = ((double)nf < (double)n / beta && nf < prev_nf) ? GP_PUSH : GP_PULL;
-        }
-        if (L > 0 && dir != prev_dir) ++switches;
-        const int nxt = cur ^ 1;
-        a.L = L;
-        a.cur = ctr + cur;
-        a.nxt = ctr + nxt;
-        a.queue_cur = w.queue[cur];
-        a.h_cur = w.hchunk[cur];
-        a.bits_cur = w.bits[cur];
-        a.queue_next = w.queue[nxt];
-        a.h_next = w.hchunk[nxt];
-        a.bits_next = w.bits[nxt];
-        if (dir == GP_PUSH && !in_queue) {
-            BfsArgs conv = a;  // the queue form is written in place of the bitmap's slot
-            conv.nxt = a.cur;
-            conv.queue_next = w.queue[cur];
-            conv.h_next = w.hchunk[cur];
-            GP_LAUNCH("bfs_bits_to_queue", s, (k_bits_to_queue<<<wb, 256, 0, s>>>(conv)));
-            GP_TRY(check_launch("bits_to_queue"));
-        } else if (dir == GP_PULL && in_queue) {
-            GP_CUDA(cudaMemsetAsync(w.bits[cur], 0, (size_t)nwords * sizeof(uint32_t), s));
-            GP_LAUNCH("bfs_queue_to_bits", s,
-                      (k_queue_to_bits<<<ib, 256, 0, s>>>(ctr + cur, w.queue[cur], w.hchunk[cur], g->push_bins.chunks,
-                                                          w.bits[cur])));
-            GP_TRY(check_launch("queue_to_bits"));
-        }
-        GP_CUDA(cudaMemsetAsync(ctr + nxt, 0, sizeof(BfsCtr), s));
-        if (dir == GP_PUSH) {
-            GP_LAUNCH("bfs_topdown", s, (k_bfs_topdown<<<gb, 256, 0, s>>>(a)));
-            in_queue = true;
-        } else {
-            GP_LAUNCH("bfs_bottomup", s, (k_bfs_bottomup<<<wb, 256, 0, s>>>(a)));
-            in_queue = false;
-        }
-        GP_TRY(check_launch("bfs level"));
-        GP_CUDA(cudaMemcpyAsync(hctr + nxt, ctr + nxt, sizeof(BfsCtr), cudaMemcpyDeviceToHost, s));
-        GP_CUDA(cudaStreamSynchronize(s));
-        const BfsCtr &c = hctr[nxt];
-        if (stats && L < GP_BFS_MAX_LEVELS) {
-            stats->direction[L] = (int8_t)dir;
-            stats->frontier[L] = (int64_t)nf;
-            stats->examined[L] = (int64_t)c.examined;
-        }
-        examined += (int64_t)c.examined;
-        reached += (int64_t)c.nf;
-        edges_reached += (int64_t)c.mf;
-        prev_nf = nf;
-        nf = c.nf;
-        mf = c.mf;
-        mu -= (long long)c.mu_dec;
-        prev_dir = dir;
-        cur = nxt;
-        ++L;
+    BfsRun R;
+    memset(&R, 0, sizeof(R));
+    R.base.n = n;
+    R.base.csr_off = g->csr_off;
+    R.base.csc_off = g->csc_off;
+    R.base.csr_idx = g->csr_idx;
+    R.base.csc_idx = g->csc_idx;
+    R.base.push_rank = g->push_bins.rank;
+    R.base.push_cstart = g->push_bins.cstart;
+    R.base.push_chunks = g->push_bins.chunks;
+    R.base.level = level;
+    R.base.parent = parent;
+    for (int i = 0; i < 2; ++i) {
+        R.queue[i] = w.queue[i];
+        R.hchunk[i] = w.hchunk[i];
+        R.bits[i] = w.bits[i];
+    }
+    R.ctr = (BfsCtr *)w.ctr;
+    R.mode = mode;
+    R.alpha = g->opt.bfs_alpha;
+    R.beta = g->opt.bfs_beta;
+    R.m = g->m;
+    R.src = src;
+    R.stats = (BfsLevelStat *)w.stats;
+    R.summary = (BfsSummary *)w.summary;
+    R.sync = (GridSync *)w.sync;
+    if (dirs) {
+        const int nd = std::min(ndirs, GP_BFS_MAX_LEVELS);
+        GP_CUDA(cudaMemcpyAsync(w.dirs, dirs, nd, cudaMemcpyHostToDevice, s));
+        R.dirs = (const int8_t *)w.dirs;
+        R.ndirs = nd;
+    }
+    GP_CUDA(cudaMemsetAsync(w.sync, 0, sizeof(GridSync), s));
+    {
+        ProfScope ps("bfs_persistent", s);
+        void *args[] = {&R};
+        GP_CUDA(cudaLaunchCooperativeKernel((const void *)k_bfs_persistent, dim3((unsigned)w.grid), dim3(256), args, 0, s));
     }
     if (!lvl_dev) GP_CUDA(cudaMemcpyAsync(level_out, level, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     if (!par_dev) GP_CUDA(cudaMemcpyAsync(parent_out, parent, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    char *h = (char *)w.ctr_host;
+    BfsSummary *hs = (BfsSummary *)h;
+    BfsLevelStat *hl = (BfsLevelStat *)(h + sizeof(BfsSummary));
+    GridSync *hsync = (GridSync *)(h + sizeof(BfsSummary) + GP_BFS_MAX_LEVELS * sizeof(BfsLevelStat));
+    GP_CUDA(cudaMemcpyAsync(hsync, w.sync, sizeof(GridSync), cudaMemcpyDeviceToHost, s));
     if (stats) {
+        GP_CUDA(cudaMemcpyAsync(hs, w.summary, sizeof(BfsSummary), cudaMemcpyDeviceToHost, s));
+        GP_CUDA(cudaMemcpyAsync(hl, w.stats, GP_BFS_MAX_LEVELS * sizeof(BfsLevelStat), cudaMemcpyDeviceToHost, s));
         GP_CUDA(cudaEventRecord(ev1, s));
         GP_CUDA(cudaEventSynchronize(ev1));
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev0, ev1);
         cudaEventDestroy(ev0);
         cudaEventDestroy(ev1);
-        stats->levels = L;
-        stats->switches = switches;
-        stats->reached = reached;
-        stats->edges_examined = examined;
-        stats->edges_reached = edges_reached;
+        stats->levels = (int32_t)hs->levels;
+        stats->switches = (int32_t)hs->switches;
+        stats->reached = hs->reached;
+        stats->edges_examined = hs->examined;
+        stats->edges_reached = hs->edges_reached;
         stats->ms = ms;
+        const int L = (int)std::min<int64_t>(hs->levels, GP_BFS_MAX_LEVELS);
+        for (int i = 0; i < L; ++i) {
+            stats->direction[i] = (int8_t)hl[i].direction;
+            stats->frontier[i] = hl[i].frontier;
+            stats->examined[i] = hl[i].examined;
+        }
     }
-    if (!lvl_dev || !par_dev) GP_CUDA(cudaStreamSynchronize(s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    if (hsync->err) return set_error(GP_ERR_TIMEOUT, "BFS: a grid barrier wait ran out");
     return GP_OK;
 }
 

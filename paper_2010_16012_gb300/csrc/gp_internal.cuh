@@ -154,7 +154,12 @@ struct BfsWork {
     uint32_t *bits[2] = {nullptr, nullptr};  // frontier bitmaps
     int32_t *level_dev = nullptr, *parent_dev = nullptr;  // when outputs are host memory
     void *ctr = nullptr;                     // device counters
-    void *ctr_host = nullptr;                // pinned mirror
+    void *ctr_host = nullptr;                // pinned mirror of the summary, level stats and barrier word
+    void *stats = nullptr;                   // per-level statistics (device)
+    void *summary = nullptr;                 // search summary (device)
+    void *sync = nullptr;                    // grid barrier word
+    int8_t *dirs = nullptr;                  // forced directions (device copy)
+    int grid = 0;                            // blocks of the cooperative launch
     Arena mem;
 };
 
@@ -235,6 +240,51 @@ __device__ __forceinline__ T block_sum(T v, T *smem /* >= 32 entries */) {
         r = warp_sum(r);
     }
     return r;
+}
+
+// ------------------------------------------------------------------ grid barrier
+
+// Grid-wide barrier for cooperative launches (all blocks co-resident).  The
+// spin-wait has an iteration limit: a block that gives up sets `err`, every
+// other waiting block sees it and gives up too, and all of them return false so
+// the kernel can return; the host then reports GP_ERR_TIMEOUT.
+struct GridSync {
+    unsigned count;
+    unsigned gen;
+    int err;
+    int pad;
+};
+
+constexpr unsigned long long GRID_SPIN_LIMIT = 1ull << 24;  // ~2 s of 128 ns sleeps
+
+__device__ __forceinline__ bool grid_sync(GridSync *gs, unsigned nblocks) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &gs->gen;
+        volatile int *verr = &gs->err;
+        const unsigned g0 = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&gs->count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&gs->count, 0u);
+            __threadfence();
+            atomicAdd(&gs->gen, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*vgen == g0) {
+                if (*verr || ++spins > GRID_SPIN_LIMIT) {
+                    atomicExch(&gs->err, 1);
+                    break;
+                }
+                __nanosleep(128);
+            }
+        }
+        __threadfence();
+        s_ok = *verr == 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
 }
 
 }  // namespace gp
