@@ -158,7 +158,10 @@ typedef struct gp_options {
                                  atomics (default; ranks stay FP32), 0 = FP32 atomics */
     int32_t pull_hot_slots;   /* pull PageRank: contributions of this many highest out-degree
                                  vertices are served from shared memory (0 = off, <= 49152) */
-    int32_t reserved[6];
+    int32_t push_hot_slots;   /* push PageRank: updates to this many highest in-degree vertices are
+                                 summed in shared memory per block, then flushed with one atomic
+                                 per vertex and block (0 = off, <= 49152) */
+    int32_t reserved[5];
 } gp_options;
 
 /* Fill *opt with the built-in defaults. */
@@ -173,7 +176,7 @@ int gp_graph_get_options(const gp_graph *g, gp_options *opt);
 /* ------------------------------------------------------------------ autotuning */
 
 #define GP_TUNE_PULL 0x1u /* pull_light_max, chunk_edges, pull_hot_slots */
-#define GP_TUNE_PUSH 0x2u /* push_light_max, blocks_per_sm */
+#define GP_TUNE_PUSH 0x2u /* push_light_max, blocks_per_sm, push_hot_slots */
 #define GP_TUNE_AUTO 0x4u /* pr_auto_mode: the faster of pull and push for this graph */
 #define GP_TUNE_BFS 0x8u  /* bfs_alpha, bfs_beta */
 #define GP_TUNE_ALL 0xFu

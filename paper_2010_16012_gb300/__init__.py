@@ -43,7 +43,7 @@ class gp_options(ctypes.Structure):
                 ("poll_interval", ctypes.c_int32), ("pr_auto_mode", ctypes.c_int32),
                 ("bfs_alpha", ctypes.c_float), ("bfs_beta", ctypes.c_float),
                 ("push_fp64_accum", ctypes.c_int32), ("pull_hot_slots", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("push_hot_slots", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class gp_graph_info(ctypes.Structure):
@@ -419,7 +419,7 @@ class Batch:
 
 
 OPTION_FIELDS = ["pull_light_max", "push_light_max", "chunk_edges", "blocks_per_sm", "poll_interval", "pr_auto_mode",
-                 "bfs_alpha", "bfs_beta", "push_fp64_accum", "pull_hot_slots"]
+                 "bfs_alpha", "bfs_beta", "push_fp64_accum", "pull_hot_slots", "push_hot_slots"]
 
 
 def options_dict(o: gp_options) -> dict:

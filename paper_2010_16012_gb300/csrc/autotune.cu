@@ -5,7 +5,7 @@
 // CUDA events on the caller's stream:
 //   pull PageRank: pull_light_max, then chunk_edges, then pull_hot_slots
 //                  (a few sweeps of gp_pagerank(GP_PULL) per candidate);
-//   push PageRank: push_light_max, then blocks_per_sm;
+//   push PageRank: push_light_max, then blocks_per_sm, then push_hot_slots;
 //   AUTO:          pr_auto_mode = whichever of pull and push sweeps faster
 //                  (the per-graph push/pull choice of the Generic-Switch idea, Section 5);
 //   BFS switch:    bfs_alpha, then bfs_beta (gp_bfs(GP_AUTO) from the given sources).
@@ -122,7 +122,9 @@ extern "C" int gp_autotune(gp_graph *g, unsigned what, const int32_t *sources, i
         st = push(push_ms);
         ++evaluated;
         if (st == GP_OK) st = try_values<int32_t>(g, best, push_ms, &gp_options::push_light_max, {8, 16, 32, 64}, s, push, evaluated);
-        if (st == GP_OK) st = try_values<int32_t>(g, best, push_ms, &gp_options::blocks_per_sm, {2, 4, 8}, s, push, evaluated);
+        if (st == GP_OK) st = try_values<int32_t>(g, best, push_ms, &gp_options::blocks_per_sm, {4, 8, 12}, s, push, evaluated);
+        if (st == GP_OK)
+            st = try_values<int32_t>(g, best, push_ms, &gp_options::push_hot_slots, {0, 8192, 16384, 24576}, s, push, evaluated);
     }
     if (st == GP_OK && (what & GP_TUNE_AUTO)) {
         if (!(what & GP_TUNE_PULL)) st = pull(pull_ms);

@@ -112,7 +112,9 @@ __device__ void flush_counters(const BfsArgs &a, unsigned long long nf, unsigned
 
 // ------------------------------------------------------------------ level steps (device functions)
 
-// Top-down level: heavy frontier vertices (chunk ids) one warp per chunk, light
+constexpr int TD_SPLIT = 4;
+
+// Top-down level: heavy frontier vertices (chunk ids) split over warps, light
 // ones 32 queue entries per warp with a merged edge stream.
 __device__ void bfs_topdown_step(const BfsArgs &a) {
     const int lane = lane_id();
@@ -121,13 +123,17 @@ __device__ void bfs_topdown_step(const BfsArgs &a) {
     const int64_t h_len = (int64_t)((volatile BfsCtr *)a.cur)->h_len;
     const int64_t q_len = (int64_t)((volatile BfsCtr *)a.cur)->q_len;
     unsigned long long nf = 0, mf = 0, mu = 0, ex = 0;
-    for (int64_t j = warp; j < h_len; j += nwarps) {
-        const Chunk ch = a.push_chunks[a.h_cur[j]];
-        for (int i0 = 0; i0 < ch.len; i0 += 32) {
+    // each heavy chunk is split TD_SPLIT ways so a frontier of a few hubs still spreads over many warps
+    for (int64_t j = warp; j < h_len * TD_SPLIT; j += nwarps) {
+        const Chunk ch = a.push_chunks[a.h_cur[j / TD_SPLIT]];
+        const int part = (int)(j % TD_SPLIT);
+        const int plen = (ch.len + TD_SPLIT - 1) / TD_SPLIT;
+        const int lo = part * plen, hi = min(ch.len, lo + plen);
+        for (int i0 = lo; i0 < hi; i0 += 32) {
             const int i = i0 + lane;
             bool take = false;
             int32_t w = 0;
-            if (i < ch.len) {
+            if (i < hi) {
                 w = __ldg(a.csr_idx + ch.beg + i);
                 take = td_claim(a, w, ch.v);
                 ++ex;
@@ -251,7 +257,7 @@ struct BfsRun {
     int32_t *queue[2];
     int32_t *hchunk[2];
     uint32_t *bits[2];
-    BfsCtr *ctr;  // [2]
+    BfsCtr *ctr;  // [3], a ring
     const int8_t *dirs;  // forced directions (device) or nullptr
     int32_t ndirs;
     int32_t mode;
@@ -263,10 +269,14 @@ struct BfsRun {
     GridSync *sync;
 };
 
+// 1024-thread blocks: fewer blocks arrive at each grid barrier (one global
+// counter), which is what a level's fixed cost is made of.
+constexpr int BFS_THREADS = 1024;
+
 // Every block keeps identical copies of the frontier statistics (read from the
 // counters after each barrier), so all blocks take the same direction decision
 // without a host round trip.
-__global__ void __launch_bounds__(256) k_bfs_persistent(BfsRun R) {
+__global__ void __launch_bounds__(BFS_THREADS) k_bfs_persistent(BfsRun R) {
     const int64_t n = R.base.n;
     const int64_t gthread = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
@@ -275,8 +285,9 @@ __global__ void __launch_bounds__(256) k_bfs_persistent(BfsRun R) {
         R.base.level[v] = -1;
         if (R.base.parent) R.base.parent[v] = -1;
     }
-    if (gthread < 2 * (int64_t)(sizeof(BfsCtr) / sizeof(unsigned long long)))
+    if (gthread < 3 * (int64_t)(sizeof(BfsCtr) / sizeof(unsigned long long)))
         ((unsigned long long *)R.ctr)[gthread] = 0;
+    for (int64_t i = gthread; i < nwords; i += nthreads) R.bits[0][i] = 0u;
     if (!grid_sync(R.sync, gridDim.x)) return;
     BfsArgs a = R.base;
     // frontier 0 = {src}, in queue form, counters in ctr[0]
@@ -305,6 +316,12 @@ __global__ void __launch_bounds__(256) k_bfs_persistent(BfsRun R) {
     int cur = 0, prev_dir = GP_PUSH, L = 0, switches = 0;
     bool in_queue = true;
     long long reached = 1, examined = 0, edges_reached = (long long)mf;
+    constexpr int CW = (int)(sizeof(BfsCtr) / sizeof(unsigned long long));
+    // Counters form a ring of three: level L reads slot L%3 (its frontier) and
+    // fills slot (L+1)%3; slot (L+2)%3, last used by level L-1, is zeroed during
+    // level L's step for level L+1, so no barrier is spent on clearing it.
+    // Bitmaps: bits[b] is the next level's bitmap slot; the top-down step clears
+    // the other slot while it runs, so a switch to bottom-up finds it zero.
     while (nf > 0) {
         int dir;
         if (R.dirs) {
@@ -317,32 +334,33 @@ __global__ void __launch_bounds__(256) k_bfs_persistent(BfsRun R) {
             dir = ((double)nf < (double)n / R.beta && nf < prev_nf) ? GP_PUSH : GP_PULL;
         }
         if (L > 0 && dir != prev_dir) ++switches;
-        const int nxt = cur ^ 1;
+        const int nxt = (cur + 1) % 3, spare = (cur + 2) % 3;
+        const int bc = L & 1, bn = bc ^ 1;  // bitmap slots: current frontier, next frontier
         a.L = L;
         a.cur = R.ctr + cur;
         a.nxt = R.ctr + nxt;
-        a.queue_cur = R.queue[cur];
-        a.h_cur = R.hchunk[cur];
-        a.bits_cur = R.bits[cur];
-        a.queue_next = R.queue[nxt];
-        a.h_next = R.hchunk[nxt];
-        a.bits_next = R.bits[nxt];
+        a.queue_cur = R.queue[L & 1];
+        a.h_cur = R.hchunk[L & 1];
+        a.bits_cur = R.bits[bc];
+        a.queue_next = R.queue[bn];
+        a.h_next = R.hchunk[bn];
+        a.bits_next = R.bits[bn];
         if (dir == GP_PUSH && !in_queue) {
-            BfsArgs c = a;  // the queue form is written in place of the bitmap's slot
+            BfsArgs c = a;  // the queue form of the current frontier goes to its own slot
             c.nxt = a.cur;
-            c.queue_next = R.queue[cur];
-            c.h_next = R.hchunk[cur];
+            c.queue_next = R.queue[L & 1];
+            c.h_next = R.hchunk[L & 1];
             bits_to_queue_step(c);
-        } else if (dir == GP_PULL && in_queue) {
-            for (int64_t i = gthread; i < nwords; i += nthreads) R.bits[cur][i] = 0u;
             if (!grid_sync(R.sync, gridDim.x)) return;
-            queue_to_bits_step(R.ctr + cur, R.queue[cur], R.hchunk[cur], a.push_chunks, R.bits[cur]);
+        } else if (dir == GP_PULL && in_queue) {
+            queue_to_bits_step(R.ctr + cur, R.queue[L & 1], R.hchunk[L & 1], a.push_chunks, R.bits[bc]);
+            if (!grid_sync(R.sync, gridDim.x)) return;
         }
-        if (gthread < (int64_t)(sizeof(BfsCtr) / sizeof(unsigned long long)))
-            ((unsigned long long *)(R.ctr + nxt))[gthread] = 0;
-        if (!grid_sync(R.sync, gridDim.x)) return;
+        if (gthread < CW) ((unsigned long long *)(R.ctr + spare))[gthread] = 0;
         if (dir == GP_PUSH) {
             bfs_topdown_step(a);
+            // clear the next level's bitmap slot in case it switches to bottom-up
+            for (int64_t i = gthread; i < nwords; i += nthreads) R.bits[bn][i] = 0u;
             in_queue = true;
         } else {
             bfs_bottomup_step(a);
@@ -396,7 +414,7 @@ static int ensure_bfs_work(gp_graph *g, cudaStream_t s) {
         GP_TRY(w.mem.alloc(w.bits[i], words, s));
     }
     BfsCtr *c = nullptr;
-    GP_TRY(w.mem.alloc(c, 2, s));
+    GP_TRY(w.mem.alloc(c, 3, s));
     w.ctr = c;
     BfsLevelStat *st = nullptr;
     GP_TRY(w.mem.alloc(st, GP_BFS_MAX_LEVELS, s));
@@ -411,7 +429,7 @@ static int ensure_bfs_work(gp_graph *g, cudaStream_t s) {
     GP_TRY(w.mem.alloc(d, GP_BFS_MAX_LEVELS, s));
     w.dirs = d;
     int per_sm = 0;
-    GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs_persistent, 256, 0));
+    GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs_persistent, BFS_THREADS, 0));
     if (per_sm < 1) return set_error(GP_ERR_UNSUPPORTED, "BFS kernel does not fit on an SM");
     w.grid = per_sm * g->num_sms;
     GP_CUDA(cudaMallocHost(&w.ctr_host, sizeof(BfsSummary) + GP_BFS_MAX_LEVELS * sizeof(BfsLevelStat) + sizeof(GridSync)));
@@ -481,7 +499,8 @@ static int bfs_run(const gp_graph *gc, int32_t src, int mode, const int8_t *dirs
     {
         ProfScope ps("bfs_persistent", s);
         void *args[] = {&R};
-        GP_CUDA(cudaLaunchCooperativeKernel((const void *)k_bfs_persistent, dim3((unsigned)w.grid), dim3(256), args, 0, s));
+        GP_CUDA(cudaLaunchCooperativeKernel((const void *)k_bfs_persistent, dim3((unsigned)w.grid), dim3(BFS_THREADS), args,
+                                            0, s));
     }
     if (!lvl_dev) GP_CUDA(cudaMemcpyAsync(level_out, level, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     if (!par_dev) GP_CUDA(cudaMemcpyAsync(parent_out, parent, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));

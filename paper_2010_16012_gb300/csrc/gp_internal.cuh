@@ -179,6 +179,7 @@ struct gp_graph {
     gp::BigBins pull_bins;  // by in-degree (CSC)
     gp::BigBins push_bins;  // by out-degree (CSR)
     gp::HotSet pull_hot;    // shared-memory contribution cache of the pull sweep
+    gp::HotSet push_hot;    // shared-memory accumulators of the push scatter
     gp::PrWork pr;
     gp::BfsWork bfs;
     gp::Arena mem;          // copies of the arrays and degree data
@@ -190,6 +191,7 @@ namespace gp {
 int build_bins(gp_graph *g, BigBins &b, const int64_t *off, int32_t light_max, int32_t chunk_edges,
                cudaStream_t s);
 int build_pull_hot(gp_graph *g, int32_t slots, cudaStream_t s);
+int build_push_hot(gp_graph *g, int32_t slots, cudaStream_t s);
 int select_by_degree(const int64_t *off, int64_t n, int64_t lo, int64_t hi, Arena &mem, int32_t *&list,
                      int64_t &count, int64_t cap, int32_t *rank, cudaStream_t s);
 int grid_blocks(const gp_graph *g, int threads_per_block);

@@ -73,6 +73,7 @@ struct PrArgs {
     float *chunk_part;
     double *acc64;  // FP64 push accumulator (or nullptr)
     const float *c_hot;  // hot contributions (pull, HOT kernels)
+    const int32_t *hot_id;  // hot vertices (push HOT kernels)
     int64_t nhot;
     PrStatus *status;
     int32_t split_blocks;  // pull: light-tile blocks; push: big-chunk blocks
@@ -360,88 +361,111 @@ __global__ void k_hot_gather(const int32_t *hot_id, int64_t nhot, const float *c
 // Accumulator of the scattered updates: FP32 (the paper's float atomics) or
 // FP64 (same atomic count; the order-dependent rounding of FP32 atomics at hubs
 // otherwise leaves an L1 residual floor above 1e-7 on graphs with 4M vertices).
-template <bool W, class T>
-__global__ void __launch_bounds__(256) k_push_scatter(PrArgs a) {
+// HOT: the partition-awareness of the paper's Section 5 recast for a GPU block --
+// updates to the H most updated vertices (encoded in the index array) are
+// summed in the block's shared memory with shared-memory atomics and flushed
+// once per block; only the other updates use global atomics.
+template <class T, bool HOT>
+__device__ __forceinline__ void scatter_add(T *y, float *sh, int32_t dst, T val) {
+    if (HOT && dst < 0)
+        atomicAdd(sh + (dst & 0x7fffffff), (float)val);
+    else
+        atomicAdd(y + dst, val);
+}
+
+template <bool W, class T, bool HOT>
+__global__ void __launch_bounds__(1024) k_push_scatter(PrArgs a) {
+    extern __shared__ float sh_acc[];
     if (pr_gate(a, a.k)) return;
+    if (HOT) {
+        for (int64_t i = threadIdx.x; i < a.nhot; i += blockDim.x) sh_acc[i] = 0.f;
+        __syncthreads();
+    }
     const int lane = lane_id();
     const int32_t *__restrict__ idx = a.idx;
     const float *__restrict__ wv = a.w;
     T *y = sizeof(T) == 8 ? (T *)a.acc64 : (T *)a.y;
-    if ((int)blockIdx.x < a.split_blocks) {
-        const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        const int64_t nwarps = ((int64_t)a.split_blocks * blockDim.x) >> 5;
-        for (int64_t j = warp; j < a.nchunks; j += nwarps) {
-            const Chunk ch = a.chunks[j];
-            const float cu = a.d * __ldg(a.c + ch.v);
-            const int32_t *ip = idx + ch.beg;
-            const float *wp = W ? wv + ch.beg : nullptr;
-            int i = lane;
-            for (; i + 96 < ch.len; i += 128) {
-                const int v0 = __ldg(ip + i), v1 = __ldg(ip + i + 32), v2 = __ldg(ip + i + 64), v3 = __ldg(ip + i + 96);
-                atomicAdd(y + v0, (T)(W ? cu * __ldg(wp + i) : cu));
-                atomicAdd(y + v1, (T)(W ? cu * __ldg(wp + i + 32) : cu));
-                atomicAdd(y + v2, (T)(W ? cu * __ldg(wp + i + 64) : cu));
-                atomicAdd(y + v3, (T)(W ? cu * __ldg(wp + i + 96) : cu));
-            }
-            for (; i < ch.len; i += 32) atomicAdd(y + __ldg(ip + i), (T)(W ? cu * __ldg(wp + i) : cu));
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // big sources: one warp per chunk of out-edges
+    for (int64_t j = warp; j < a.nchunks; j += nwarps) {
+        const Chunk ch = a.chunks[j];
+        const float cu = a.d * __ldg(a.c + ch.v);
+        const int32_t *ip = idx + ch.beg;
+        const float *wp = W ? wv + ch.beg : nullptr;
+        int i = lane;
+        for (; i + 96 < ch.len; i += 128) {
+            const int v0 = __ldg(ip + i), v1 = __ldg(ip + i + 32), v2 = __ldg(ip + i + 64), v3 = __ldg(ip + i + 96);
+            scatter_add<T, HOT>(y, sh_acc, v0, (T)(W ? cu * __ldg(wp + i) : cu));
+            scatter_add<T, HOT>(y, sh_acc, v1, (T)(W ? cu * __ldg(wp + i + 32) : cu));
+            scatter_add<T, HOT>(y, sh_acc, v2, (T)(W ? cu * __ldg(wp + i + 64) : cu));
+            scatter_add<T, HOT>(y, sh_acc, v3, (T)(W ? cu * __ldg(wp + i + 96) : cu));
         }
-    } else {
-        __shared__ T agg[256];
-        const int64_t n = a.n;
-        const int64_t warp = ((int64_t)(blockIdx.x - a.split_blocks) * blockDim.x + threadIdx.x) >> 5;
-        const int64_t nwarps = ((int64_t)(gridDim.x - a.split_blocks) * blockDim.x) >> 5;
-        const int64_t ntiles = (n + 31) >> 5;
-        for (int64_t t = warp; t < ntiles; t += nwarps) {
-            const int64_t u = t * 32 + lane;
-            int64_t b = 0, e = 0;
-            float cu = 0.f;
-            if (u < n) {
-                b = a.off[u];
-                e = a.off[u + 1];
-            }
-            const int64_t dd = e - b;
-            const bool big = dd > a.light_max;
-            const int deg = big ? 0 : (int)dd;
-            if (deg > 0) cu = a.d * __ldg(a.c + u);
-            const int incl = warp_incl_scan(deg);
-            const int excl = incl - deg;
-            const int E = __shfl_sync(FULL, incl, 31);
-            for (int base = 0; base < E; base += 32) {
-                const int eid = base + lane;
-                int k = 0;
+        for (; i < ch.len; i += 32) scatter_add<T, HOT>(y, sh_acc, __ldg(ip + i), (T)(W ? cu * __ldg(wp + i) : cu));
+    }
+    // light sources: 32 consecutive sources per warp, one merged edge stream
+    __shared__ T agg[1024];
+    const int64_t n = a.n;
+    const int64_t ntiles = (n + 31) >> 5;
+    for (int64_t t = warp; t < ntiles; t += nwarps) {
+        const int64_t u = t * 32 + lane;
+        int64_t b = 0, e = 0;
+        float cu = 0.f;
+        if (u < n) {
+            b = a.off[u];
+            e = a.off[u + 1];
+        }
+        const int64_t dd = e - b;
+        const bool big = dd > a.light_max;
+        const int deg = big ? 0 : (int)dd;
+        if (deg > 0) cu = a.d * __ldg(a.c + u);
+        const int incl = warp_incl_scan(deg);
+        const int excl = incl - deg;
+        const int E = __shfl_sync(FULL, incl, 31);
+        for (int base = 0; base < E; base += 32) {
+            const int eid = base + lane;
+            int k = 0;
 #pragma unroll
-                for (int s = 16; s > 0; s >>= 1) {
-                    const int ex = __shfl_sync(FULL, excl, k + s);
-                    if (ex <= eid) k += s;
-                }
-                const int64_t kb = __shfl_sync(FULL, b, k);
-                const int kex = __shfl_sync(FULL, excl, k);
-                const float ck = __shfl_sync(FULL, cu, k);
-                int32_t dst = -1 - lane;  // distinct dummy keys for idle lanes
-                T val = 0;
-                if (eid < E) {
-                    const int64_t pos = kb + (eid - kex);
-                    dst = __ldg(idx + pos);
-                    val = (T)(W ? ck * __ldg(wv + pos) : ck);
-                }
-                // Updates from different sources of the tile that hit the same vertex
-                // (typically a hub) are summed in the warp first, so the vertex takes one
-                // atomic per window instead of one per edge.
-                const unsigned peers = __match_any_sync(FULL, dst);
-                if (__all_sync(FULL, peers == (1u << lane))) {
-                    if (eid < E) atomicAdd(y + dst, val);
-                } else {
-                    agg[threadIdx.x] = val;
-                    __syncwarp();
-                    if (eid < E && (peers & ((1u << lane) - 1u)) == 0) {  // lowest lane of its group
-                        T sum = val;
-                        for (unsigned rest = peers & ~(1u << lane); rest; rest &= rest - 1)
-                            sum += agg[(threadIdx.x & ~31u) + (__ffs(rest) - 1)];
-                        atomicAdd(y + dst, sum);
-                    }
-                    __syncwarp();
-                }
+            for (int s = 16; s > 0; s >>= 1) {
+                const int ex = __shfl_sync(FULL, excl, k + s);
+                if (ex <= eid) k += s;
             }
+            const int64_t kb = __shfl_sync(FULL, b, k);
+            const int kex = __shfl_sync(FULL, excl, k);
+            const float ck = __shfl_sync(FULL, cu, k);
+            // idle lanes get keys no real edge has: positive and >= n is impossible for
+            // plain vertices, and HOT keys are negative
+            int32_t dst = (int32_t)(0x7fffffff - lane);
+            T val = 0;
+            if (eid < E) {
+                const int64_t pos = kb + (eid - kex);
+                dst = __ldg(idx + pos);
+                val = (T)(W ? ck * __ldg(wv + pos) : ck);
+            }
+            // Updates from different sources of the tile that hit the same vertex
+            // (typically a hub) are summed in the warp first, so the vertex takes one
+            // atomic per window instead of one per edge.
+            const unsigned peers = __match_any_sync(FULL, dst);
+            if (__all_sync(FULL, peers == (1u << lane))) {
+                if (eid < E) scatter_add<T, HOT>(y, sh_acc, dst, val);
+            } else {
+                agg[threadIdx.x] = val;
+                __syncwarp();
+                if (eid < E && (peers & ((1u << lane) - 1u)) == 0) {  // lowest lane of its group
+                    T sum = val;
+                    for (unsigned rest = peers & ~(1u << lane); rest; rest &= rest - 1)
+                        sum += agg[(threadIdx.x & ~31u) + (__ffs(rest) - 1)];
+                    scatter_add<T, HOT>(y, sh_acc, dst, sum);
+                }
+                __syncwarp();
+            }
+        }
+    }
+    if (HOT) {  // flush: one global atomic per touched hot vertex per block
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < a.nhot; i += blockDim.x) {
+            const float v = sh_acc[i];
+            if (v != 0.f) atomicAdd(y + a.hot_id[i], (T)v);
         }
     }
 }
@@ -598,6 +622,15 @@ static int ensure_vec(gp_graph *g, float *&slot, cudaStream_t s) {
     return g->pr.mem.alloc(slot, (size_t)std::max<int64_t>(g->n, 1), s);
 }
 
+static const void *push_kernel(bool W, bool fp64, bool hot) {
+    if (fp64) {
+        if (W) return hot ? (const void *)k_push_scatter<true, double, true> : (const void *)k_push_scatter<true, double, false>;
+        return hot ? (const void *)k_push_scatter<false, double, true> : (const void *)k_push_scatter<false, double, false>;
+    }
+    if (W) return hot ? (const void *)k_push_scatter<true, float, true> : (const void *)k_push_scatter<true, float, false>;
+    return hot ? (const void *)k_push_scatter<false, float, true> : (const void *)k_push_scatter<false, float, false>;
+}
+
 // One power iteration y = base + d * post_scale * (gather or scatter over the
 // given adjacency) of a PageRank-type linear system, with on-device
 // convergence; used for the forward pass and for the adjoint.
@@ -671,6 +704,16 @@ static int pr_iterate(gp_graph *g, const IterSpec &sp, float *out, PrStatus &fin
         tbp = 1024;
         tbl = 512;
     }
+    if (push && sp.hot) {
+        if (g->push_hot.slots != g->opt.push_hot_slots) GP_TRY(build_push_hot(g, g->opt.push_hot_slots, s));
+        hot = g->push_hot.nhot > 0;
+        if (hot) {
+            smem = (size_t)g->push_hot.nhot * sizeof(float);
+            a.hot_id = g->push_hot.hot_id;
+            a.nhot = g->push_hot.nhot;
+            a.idx = g->push_hot.enc_idx;
+        }
+    }
     int g1, g2, split;
     if (!push) {
         int ob = 0, ol = 0;
@@ -685,8 +728,15 @@ static int pr_iterate(gp_graph *g, const IterSpec &sp, float *out, PrStatus &fin
         split = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ol * g->num_sms, (ntiles + wpl - 1) / wpl));
         g2 = split + (int)((bins.nbig + tbl - 1) / tbl);
     } else {
-        split = (int)std::min<int64_t>(gb, (bins.nchunks + 7) / 8);
-        g1 = split + (int)std::max<int64_t>(1, std::min<int64_t>(gb, (ntiles + 7) / 8));
+        // one grid for big chunks and light tiles; as many resident blocks as fit,
+        // capped by blocks_per_sm (256-thread units)
+        const void *ks = push_kernel(W, g->opt.push_fp64_accum != 0, hot);
+        int os = 0;
+        GP_TRY(occupancy(ks, 1024, smem, os));
+        const int cap = std::max(1, g->opt.blocks_per_sm / 4) * g->num_sms;
+        const int64_t work = std::max<int64_t>((bins.nchunks + 31) / 32, (ntiles + 31) / 32);
+        split = 0;
+        g1 = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>((int64_t)os * g->num_sms, cap), work));
         g2 = (int)std::max<int64_t>(1, std::min<int64_t>(gb, (n + 255) / 256));
     }
     if (g2 > w.max_blocks) return set_error(GP_ERR_INVALID, "internal: partials too small");
@@ -706,7 +756,7 @@ static int pr_iterate(gp_graph *g, const IterSpec &sp, float *out, PrStatus &fin
                                                                     g->pull_hot.c_hot)));
         return check_launch("hot_gather");
     };
-    if (hot) GP_TRY(enqueue_hot_gather(C[0]));
+    if (hot && !push) GP_TRY(enqueue_hot_gather(C[0]));
 
     auto enqueue_sweep = [&](int k) -> int {
         PrArgs b = a;
@@ -733,19 +783,16 @@ static int pr_iterate(gp_graph *g, const IterSpec &sp, float *out, PrStatus &fin
         } else {
             b.c = C[0];
             b.c_next = C[0];
-            if (fp64) {
-                if (W)
-                    GP_LAUNCH("push_scatter", s, (k_push_scatter<true, double><<<g1, 256, 0, s>>>(b)));
-                else
-                    GP_LAUNCH("push_scatter", s, (k_push_scatter<false, double><<<g1, 256, 0, s>>>(b)));
-                GP_LAUNCH("push_epilogue", s, (k_push_epilogue<double><<<g2, 256, 0, s>>>(b)));
-            } else {
-                if (W)
-                    GP_LAUNCH("push_scatter", s, (k_push_scatter<true, float><<<g1, 256, 0, s>>>(b)));
-                else
-                    GP_LAUNCH("push_scatter", s, (k_push_scatter<false, float><<<g1, 256, 0, s>>>(b)));
-                GP_LAUNCH("push_epilogue", s, (k_push_epilogue<float><<<g2, 256, 0, s>>>(b)));
+            const void *ks = push_kernel(W, fp64, hot);
+            {
+                ProfScope ps("push_scatter", s);
+                void *args[] = {&b};
+                GP_CUDA(cudaLaunchKernel(ks, dim3((unsigned)g1), dim3(1024), args, smem, s));
             }
+            if (fp64)
+                GP_LAUNCH("push_epilogue", s, (k_push_epilogue<double><<<g2, 256, 0, s>>>(b)));
+            else
+                GP_LAUNCH("push_epilogue", s, (k_push_epilogue<float><<<g2, 256, 0, s>>>(b)));
         }
         return check_launch("pagerank sweep");
     };
@@ -892,7 +939,7 @@ extern "C" int gp_pagerank(const gp_graph *gc, int mode, float damping, int iter
     const bool push = mode == GP_PUSH;
     IterSpec sp;
     sp.push = push;
-    sp.hot = !push;
+    sp.hot = true;
     sp.off = push ? g->csr_off : g->csc_off;
     sp.idx = push ? g->csr_idx : g->csc_idx;
     sp.w = g->weighted ? (push ? g->csr_w : g->csc_w) : nullptr;

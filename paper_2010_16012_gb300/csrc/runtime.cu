@@ -445,12 +445,26 @@ __global__ void k_fill_chunks(const int32_t *big, int64_t nbig, const int64_t *o
 
 constexpr int HOT_HIST = 65536;  // out-degree histogram buckets (the last one collects all larger degrees)
 
+constexpr int HOT_HIST_SMEM = 8192;  // low buckets counted per block in shared memory
+
+// Degree histogram; the low buckets, which almost every vertex falls into, are
+// counted in shared memory first so the global atomics are one per bucket and block.
 __global__ void k_deg_hist(const int64_t *off, int64_t n, unsigned long long *hist) {
+    __shared__ unsigned sh[HOT_HIST_SMEM];
+    for (int i = threadIdx.x; i < HOT_HIST_SMEM; i += blockDim.x) sh[i] = 0u;
+    __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         const int64_t d = off[v + 1] - off[v];
-        if (d > 0) atomicAdd(hist + (d < HOT_HIST - 1 ? d : HOT_HIST - 1), 1ull);
+        if (d <= 0) continue;
+        if (d < HOT_HIST_SMEM)
+            atomicAdd(sh + d, 1u);
+        else
+            atomicAdd(hist + (d < HOT_HIST - 1 ? d : HOT_HIST - 1), 1ull);
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < HOT_HIST_SMEM; i += blockDim.x)
+        if (sh[i]) atomicAdd(hist + i, (unsigned long long)sh[i]);
 }
 
 __global__ void k_fill_slots(const int32_t *hot_id, int64_t nhot, int32_t *slot) {
@@ -467,10 +481,11 @@ __global__ void k_encode_hot(const int32_t *idx, int64_t m, const int32_t *slot,
     }
 }
 
-// Picks the `slots` vertices with the largest out-degree (ties: lowest ids),
-// builds the encoded copy of the CSC indices and the slot -> vertex table.
-int build_pull_hot(gp_graph *g, int32_t slots, cudaStream_t s) {
-    HotSet &h = g->pull_hot;
+// Picks the `slots` vertices with the largest degree by `sel_off` (ties: lowest
+// ids), builds the copy of `enc_src` (an index array of the graph) with those
+// vertices encoded as HOT_BIT | slot, and the slot -> vertex table.
+static int build_hot(gp_graph *g, HotSet &h, int32_t slots, const int64_t *sel_off, const int32_t *enc_src,
+                     cudaStream_t s) {
     h.mem.release(s);
     h = HotSet();
     h.slots = slots;
@@ -484,7 +499,7 @@ int build_pull_hot(gp_graph *g, int32_t slots, cudaStream_t s) {
         cudaError_t e = cudaMemsetAsync(hist, 0, HOT_HIST * sizeof(unsigned long long), s);
         int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)g->num_sms * 8));
         if (e == cudaSuccess) {
-            GP_LAUNCH("deg_hist", s, (k_deg_hist<<<blocks, 256, 0, s>>>(g->csr_off, n, hist)));
+            GP_LAUNCH("deg_hist", s, (k_deg_hist<<<blocks, 256, 0, s>>>(sel_off, n, hist)));
             e = cudaMemcpyAsync(hh.data(), hist, HOT_HIST * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -506,10 +521,10 @@ int build_pull_hot(gp_graph *g, int32_t slots, cudaStream_t s) {
     int64_t c1 = 0, c2 = 0;
     const int64_t top_lo = B > 0 ? (int64_t)B + 1 : 1;
     if (st == GP_OK && top_lo <= HOT_HIST - 1)
-        st = select_by_degree(g->csr_off, n, top_lo, INT64_MAX, tmp, list1, c1, slots, nullptr, s);
+        st = select_by_degree(sel_off, n, top_lo, INT64_MAX, tmp, list1, c1, slots, nullptr, s);
     if (st == GP_OK && B > 0) {
         const int64_t hi = B == HOT_HIST - 1 ? INT64_MAX : (int64_t)B;
-        st = select_by_degree(g->csr_off, n, B, hi, tmp, list2, c2, slots - c1, nullptr, s);
+        st = select_by_degree(sel_off, n, B, hi, tmp, list2, c2, slots - c1, nullptr, s);
     }
     const int64_t nhot = c1 + c2;
     int32_t *slot = nullptr;
@@ -529,7 +544,7 @@ int build_pull_hot(gp_graph *g, int32_t slots, cudaStream_t s) {
         int b1 = (int)std::max<int64_t>(1, std::min<int64_t>((nhot + 255) / 256, 65535));
         GP_LAUNCH("fill_slots", s, (k_fill_slots<<<b1, 256, 0, s>>>(h.hot_id, nhot, slot)));
         int b2 = (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, (int64_t)g->num_sms * 8));
-        GP_LAUNCH("encode_hot", s, (k_encode_hot<<<b2, 256, 0, s>>>(g->csc_idx, m, slot, h.enc_idx)));
+        GP_LAUNCH("encode_hot", s, (k_encode_hot<<<b2, 256, 0, s>>>(enc_src, m, slot, h.enc_idx)));
         st = check_launch("encode_hot");
     }
     if (st == GP_OK) {
@@ -544,6 +559,18 @@ int build_pull_hot(gp_graph *g, int32_t slots, cudaStream_t s) {
     }
     h.nhot = nhot;
     return GP_OK;
+}
+
+// Pull: the most gathered contributions are those of the largest out-degrees;
+// the gathered index array is CSC.
+int build_pull_hot(gp_graph *g, int32_t slots, cudaStream_t s) {
+    return build_hot(g, g->pull_hot, slots, g->csr_off, g->csc_idx, s);
+}
+
+// Push: the most updated vertices are those of the largest in-degrees; the
+// scattered index array is CSR.
+int build_push_hot(gp_graph *g, int32_t slots, cudaStream_t s) {
+    return build_hot(g, g->push_hot, slots, g->csc_off, g->csr_idx, s);
 }
 
 int grid_blocks(const gp_graph *g, int threads_per_block) {
@@ -660,6 +687,7 @@ int gp_options_default(gp_options *opt) {
     opt->bfs_beta = 24.0f;
     opt->push_fp64_accum = 1;
     opt->pull_hot_slots = 16384;
+    opt->push_hot_slots = 16384;
     return GP_OK;
 }
 
@@ -707,6 +735,7 @@ static int upload_fail(gp_graph *g, cudaStream_t s, int st) {
     g->pull_bins.mem.release(s);
     g->push_bins.mem.release(s);
     g->pull_hot.mem.release(s);
+    g->push_hot.mem.release(s);
     g->mem.release(s);
     delete g;
     return st;
@@ -864,6 +893,7 @@ int gp_graph_free(gp_graph *g) {
     g->pull_bins.mem.release(s);
     g->push_bins.mem.release(s);
     g->pull_hot.mem.release(s);
+    g->push_hot.mem.release(s);
     g->mem.release(s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (dev != g->device && dev >= 0) cudaSetDevice(dev);
@@ -907,7 +937,7 @@ int gp_graph_set_options(gp_graph *g, const gp_options *opt, void *stream) {
         opt->blocks_per_sm < 1 || opt->blocks_per_sm > 32 || opt->poll_interval < 1 ||
         !(opt->bfs_alpha > 0.f) || !(opt->bfs_beta > 0.f) || opt->pr_auto_mode < -1 || opt->pr_auto_mode > 1 ||
         (opt->push_fp64_accum != 0 && opt->push_fp64_accum != 1) || opt->pull_hot_slots < 0 ||
-        opt->pull_hot_slots > 49152)
+        opt->pull_hot_slots > 49152 || opt->push_hot_slots < 0 || opt->push_hot_slots > 49152)
         return set_error(GP_ERR_INVALID, "gp_graph_set_options: option out of range");
     cudaStream_t s = (cudaStream_t)stream;
     const gp_options old = g->opt;

@@ -62,8 +62,8 @@ ZOO = [
 ]
 OPTS = [None, {"pull_light_max": 0, "push_light_max": 0}, {"pull_light_max": 2, "push_light_max": 2, "chunk_edges": 32},
         {"pull_light_max": 1 << 20, "push_light_max": 1 << 20},
-        {"pull_hot_slots": 0},                            # no shared-memory contribution cache
-        {"pull_hot_slots": 3, "pull_light_max": 4}]       # cache cut inside a degree tie
+        {"pull_hot_slots": 0, "push_hot_slots": 0},       # no shared-memory caches
+        {"pull_hot_slots": 3, "push_hot_slots": 3, "pull_light_max": 4}]  # caches cut inside a degree tie
 
 
 @pytest.mark.parametrize("gi", range(len(ZOO)))
@@ -296,9 +296,11 @@ def test_oom_from_allocator_hook(gp):
 
 @pytest.mark.parametrize("slots", [0, 1, 7, 100, 4096, 12288, 12289, 49152])
 def test_hot_slot_counts(gp, slots):
-    """Any number of cached hot contributions gives the same iterate."""
+    """Any number of cached hot contributions (pull) or privatised hot
+    accumulators (push) gives the same iterate."""
     g = gg.rmat(12, 16, seed=13, symmetrize=False)
     run_and_check(gp, g, gp.PULL, iters=12, opts={"pull_hot_slots": slots})
+    run_and_check(gp, g, gp.PUSH, iters=12, opts={"push_hot_slots": slots})
 
 
 def test_graph_info(gp):
