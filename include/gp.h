@@ -410,6 +410,17 @@ typedef struct gp_kernel_time {
  * != 0 clears the accumulators afterwards. */
 int gp_profile_read(gp_kernel_time *out, int cap, int *count, int reset);
 
+/* ------------------------------------------------------------------ diagnostics */
+
+/* Self-check of the binary64 -> binary32 rounding that the push epilogue uses
+ * (integer operations on the IEEE 754 encodings, round to nearest, ties to
+ * even; magnitudes below 2^-126 give signed zero).  For each of the n values of
+ * the device array `in` (f64[n]) writes that rounding to `ours` and the
+ * hardware conversion (__double2float_rn) to `hw` (device f32[n] each, caller-
+ * owned).  Asynchronous on `stream`.  GP_ERR_INVALID for n < 0 or a NULL array
+ * with n > 0. */
+int gp_selftest_narrow(int64_t n, const double *in, float *ours, float *hw, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -61,7 +61,7 @@ def _get():
             lib.or_bfs_levelsync.argtypes = [vp, c.c_int32, vp, c.c_int, vp, vp, vp, c.c_int]
             lib.or_pagerank_adjoint.restype = c.c_int
             lib.or_pagerank_adjoint.argtypes = [vp, c.c_double, vp, vp, c.c_int, c.c_double, vp, vp, vp,
-                                                c.POINTER(c.c_double)]
+                                                c.POINTER(c.c_double), c.c_int]
             lib.or_max_threads.restype = c.c_int
             lib.or_max_threads.argtypes = []
             _lib = lib
@@ -136,7 +136,8 @@ class OracleGraph:
         return level, parent, used[:min(L, max_levels)].copy()
 
     # ------------------------------------------------------------ adjoint
-    def pagerank_adjoint(self, x, g, damping: float = 0.85, iters: int = 10000, tol: float = 1e-14):
+    def pagerank_adjoint(self, x, g, damping: float = 0.85, iters: int = 10000, tol: float = 1e-14,
+                         nthreads: int = 1):
         """Adjoint of the fixed point for L = g.x.  Returns (lambda, grad_s,
         grad_w in input edge order, iters_done, residual)."""
         lam = np.empty(self.n, dtype=np.float64)
@@ -146,7 +147,8 @@ class OracleGraph:
         xa = np.ascontiguousarray(x, dtype=np.float64)
         ga = np.ascontiguousarray(g, dtype=np.float64)
         k = self._lib.or_pagerank_adjoint(self._h, float(damping), _ptr(xa), _ptr(ga), int(iters),
-                                          float(tol), _ptr(lam), _ptr(gs), _ptr(gw), ctypes.byref(r))
+                                          float(tol), _ptr(lam), _ptr(gs), _ptr(gw), ctypes.byref(r),
+                                          int(nthreads))
         return lam, gs, gw, k, r.value
 
 

@@ -310,14 +310,18 @@ int or_bfs_levelsync(const or_graph *g, int32_t src, const int8_t *dirs, int ndi
  * Returns the number of iterations done.
  */
 int or_pagerank_adjoint(const or_graph *g, double d, const double *x, const double *gv, int iters,
-                        double tol, double *lambda, double *grad_s, double *grad_w, double *residual) {
+                        double tol, double *lambda, double *grad_s, double *grad_w, double *residual,
+                        int nthreads) {
     const int64_t n = g->n;
+    or_set_threads(nthreads);
     double *lam = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
     double *nxt = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
     for (int64_t v = 0; v < n; ++v) lam[v] = gv[v];
     int k = 0;
     double r = 0.0;
     while (k < iters) {
+        /* each nxt[u] is one in-order sum, so the thread count does not change the result */
+#pragma omp parallel for schedule(dynamic, 1024) if (nthreads > 1)
         for (int64_t u = 0; u < n; ++u) {
             double acc = 0.0;
             for (int64_t j = g->out_off[u]; j < g->out_off[u + 1]; ++j)

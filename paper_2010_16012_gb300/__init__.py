@@ -116,6 +116,7 @@ SIGNATURES = [
     ("gp_profile_enable", ctypes.c_int, [ctypes.c_int]),
     ("gp_profile_read", ctypes.c_int, [ctypes.POINTER(gp_kernel_time), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    ("gp_selftest_narrow", ctypes.c_int, [_I64, _VP, _VP, _VP, _VP]),
 ]
 
 
@@ -500,6 +501,16 @@ def pull_sweep_noalloc(n, m, csc_off, csc_idx, inv_deg, x, y, residual, damping=
 
 def profile_enable(on: bool = True):
     _check(load().gp_profile_enable(int(on)), "gp_profile_enable")
+
+
+def selftest_narrow(values, stream=None):
+    """gp_selftest_narrow on a CUDA float64 tensor: (library rounding, hardware rounding)."""
+    torch = _torch()
+    ours = torch.empty(values.shape[0], dtype=torch.float32, device=values.device)
+    hw = torch.empty_like(ours)
+    _check(load().gp_selftest_narrow(int(values.shape[0]), _ptr(values), _ptr(ours), _ptr(hw), _stream_ptr(stream)),
+           "gp_selftest_narrow")
+    return ours, hw
 
 
 def profile_read(reset: bool = True) -> list:

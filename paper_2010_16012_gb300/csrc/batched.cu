@@ -150,7 +150,7 @@ __device__ __forceinline__ void gather_rows(const BatchDev &B, const BGraph &G, 
 // accumulates |y - x| of active columns.
 template <int KPL>
 __device__ __forceinline__ void finish_row(const BatchDev &B, int gi, const BGraph &G, const float *Xc, float *Y,
-                                           int64_t v, const float (&acc)[KPL], double (&res)[KPL]) {
+                                           int64_t v, const float (&acc)[KPL], ResSum (&res)[KPL]) {
     const int lane = lane_id();
     const int K = 32 * KPL;
     const int64_t o = v * K + lane * KPL;
@@ -162,31 +162,36 @@ __device__ __forceinline__ void finish_row(const BatchDev &B, int gi, const BGra
         if (B.active[gi * K + j]) {
             const float base = (B.seeds[gi * K + j] == (int32_t)v) ? B.one_minus_d : 0.f;
             y = base + B.d * acc[q];
-            res[q] += fabs((double)y - (double)x);
+            res[q].add(y, x);
         }
         Y[o + q] = y;
     }
 }
 
-// Block-level reduction of per-lane column residuals into res_part[row][K].
+// Block-level reduction of per-lane column residuals into res_part[row][K]:
+// every warp leaves its column partials in shared memory, then one thread per
+// column adds the warps' partials in warp order (deterministic), compensated.
 template <int KPL>
-__device__ void flush_res(const BatchDev &B, int64_t row, double (&res)[KPL], double *sm /* [K] */) {
-    const int lane = lane_id();
+__device__ void flush_res(const BatchDev &B, int64_t row, ResSum (&res)[KPL], float *sm /* [warps][K] */) {
+    const int lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int K = 32 * KPL;
-    for (int j = threadIdx.x; j < K; j += blockDim.x) sm[j] = 0.0;
-    __syncthreads();
 #pragma unroll
-    for (int q = 0; q < KPL; ++q) atomicAdd(sm + lane * KPL + q, res[q]);
+    for (int q = 0; q < KPL; ++q) {
+        sm[w * K + lane * KPL + q] = res[q].getf();
+        res[q] = ResSum();
+    }
     __syncthreads();
-    for (int j = threadIdx.x; j < K; j += blockDim.x) B.res_part[row * K + j] = sm[j];
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+        ResSum t;
+        for (int i = 0; i < nw; ++i) t.push(sm[i * K + j]);
+        B.res_part[row * K + j] = t.get();
+    }
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < KPL; ++q) res[q] = 0.0;
 }
 
 template <int KPL>
 __global__ void __launch_bounds__(BT_THREADS) k_ppr_persistent(BatchDev B) {
-    __shared__ double sm[32 * KPL];
+    __shared__ float sm[(BT_THREADS / 32) * 32 * KPL];
     const int K = 32 * KPL;
     const int lane = lane_id();
     const int wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
@@ -228,9 +233,7 @@ __global__ void __launch_bounds__(BT_THREADS) k_ppr_persistent(BatchDev B) {
             const BGraph &G = B.graphs[tl.graph];
             const float *Xc = (k & 1) ? G.X0 : G.X1;
             float *Y = (k & 1) ? G.X1 : G.X0;
-            double res[KPL];
-#pragma unroll
-            for (int q = 0; q < KPL; ++q) res[q] = 0.0;
+            ResSum res[KPL];
             for (int i = wib; i < tl.cnt; i += wpb) {
                 const int64_t v = tl.v0 + i;
                 const int64_t b = G.csc_off[v], e = G.csc_off[v + 1];
@@ -251,9 +254,7 @@ __global__ void __launch_bounds__(BT_THREADS) k_ppr_persistent(BatchDev B) {
             const BGraph &G = B.graphs[tl.graph];
             const float *Xc = (k & 1) ? G.X0 : G.X1;
             float *Y = (k & 1) ? G.X1 : G.X0;
-            double res[KPL];
-#pragma unroll
-            for (int q = 0; q < KPL; ++q) res[q] = 0.0;
+            ResSum res[KPL];
             for (int i = wib; i < tl.cnt; i += wpb) {
                 const int64_t r = tl.v0 + i;
                 const int64_t v = B.big[r];

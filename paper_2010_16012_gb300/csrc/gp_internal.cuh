@@ -244,6 +244,43 @@ __device__ __forceinline__ T block_sum(T v, T *smem /* >= 32 entries */) {
     return r;
 }
 
+// Per-thread part of the L1 residual sum |y - x|: compensated (Kahan) FP32
+// summation, whose error does not grow with the number of terms, converted to
+// FP64 for the cross-thread reduction (warp, block, grid partials are FP64).
+// FP64 arithmetic per vertex would run on this GPU's narrow FP64 pipe.
+struct ResSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void push(float v) {
+        v -= c;
+        const float t = s + v;
+        c = (t - s) - v;
+        s = t;
+    }
+    __device__ __forceinline__ void add(float y, float x) { push(fabsf(y - x)); }
+    __device__ __forceinline__ float getf() const { return s - c; }
+    __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+
+// binary64 -> binary32, round to nearest (ties to even), by integer operations
+// on the IEEE 754 encodings (1 sign, 11/8 exponent bits with bias 1023/127,
+// 52/23 fraction bits).  Results below the binary32 normal range (|v| < 2^-126)
+// become signed zero; results above it become infinity; NaN stays NaN.
+__device__ __forceinline__ float f64_to_f32_rn(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int e11 = (int)((b >> 52) & 0x7ff);
+    const unsigned long long frac = b & 0xfffffffffffffull;
+    if (e11 == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (frac ? 0x400000u : 0u));
+    const int e8 = e11 - 1023 + 127;
+    if (e8 <= 0) return __uint_as_float(sign);
+    if (e8 >= 0xff) return __uint_as_float(sign | 0x7f800000u);
+    const unsigned keep = (unsigned)(frac >> 29);                // top 23 fraction bits
+    const unsigned rest = (unsigned)(frac & 0x1fffffffull);       // 29 dropped bits
+    unsigned r = ((unsigned)e8 << 23) | keep;
+    if (rest > 0x10000000u || (rest == 0x10000000u && (keep & 1u))) ++r;  // a carry into the exponent is exact
+    return __uint_as_float(sign | r);  // a carry out of e8 = 254 gives 0x7f800000: infinity
+}
+
 // ------------------------------------------------------------------ grid barrier
 
 // Grid-wide barrier for cooperative launches (all blocks co-resident).  The

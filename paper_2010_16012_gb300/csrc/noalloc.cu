@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(256) k_na_sweep(int64_t n, int64_t m, const in
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t ntiles = (n + 31) >> 5;
-    double res = 0.0;
+    ResSum res;
     bool bad = false;
     for (int64_t t = warp; t < ntiles; t += nwarps) {
         const int64_t v = t * 32 + lane;
@@ -135,13 +135,13 @@ __global__ void __launch_bounds__(256) k_na_sweep(int64_t n, int64_t m, const in
         }
         if (v < n) {
             const float yv = (s ? one_minus_d * s[v] : base_uniform) + d * acc;
-            res += fabs((double)yv - (double)x[v]);
+            res.add(yv, x[v]);
             y[v] = yv;
         }
     }
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(&sc->bad, 1u);
-    res = block_sum(res, red);
-    if (threadIdx.x == 0) sc->partials[blockIdx.x] = res;
+    const double r = block_sum(res.get(), red);
+    if (threadIdx.x == 0) sc->partials[blockIdx.x] = r;
 }
 
 // Sums the block partials in block order; NaN signals malformed input.

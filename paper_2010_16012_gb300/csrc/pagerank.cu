@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(512, GP_LIGHT_MIN_BLOCKS) k_pull_light(PrArgs 
     __shared__ double sm[32];
     if (((volatile PrStatus *)a.status)->done) return;
     const int lane = lane_id();
-    double res = 0.0;
+    ResSum res;
     const int64_t n = a.n;
     if ((int)blockIdx.x < a.split_blocks) {
         load_hot<HOT>(a, sh_hot);
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(512, GP_LIGHT_MIN_BLOCKS) k_pull_light(PrArgs 
             }
             if (v < n && !big) {
                 const float y = base_v + a.d * (ps * acc);
-                res += fabs((double)y - (double)xv);
+                res.add(y, xv);
                 a.y[v] = y;
                 a.c_next[v] = y * cm;
             }
@@ -341,13 +341,13 @@ __global__ void __launch_bounds__(512, GP_LIGHT_MIN_BLOCKS) k_pull_light(PrArgs 
             float acc = 0.f;
             for (int64_t j = a.cstart[r]; j < a.cstart[r + 1]; ++j) acc += a.chunk_part[j];
             const float y = base_term(a, v) + a.d * (post_factor(a, v) * acc);
-            res += fabs((double)y - (double)a.x[v]);
+            res.add(y, a.x[v]);
             a.y[v] = y;
             a.c_next[v] = y * c_factor(a, v);
         }
     }
-    res = block_sum(res, sm);
-    if (threadIdx.x == 0) a.partials[blockIdx.x] = res;
+    const double r = block_sum(res.get(), sm);
+    if (threadIdx.x == 0) a.partials[blockIdx.x] = r;
 }
 
 // c_hot[slot] = c[hot_id[slot]] for the sweep that reads c next.
@@ -366,11 +366,11 @@ __global__ void k_hot_gather(const int32_t *hot_id, int64_t nhot, const float *c
 // summed in the block's shared memory with shared-memory atomics and flushed
 // once per block; only the other updates use global atomics.
 template <class T, bool HOT>
-__device__ __forceinline__ void scatter_add(T *y, float *sh, int32_t dst, T val) {
+__device__ __forceinline__ void scatter_add(T *y, float *sh, int32_t dst, float val) {
     if (HOT && dst < 0)
-        atomicAdd(sh + (dst & 0x7fffffff), (float)val);
+        atomicAdd(sh + (dst & 0x7fffffff), val);
     else
-        atomicAdd(y + dst, val);
+        atomicAdd(y + dst, (T)val);
 }
 
 template <bool W, class T, bool HOT>
@@ -396,15 +396,15 @@ __global__ void __launch_bounds__(1024) k_push_scatter(PrArgs a) {
         int i = lane;
         for (; i + 96 < ch.len; i += 128) {
             const int v0 = __ldg(ip + i), v1 = __ldg(ip + i + 32), v2 = __ldg(ip + i + 64), v3 = __ldg(ip + i + 96);
-            scatter_add<T, HOT>(y, sh_acc, v0, (T)(W ? cu * __ldg(wp + i) : cu));
-            scatter_add<T, HOT>(y, sh_acc, v1, (T)(W ? cu * __ldg(wp + i + 32) : cu));
-            scatter_add<T, HOT>(y, sh_acc, v2, (T)(W ? cu * __ldg(wp + i + 64) : cu));
-            scatter_add<T, HOT>(y, sh_acc, v3, (T)(W ? cu * __ldg(wp + i + 96) : cu));
+            scatter_add<T, HOT>(y, sh_acc, v0, W ? cu * __ldg(wp + i) : cu);
+            scatter_add<T, HOT>(y, sh_acc, v1, W ? cu * __ldg(wp + i + 32) : cu);
+            scatter_add<T, HOT>(y, sh_acc, v2, W ? cu * __ldg(wp + i + 64) : cu);
+            scatter_add<T, HOT>(y, sh_acc, v3, W ? cu * __ldg(wp + i + 96) : cu);
         }
-        for (; i < ch.len; i += 32) scatter_add<T, HOT>(y, sh_acc, __ldg(ip + i), (T)(W ? cu * __ldg(wp + i) : cu));
+        for (; i < ch.len; i += 32) scatter_add<T, HOT>(y, sh_acc, __ldg(ip + i), W ? cu * __ldg(wp + i) : cu);
     }
     // light sources: 32 consecutive sources per warp, one merged edge stream
-    __shared__ T agg[1024];
+    __shared__ float agg[1024];
     const int64_t n = a.n;
     const int64_t ntiles = (n + 31) >> 5;
     for (int64_t t = warp; t < ntiles; t += nwarps) {
@@ -436,11 +436,11 @@ __global__ void __launch_bounds__(1024) k_push_scatter(PrArgs a) {
             // idle lanes get keys no real edge has: positive and >= n is impossible for
             // plain vertices, and HOT keys are negative
             int32_t dst = (int32_t)(0x7fffffff - lane);
-            T val = 0;
+            float val = 0.f;
             if (eid < E) {
                 const int64_t pos = kb + (eid - kex);
                 dst = __ldg(idx + pos);
-                val = (T)(W ? ck * __ldg(wv + pos) : ck);
+                val = W ? ck * __ldg(wv + pos) : ck;
             }
             // Updates from different sources of the tile that hit the same vertex
             // (typically a hub) are summed in the warp first, so the vertex takes one
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(1024) k_push_scatter(PrArgs a) {
                 agg[threadIdx.x] = val;
                 __syncwarp();
                 if (eid < E && (peers & ((1u << lane) - 1u)) == 0) {  // lowest lane of its group
-                    T sum = val;
+                    float sum = val;
                     for (unsigned rest = peers & ~(1u << lane); rest; rest &= rest - 1)
                         sum += agg[(threadIdx.x & ~31u) + (__ffs(rest) - 1)];
                     scatter_add<T, HOT>(y, sh_acc, dst, sum);
@@ -478,24 +478,25 @@ __global__ void __launch_bounds__(256) k_push_epilogue(PrArgs a) {
     __shared__ double sm[32];
     if (((volatile PrStatus *)a.status)->done) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    double res = 0.0;
+    ResSum res;
     float *x_reset = const_cast<float *>(a.x);
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += stride) {
         const float base = base_term(a, v), ps = post_factor(a, v);
         float y;
         if (sizeof(T) == 8) {
-            y = (float)((double)base + (double)ps * a.acc64[v]);
+            // the FP64 sum rounded once to FP32, then the FP32 epilogue
+            y = fmaf(ps, f64_to_f32_rn(a.acc64[v]), base);
             a.acc64[v] = 0.0;
         } else {
             y = base + ps * a.y[v];
         }
-        res += fabs((double)y - (double)a.x[v]);
+        res.add(y, a.x[v]);
         a.y[v] = y;
         a.c_next[v] = y * c_factor(a, v);
         if (sizeof(T) != 8) x_reset[v] = 0.f;  // the next sweep accumulates into this buffer
     }
-    res = block_sum(res, sm);
-    if (threadIdx.x == 0) a.partials[blockIdx.x] = res;
+    const double r = block_sum(res.get(), sm);
+    if (threadIdx.x == 0) a.partials[blockIdx.x] = r;
 }
 
 // ------------------------------------------------------------------ adjoint gradients

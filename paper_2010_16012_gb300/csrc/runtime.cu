@@ -691,6 +691,25 @@ int gp_options_default(gp_options *opt) {
     return GP_OK;
 }
 
+static __global__ void k_selftest_narrow(int64_t n, const double *in, float *ours, float *hw) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        ours[i] = f64_to_f32_rn(in[i]);
+        hw[i] = __double2float_rn(in[i]);
+    }
+}
+
+int gp_selftest_narrow(int64_t n, const double *in, float *ours, float *hw, void *stream) {
+    clear_error();
+    if (n < 0 || (n > 0 && (!in || !ours || !hw))) return set_error(GP_ERR_INVALID, "gp_selftest_narrow: bad arguments");
+    if (n == 0) return GP_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    k_selftest_narrow<<<blocks, 256, 0, s>>>(n, in, ours, hw);
+    GP_CUDA(cudaGetLastError());
+    return GP_OK;
+}
+
 int gp_profile_enable(int on) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_prof_on = on != 0;

@@ -154,3 +154,24 @@ def check_parents_np(csr_off, csr_idx, root, level, parent):
     found[inrow] = csr_idx[lo[inrow]] == v[inrow]
     bad += int(np.count_nonzero(~found))
     return bad
+
+
+def edge_sources(csr_off):
+    """Tail of every CSR edge slot (int32[m])."""
+    deg = np.diff(csr_off)
+    return np.repeat(np.arange(deg.shape[0], dtype=np.int32), deg)
+
+
+def check_levels_by_edges(csr_src, csr_idx, root, level):
+    """Edge conditions that, together with valid parents (check_parents_np),
+    make `level` exactly the BFS distance from `root` at any graph size: the
+    root has level 0, and no edge u->v leaves a reached u towards an unreached
+    v or a v more than one level below u.  (Parents give a path of length
+    level[v], so level >= distance; the edge rule along a shortest path gives
+    level <= distance.)  Returns the number of violations."""
+    lv = level.astype(np.int64)
+    lu = lv[csr_src]
+    lh = lv[csr_idx]
+    bad = int(lv[root] != 0)
+    bad += int(np.count_nonzero((lu >= 0) & ((lh < 0) | (lh > lu + 1))))
+    return bad

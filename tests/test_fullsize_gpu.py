@@ -1,0 +1,205 @@
+"""Parity at the full workload sizes, in the launch configuration the benchmark
+times (options chosen by gp_autotune on the graph itself):
+
+- R-MAT scale 22 (n = 4,194,304, m = 128,316,514): PageRank PULL / PUSH / AUTO
+  to L1 tol 1e-7, every vertex against the FP64 oracle at the GPU's sweep
+  count; BFS AUTO from the 64 benchmark sources, levels bit-exact against the
+  oracle on a sample and, on every checked source, valid parents plus the edge
+  rule that together pin BFS distances at any size;
+- directed Erdos-Renyi G(2^24, 16 * 2^24 draws): PageRank pull and push for 20
+  sweeps against the oracle; BFS top-down, bottom-up and switching from 16
+  sources, identical across directions and checked against the oracle;
+- the batch of 32 R-MAT graphs (scales 12..18): 256 personalised vectors and
+  64 BFS sources per graph in one persistent launch, sampled vectors and
+  sources against the oracle;
+- weighted R-MAT scale 20: forward PageRank then the adjoint, against the FP64
+  oracle's adjoint of its own fixed point (1e-4 relative).
+
+The threaded oracle finishes each comparison in seconds on the host cores."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from helpers import check_levels_by_edges, check_parents_np, edge_sources
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+MAX_ABS, L1 = 1e-6, 1e-5
+REL = 1e-4
+NT = oracle.max_threads()
+
+
+@pytest.fixture(scope="module")
+def gp():
+    import torch
+
+    import paper_2010_16012_gb300 as gp
+
+    assert torch.cuda.is_available()
+    gp.load()
+    return gp
+
+
+def pr_errors(x_gpu, ref):
+    err = np.abs(x_gpu.cpu().numpy().astype(np.float64) - ref)
+    return float(err.max()), float(err.sum())
+
+
+class OracleRuns:
+    """Oracle pull PageRank results keyed by sweep count (uniform teleport)."""
+
+    def __init__(self, O):
+        self.O, self.by_k = O, {}
+
+    def at(self, k):
+        if k not in self.by_k:
+            x, kk, _, _ = self.O.pagerank(oracle.PULL, 0.85, iters=k, tol=0.0, nthreads=NT)
+            assert kk == k
+            self.by_k[k] = x
+        return self.by_k[k]
+
+
+# ---------------------------------------------------------------- R-MAT scale 22
+
+@pytest.fixture(scope="module")
+def rmat22(gp):
+    g = gg.rmat(22, 16, seed=1)
+    srcs = gg.pick_vertices(g, 64, seed=2)
+    G = gp.Graph.from_graphgen(g)
+    gp.autotune(G, gp.TUNE_ALL, sources=srcs[:16], use_cache=False)
+    O = oracle.OracleGraph.from_graph(g)
+    yield g, G, O, srcs, OracleRuns(O)
+    G.free()
+
+
+@pytest.mark.parametrize("mode", ["pull", "push", "auto"])
+def test_rmat22_pagerank_to_tolerance(gp, rmat22, mode):
+    g, G, O, _, runs = rmat22
+    x, st = gp.pagerank(G, {"pull": gp.PULL, "push": gp.PUSH, "auto": gp.AUTO}[mode], 0.85, 300, 1e-7)
+    assert st["converged"] and st["residual"] < 1e-7
+    k = st["iters_done"]
+    # it stopped where the FP64 iteration first drops below tol, give or take the FP32 rounding of one sweep
+    _, k_exact, _, conv = O.pagerank(oracle.PULL, 0.85, iters=300, tol=1e-7, nthreads=NT)
+    assert conv and abs(k - k_exact) <= 1
+    mx, l1 = pr_errors(x, runs.at(k))
+    assert mx <= MAX_ABS and l1 <= L1, (mode, k, mx, l1)
+
+
+def test_rmat22_bfs_auto(gp, rmat22):
+    import torch
+
+    g, G, O, srcs, _ = rmat22
+    esrc = edge_sources(g.csr_off)
+    level = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    lv_by_src = []
+    for i, s in enumerate(srcs):
+        gp.bfs(G, int(s), gp.AUTO, level=level, parent=parent)
+        if i % 8 == 0:  # 8 of the 64 sources checked in full
+            lv, pa = level.cpu().numpy(), parent.cpu().numpy()
+            assert check_levels_by_edges(esrc, g.csr_idx, int(s), lv) == 0, s
+            assert check_parents_np(g.csr_off, g.csr_idx, int(s), lv, pa) == 0, s
+            lv_by_src.append((int(s), lv))
+    for s, lv in lv_by_src[:3]:
+        ref, _ = O.bfs(s)
+        assert np.array_equal(lv, ref), s
+
+
+# ---------------------------------------------------------------- Erdos-Renyi 2^24
+
+@pytest.fixture(scope="module")
+def er24(gp):
+    g = gg.erdos_renyi(1 << 24, 16 << 24, seed=3)
+    G = gp.Graph.from_graphgen(g)
+    srcs = gg.pick_vertices(g, 16, seed=4)
+    gp.autotune(G, gp.TUNE_ALL, sources=srcs[:4], use_cache=False)
+    O = oracle.OracleGraph.from_graph(g)
+    yield g, G, O, srcs
+    G.free()
+
+
+def test_er24_pagerank_20_sweeps(gp, er24):
+    g, G, O, _ = er24
+    ref, _, _, _ = O.pagerank(oracle.PULL, 0.85, iters=20, tol=0.0, nthreads=NT)
+    for mode in (gp.PULL, gp.PUSH):
+        x, st = gp.pagerank(G, mode, 0.85, 20, 0.0)
+        assert st["iters_done"] == 20
+        mx, l1 = pr_errors(x, ref)
+        assert mx <= MAX_ABS and l1 <= L1, (mode, mx, l1)
+
+
+def test_er24_bfs_directions_agree(gp, er24):
+    import torch
+
+    g, G, O, srcs = er24
+    esrc = edge_sources(g.csr_off)
+    level = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    for i, s in enumerate(srcs):
+        got = []
+        for mode in (gp.PUSH, gp.PULL, gp.AUTO):
+            gp.bfs(G, int(s), mode, level=level, parent=parent)
+            got.append(level.cpu().numpy())
+            if i < 2:
+                assert check_parents_np(g.csr_off, g.csr_idx, int(s), got[-1], parent.cpu().numpy()) == 0
+        assert np.array_equal(got[0], got[1]) and np.array_equal(got[0], got[2]), s
+        if i < 2:
+            assert check_levels_by_edges(esrc, g.csr_idx, int(s), got[0]) == 0
+            ref, _ = O.bfs(int(s))
+            assert np.array_equal(got[0], ref), s
+
+
+# ---------------------------------------------------------------- 32-graph batch
+
+def test_batch_32_graphs(gp):
+    K, NSRC = 256, 64
+    scales = [12 + int(gg.draw(5, i) % 7) for i in range(32)]
+    graphs = [gg.rmat(s, 16, seed=100 + i) for i, s in enumerate(scales)]
+    G = [gp.Graph.from_graphgen(g) for g in graphs]
+    B = gp.Batch(G, k_ppr=K)
+    seeds = np.stack([np.resize(gg.pick_vertices(g, K, seed=6 + 1000 * i), K) for i, g in enumerate(graphs)])
+    srcs = np.stack([np.resize(gg.pick_vertices(g, NSRC, seed=7 + 1000 * i), NSRC) for i, g in enumerate(graphs)])
+    outs, done, st = B.ppr(seeds.astype(np.int32), iters=1000, tol=1e-6)
+    assert done.min() >= 1 and st["sweeps"] == done.max()
+    louts, _ = B.msbfs(srcs.astype(np.int32))
+    rng = np.random.default_rng(12)
+    big = int(np.argmax(scales))
+    for i in sorted({big, int(np.argmin(scales))} | set(rng.choice(32, size=4, replace=False).tolist())):
+        O = oracle.OracleGraph.from_graph(graphs[i])
+        X = outs[i].cpu().numpy()
+        for j in (int(rng.integers(K)), K - 1):
+            e = np.zeros(graphs[i].n)
+            e[seeds[i, j]] = 1.0
+            ref, _, _, _ = O.pagerank(oracle.PULL, 0.85, iters=int(done[i, j]), personalization=e, nthreads=NT)
+            err = np.abs(X[:, j].astype(np.float64) - ref)
+            assert err.max() <= MAX_ABS and err.sum() <= L1, (i, j, err.max(), err.sum())
+        L = louts[i].cpu().numpy()
+        for j in (0, int(rng.integers(NSRC)), NSRC - 1):
+            ref, _ = O.bfs(int(srcs[i, j]))
+            assert np.array_equal(L[:, j], ref), (i, j)
+    B.free()
+    for x in G:
+        x.free()
+
+
+# ---------------------------------------------------------------- weighted R-MAT scale 20 adjoint
+
+def test_weighted_rmat20_forward_and_adjoint(gp):
+    import torch
+
+    g = gg.rmat(20, 16, seed=8).with_weights(9)
+    G = gp.Graph.from_graphgen(g)
+    gvec = np.random.default_rng(10).normal(size=g.n)
+    x, st = gp.pagerank(G, gp.PULL, 0.85, 300, 0.0)  # 0.85^300: converged to FP32 rounding
+    gw, gs, _ = gp.pagerank_backward(G, x, torch.from_numpy(gvec.astype(np.float32)).cuda(), iters=300, tol=0.0)
+    O = oracle.OracleGraph.from_graph(g)
+    xr, _, _, conv = O.pagerank(oracle.PULL, 0.85, iters=100000, tol=1e-14, nthreads=NT)
+    assert conv
+    assert np.abs(x.cpu().numpy() - xr).max() <= MAX_ABS
+    _, gs_ref, gw_ref, _, _ = O.pagerank_adjoint(xr, gvec, 0.85, nthreads=NT)
+    for a, ref in ((gs, gs_ref), (gw, gw_ref)):
+        a = a.cpu().numpy().astype(np.float64)
+        rel = np.abs(a - ref).max() / np.abs(ref).max()
+        assert rel <= REL, rel
+    G.free()

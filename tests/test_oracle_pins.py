@@ -8,8 +8,8 @@ import pytest
 
 import graphgen as gg
 import oracle
-from helpers import (check_parents, dense_pagerank, dense_transition, floyd_warshall_levels,
-                     parse_bfs_case, parse_pagerank_cases)
+from helpers import (check_levels_by_edges, check_parents, check_parents_np, dense_pagerank, dense_transition,
+                     edge_sources, floyd_warshall_levels, parse_bfs_case, parse_pagerank_cases)
 
 VARIANTS = [oracle.PUSH, oracle.PULL]
 
@@ -157,6 +157,18 @@ def test_pull_threads_identical():
     a, _, _, _ = G.pagerank(oracle.PULL, 0.85, iters=10, nthreads=1)
     b, _, _, _ = G.pagerank(oracle.PULL, 0.85, iters=10, nthreads=4)
     assert np.array_equal(a, b)
+
+
+def test_adjoint_threads_identical():
+    """The threaded adjoint sums each lambda_u in the same order: bitwise equal."""
+    g = gg.rmat(11, 8, seed=5, symmetrize=False).with_weights(6)
+    G = og(g)
+    x, _, _, _ = G.pagerank(oracle.PULL, 0.85, iters=50)
+    gvec = np.random.default_rng(7).normal(size=g.n)
+    a = G.pagerank_adjoint(x, gvec, 0.85, iters=40, nthreads=1)
+    b = G.pagerank_adjoint(x, gvec, 0.85, iters=40, nthreads=4)
+    for u, v in zip(a[:3], b[:3]):
+        assert np.array_equal(u, v)
 
 
 def test_convergence_contract():
@@ -312,3 +324,29 @@ def test_adjoint_finite_differences():
         sm[vtx] -= h
         fd = (loss(w, sp) - loss(w, sm)) / (2 * h)
         assert abs(fd - gs[vtx]) <= 1e-7 * max(1.0, abs(fd))
+
+
+def test_full_size_bfs_checkers_catch_planted_mistakes():
+    """The level/parent rules used at full size accept the oracle's BFS and
+    reject each kind of planted mistake (a level one too deep, one too shallow,
+    a reached vertex marked unreached, a parent from the wrong level)."""
+    g = gg.rmat(12, 8, seed=9)
+    O = og(g)
+    src = int(gg.pick_vertices(g, 1, seed=3)[0])
+    level, parent = O.bfs(src)
+    esrc = edge_sources(g.csr_off)
+    assert check_levels_by_edges(esrc, g.csr_idx, src, level) == 0
+    assert check_parents_np(g.csr_off, g.csr_idx, src, level, parent) == 0
+    deep = np.nonzero(level == level.max())[0][0]
+    mid = np.nonzero(level == 2)[0][0]
+    for v, delta in ((deep, 1), (mid, -1)):
+        bad = level.copy()
+        bad[v] += delta
+        assert check_levels_by_edges(esrc, g.csr_idx, src, bad) + \
+            check_parents_np(g.csr_off, g.csr_idx, src, bad, parent) > 0
+    bad = level.copy()
+    bad[mid] = -1
+    assert check_levels_by_edges(esrc, g.csr_idx, src, bad) > 0
+    badp = parent.copy()
+    badp[deep] = src
+    assert check_parents_np(g.csr_off, g.csr_idx, src, level, badp) > 0
