@@ -294,6 +294,13 @@ typedef struct gp_bfs_stats {
  *   parent_out  int32[n] "any" or NULL: a BFS parent (parent[src] = src, -1 if
  *               unreached).  Levels are unique; parents are valid but may
  *               differ between runs (any frontier in-neighbour is correct).
+ *   stats       NULL or filled on return (the call then waits for the search).
+ * Synchronisation: with stats == NULL and both outputs in device memory the
+ * call only enqueues the search on `stream` and returns; a grid-barrier
+ * timeout of that search (GP_ERR_TIMEOUT, outputs incomplete) is then returned
+ * by the next gp_bfs / gp_bfs_directed call on the same graph.  Otherwise the
+ * call waits and reports the timeout itself.  Searches on one graph share its
+ * workspace: issue them on one stream (or order the streams).
  */
 int gp_bfs(const gp_graph *g, int32_t src, int mode, int32_t *level_out, int32_t *parent_out, gp_bfs_stats *stats,
            void *stream);
@@ -420,6 +427,15 @@ int gp_profile_read(gp_kernel_time *out, int cap, int *count, int reset);
  * owned).  Asynchronous on `stream`.  GP_ERR_INVALID for n < 0 or a NULL array
  * with n > 0. */
 int gp_selftest_narrow(int64_t n, const double *in, float *ours, float *hw, void *stream);
+
+/* Self-check of the bounded grid barrier that the persistent kernels (BFS,
+ * batches) use between phases: one cooperative launch of one 128-thread block
+ * per SM in which every block except `absent` enters a barrier whose waits give
+ * up after a short limit (tens of milliseconds).  absent < 0: every block
+ * arrives and the call returns GP_OK; otherwise the waiting blocks time out,
+ * return, and the call returns GP_ERR_TIMEOUT with the device context intact.
+ * Waits for completion.  GP_ERR_INVALID for absent >= the SM count. */
+int gp_selftest_barrier(int absent, void *stream);
 
 #ifdef __cplusplus
 }

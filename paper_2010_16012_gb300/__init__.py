@@ -117,6 +117,7 @@ SIGNATURES = [
     ("gp_profile_read", ctypes.c_int, [ctypes.POINTER(gp_kernel_time), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("gp_selftest_narrow", ctypes.c_int, [_I64, _VP, _VP, _VP, _VP]),
+    ("gp_selftest_barrier", ctypes.c_int, [ctypes.c_int, _VP]),
 ]
 
 
@@ -344,22 +345,29 @@ def pagerank_autograd(graph: Graph, csr_w=None, personalization=None, csc_perm=N
 _PRF = None
 
 
-def bfs(g: Graph, src: int, mode=AUTO, level=None, parent=None, want_parent=True, dirs=None, stream=None):
-    """gp_bfs / gp_bfs_directed.  Returns (level, parent or None, stats dict)."""
+def bfs(g: Graph, src: int, mode=AUTO, level=None, parent=None, want_parent=True, dirs=None, stream=None,
+        want_stats=True):
+    """gp_bfs / gp_bfs_directed.  Returns (level, parent or None, stats dict or
+    None).  With want_stats=False and device outputs the call returns without
+    waiting for the search (a barrier timeout is then reported by the next
+    search on the graph)."""
     torch = _torch()
     if level is None:
         level = torch.empty(g.n, dtype=torch.int32, device="cuda")
     if parent is None and want_parent:
         parent = torch.empty(g.n, dtype=torch.int32, device="cuda")
     st = gp_bfs_stats()
+    stp = ctypes.byref(st) if want_stats else None
     lib = load()
     if dirs is None:
-        _check(lib.gp_bfs(g.handle, int(src), int(mode), _ptr(level), _ptr(parent), ctypes.byref(st),
-                          _stream_ptr(stream)), "gp_bfs")
+        _check(lib.gp_bfs(g.handle, int(src), int(mode), _ptr(level), _ptr(parent), stp, _stream_ptr(stream)),
+               "gp_bfs")
     else:
         d = np.ascontiguousarray(np.asarray(dirs, dtype=np.int8))
-        _check(lib.gp_bfs_directed(g.handle, int(src), _ptr(d), int(d.shape[0]), _ptr(level), _ptr(parent),
-                                   ctypes.byref(st), _stream_ptr(stream)), "gp_bfs_directed")
+        _check(lib.gp_bfs_directed(g.handle, int(src), _ptr(d), int(d.shape[0]), _ptr(level), _ptr(parent), stp,
+                                   _stream_ptr(stream)), "gp_bfs_directed")
+    if not want_stats:
+        return level, parent, None
     L = min(st.levels, BFS_MAX_LEVELS)
     stats = {"levels": st.levels, "switches": st.switches, "reached": st.reached,
              "edges_examined": st.edges_examined, "edges_reached": st.edges_reached, "ms": st.ms,

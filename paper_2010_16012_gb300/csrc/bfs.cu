@@ -12,9 +12,14 @@
 //             stops at the first u in the frontier bitmap; only v's owner
 //             writes v's level, parent and bitmap bit (a warp owns one 32-bit
 //             bitmap word), so vertex state needs no atomics.
-// The frontier is a sparse queue after a top-down level and a bitmap after a
-// bottom-up level; k_queue_to_bits / k_bits_to_queue convert when the
-// direction changes.  Frontier vertices whose out-degree exceeds
+// A top-down level produces the next frontier both as a sparse queue and as a
+// bitmap (the winner of each claim also sets the vertex's bit), so a switch to
+// bottom-up needs no conversion; a bottom-up level produces only the bitmap,
+// which is compacted into a queue when the search switches back.  Bottom-up
+// levels visit only the 32-vertex words that still hold candidates: a bitmap
+// of vertices with in-edges that may be unvisited, thinned by each bottom-up
+// level (vertices claimed top-down are dropped when a bottom-up level meets
+// them).  Frontier vertices whose out-degree exceeds
 // push_light_max are kept as chunk ids of the push chunk table, so one warp
 // handles at most chunk_edges of a hub's edges.
 // The direction heuristic (not given in the paper, which cites direction-
@@ -52,7 +57,8 @@ struct BfsArgs {
     const int32_t *h_cur;
     int32_t *h_next;
     const uint32_t *bits_cur;
-    uint32_t *bits_next;
+    uint32_t *bits_next;   // next frontier bitmap (zero on entry)
+    uint32_t *unvis;       // bottom-up candidates; each word owned by one warp of a bottom-up level
     BfsCtr *cur, *nxt;
     int32_t L;  // level being expanded: new vertices get L + 1
 };
@@ -87,12 +93,31 @@ __device__ __forceinline__ void frontier_append(const BfsArgs &a, bool take, int
     }
 }
 
-// Claim w from u at level L+1; returns true for the winner.
+// Claim w from u at level L+1; returns true for the winner, which also marks w
+// in the next frontier's bitmap and removes it from the bottom-up candidates.
 __device__ __forceinline__ bool td_claim(const BfsArgs &a, int32_t w, int32_t u) {
     if (a.level[w] != -1) return false;
     if (atomicCAS(a.level + w, -1, a.L + 1) != -1) return false;
     if (a.parent) a.parent[w] = u;
+    const uint32_t bit = 1u << (w & 31);
+    atomicOr(a.bits_next + (w >> 5), bit);
+    atomicAnd(a.unvis + (w >> 5), ~bit);
     return true;
+}
+
+// Position of the j-th (0-based) set bit of x (j < popc(x)).
+__device__ __forceinline__ int nth_set_bit(uint32_t x, int j) {
+    int pos = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        const int c = __popc(x & ((1u << s) - 1u));
+        if (j >= c) {
+            j -= c;
+            x >>= s;
+            pos += s;
+        }
+    }
+    return pos;
 }
 
 __device__ void flush_counters(const BfsArgs &a, unsigned long long nf, unsigned long long mf, unsigned long long mu,
@@ -179,49 +204,97 @@ __device__ void bfs_topdown_step(const BfsArgs &a) {
     flush_counters(a, nf, mf, mu, ex);
 }
 
-// Bottom-up level: warp per 32-vertex bitmap word, lane per vertex, early exit.
+// Bottom-up level.  A warp takes 32 consecutive words of the candidate bitmap
+// (unvisited vertices with in-edges), ranks their candidates with a warp
+// prefix sum, and gives them out 32 at a time, one per lane, so every lane works
+// on a real candidate whatever the density; each scans its in-edges and stops
+// at the first frontier vertex.  Found bits gather in the warp's shared words,
+// then each lane writes its own word of the next frontier (zero on entry) and
+// of the candidates: each word has one writer, so vertex state needs no atomics.
+#ifndef GP_BFS_WARPS
+#define GP_BFS_WARPS 32
+#endif
+#ifndef GP_BFS_MINB
+#define GP_BFS_MINB 1
+#endif
+constexpr int BFS_WARPS = GP_BFS_WARPS;  // warps per block of the persistent kernel
+#ifndef GP_BU_SCAN
+#define GP_BU_SCAN 4
+#endif
+constexpr int BU_SCAN = GP_BU_SCAN;  // in-edges a bottom-up lane checks per step
+
 __device__ void bfs_bottomup_step(const BfsArgs &a) {
-    const int lane = lane_id();
+    __shared__ uint32_t s_found[BFS_WARPS][32];
+    const int lane = lane_id(), wib = threadIdx.x >> 5;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nwords = (a.n + 31) >> 5;
     unsigned long long nf = 0, mf = 0, mu = 0, ex = 0;
-    for (int64_t wd = warp; wd < nwords; wd += nwarps) {
-        const int64_t v = wd * 32 + lane;
-        bool found = false;
-        if (v < a.n && a.level[v] == -1) {
-            const int64_t b = a.csc_off[v], e = a.csc_off[v + 1];
-            for (int64_t j = b; j < e; ++j) {
-                const int32_t u = __ldg(a.csc_idx + j);
-                ++ex;
-                if ((a.bits_cur[u >> 5] >> (u & 31)) & 1u) {
-                    a.level[v] = a.L + 1;
-                    if (a.parent) a.parent[v] = u;
-                    found = true;
-                    break;
+    for (int64_t base = warp * 32; base < nwords; base += nwarps * 32) {
+        const int64_t wd = base + lane;
+        const uint32_t cand = wd < nwords ? a.unvis[wd] : 0u;
+        const int cnt = __popc(cand);
+        const int incl = warp_incl_scan(cnt);
+        const int excl = incl - cnt;
+        const int total = __shfl_sync(FULL, incl, 31);
+        if (total == 0) continue;  // uniform across the warp
+        s_found[wib][lane] = 0u;
+        __syncwarp();
+        for (int r = 0; r < total; r += 32) {
+            const int id = r + lane;
+            int k = 0;  // the lane (word) whose candidates [excl, incl) hold id
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1) {
+                const int ek = __shfl_sync(FULL, excl, k + st);
+                if (ek <= id) k += st;
+            }
+            const uint32_t kc = __shfl_sync(FULL, cand, k);
+            const int kex = __shfl_sync(FULL, excl, k);
+            if (id < total) {
+                const int bit = nth_set_bit(kc, id - kex);
+                const int64_t v = (base + k) * 32 + bit;
+                const int64_t b = a.csc_off[v], e = a.csc_off[v + 1];
+                const int64_t dout = a.csr_off[v + 1] - a.csr_off[v];
+                // BU_SCAN in-edges per step: their bitmap probes are independent
+                for (int64_t j = b; j < e; j += BU_SCAN) {
+                    int32_t u[BU_SCAN];
+                    bool hit[BU_SCAN];
+#pragma unroll
+                    for (int q = 0; q < BU_SCAN; ++q) u[q] = j + q < e ? __ldg(a.csc_idx + j + q) : 0;
+#pragma unroll
+                    for (int q = 0; q < BU_SCAN; ++q)
+                        hit[q] = j + q < e && ((a.bits_cur[u[q] >> 5] >> (u[q] & 31)) & 1u);
+                    int first = -1;
+#pragma unroll
+                    for (int q = BU_SCAN - 1; q >= 0; --q)
+                        if (hit[q]) first = q;
+                    if (first >= 0) {
+                        int32_t p = u[0];
+#pragma unroll
+                        for (int q = 1; q < BU_SCAN; ++q)
+                            if (q == first) p = u[q];
+                        ex += (unsigned long long)(first + 1);
+                        a.level[v] = a.L + 1;
+                        if (a.parent) a.parent[v] = p;
+                        atomicOr(&s_found[wib][k], 1u << bit);
+                        nf += 1;
+                        mf += (unsigned long long)dout;
+                        mu += (unsigned long long)(e - b);
+                        break;
+                    }
+                    ex += (unsigned long long)(e - j < BU_SCAN ? e - j : BU_SCAN);
                 }
             }
-            if (found) {
-                nf += 1;
-                mf += (unsigned long long)(a.csr_off[v + 1] - a.csr_off[v]);
-                mu += (unsigned long long)(e - b);
-            }
         }
-        const unsigned word = __ballot_sync(FULL, found);
-        if (lane == 0) a.bits_next[wd] = word;
+        __syncwarp();
+        const uint32_t fw = s_found[wib][lane];
+        if (fw) {
+            a.bits_next[wd] = fw;
+            a.unvis[wd] = cand & ~fw;
+        }
+        __syncwarp();
     }
     flush_counters(a, nf, mf, mu, ex);
-}
-
-// Frontier queue (+ heavy chunk ids) -> bitmap; the bitmap must be zero.
-__device__ void queue_to_bits_step(const BfsCtr *cur, const int32_t *queue, const int32_t *h, const Chunk *chunks,
-                                   uint32_t *bits) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t q_len = (int64_t)((volatile BfsCtr *)cur)->q_len, h_len = (int64_t)((volatile BfsCtr *)cur)->h_len;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < q_len + h_len; i += stride) {
-        const int32_t v = i < q_len ? queue[i] : chunks[h[i - q_len]].v;
-        atomicOr(bits + (v >> 5), 1u << (v & 31));
-    }
 }
 
 // Bitmap -> queue + heavy chunk ids (the counters' q_len/h_len must be zero).
@@ -256,7 +329,8 @@ struct BfsRun {
     BfsArgs base;  // graph arrays, level/parent, chunk table
     int32_t *queue[2];
     int32_t *hchunk[2];
-    uint32_t *bits[2];
+    uint32_t *bits[3];      // a ring: level k's frontier bitmap in bits[k % 3]
+    const uint32_t *nzin;   // vertices with in-edges
     BfsCtr *ctr;  // [3], a ring
     const int8_t *dirs;  // forced directions (device) or nullptr
     int32_t ndirs;
@@ -271,12 +345,12 @@ struct BfsRun {
 
 // 1024-thread blocks: fewer blocks arrive at each grid barrier (one global
 // counter), which is what a level's fixed cost is made of.
-constexpr int BFS_THREADS = 1024;
+constexpr int BFS_THREADS = BFS_WARPS * 32;
 
 // Every block keeps identical copies of the frontier statistics (read from the
 // counters after each barrier), so all blocks take the same direction decision
 // without a host round trip.
-__global__ void __launch_bounds__(BFS_THREADS) k_bfs_persistent(BfsRun R) {
+__global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(BfsRun R) {
     const int64_t n = R.base.n;
     const int64_t gthread = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
@@ -287,10 +361,14 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs_persistent(BfsRun R) {
     }
     if (gthread < 3 * (int64_t)(sizeof(BfsCtr) / sizeof(unsigned long long)))
         ((unsigned long long *)R.ctr)[gthread] = 0;
-    for (int64_t i = gthread; i < nwords; i += nthreads) R.bits[0][i] = 0u;
+    for (int64_t i = gthread; i < nwords; i += nthreads) {
+        R.bits[0][i] = 0u;
+        R.bits[1][i] = 0u;
+        R.base.unvis[i] = R.nzin[i];
+    }
     if (!grid_sync(R.sync, gridDim.x)) return;
     BfsArgs a = R.base;
-    // frontier 0 = {src}, in queue form, counters in ctr[0]
+    // frontier 0 = {src}, as a queue (counters in ctr[0]) and in bits[0]
     if (blockIdx.x == 0 && threadIdx.x < 32) {
         a.nxt = R.ctr;
         a.queue_next = R.queue[0];
@@ -300,6 +378,8 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs_persistent(BfsRun R) {
         if (take) {
             a.level[R.src] = 0;
             if (a.parent) a.parent[R.src] = R.src;
+            R.bits[0][R.src >> 5] = 1u << (R.src & 31);
+            R.base.unvis[R.src >> 5] &= ~(1u << (R.src & 31));
         }
         frontier_append(a, take, R.src, nf, mf, mu);
         if (take) {
@@ -317,11 +397,10 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs_persistent(BfsRun R) {
     bool in_queue = true;
     long long reached = 1, examined = 0, edges_reached = (long long)mf;
     constexpr int CW = (int)(sizeof(BfsCtr) / sizeof(unsigned long long));
-    // Counters form a ring of three: level L reads slot L%3 (its frontier) and
-    // fills slot (L+1)%3; slot (L+2)%3, last used by level L-1, is zeroed during
-    // level L's step for level L+1, so no barrier is spent on clearing it.
-    // Bitmaps: bits[b] is the next level's bitmap slot; the top-down step clears
-    // the other slot while it runs, so a switch to bottom-up finds it zero.
+    // Counters and bitmaps form rings of three: level L reads slot L%3 (its
+    // frontier) and fills slot (L+1)%3; slot (L+2)%3, last used by level L-1, is
+    // zeroed during level L's step for level L+1, so no barrier is spent on
+    // clearing it.
     while (nf > 0) {
         int dir;
         if (R.dirs) {
@@ -335,16 +414,15 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs_persistent(BfsRun R) {
         }
         if (L > 0 && dir != prev_dir) ++switches;
         const int nxt = (cur + 1) % 3, spare = (cur + 2) % 3;
-        const int bc = L & 1, bn = bc ^ 1;  // bitmap slots: current frontier, next frontier
         a.L = L;
         a.cur = R.ctr + cur;
         a.nxt = R.ctr + nxt;
         a.queue_cur = R.queue[L & 1];
         a.h_cur = R.hchunk[L & 1];
-        a.bits_cur = R.bits[bc];
-        a.queue_next = R.queue[bn];
-        a.h_next = R.hchunk[bn];
-        a.bits_next = R.bits[bn];
+        a.bits_cur = R.bits[cur];
+        a.queue_next = R.queue[(L + 1) & 1];
+        a.h_next = R.hchunk[(L + 1) & 1];
+        a.bits_next = R.bits[nxt];
         if (dir == GP_PUSH && !in_queue) {
             BfsArgs c = a;  // the queue form of the current frontier goes to its own slot
             c.nxt = a.cur;
@@ -352,15 +430,11 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs_persistent(BfsRun R) {
             c.h_next = R.hchunk[L & 1];
             bits_to_queue_step(c);
             if (!grid_sync(R.sync, gridDim.x)) return;
-        } else if (dir == GP_PULL && in_queue) {
-            queue_to_bits_step(R.ctr + cur, R.queue[L & 1], R.hchunk[L & 1], a.push_chunks, R.bits[bc]);
-            if (!grid_sync(R.sync, gridDim.x)) return;
         }
         if (gthread < CW) ((unsigned long long *)(R.ctr + spare))[gthread] = 0;
+        for (int64_t i = gthread; i < nwords; i += nthreads) R.bits[spare][i] = 0u;
         if (dir == GP_PUSH) {
             bfs_topdown_step(a);
-            // clear the next level's bitmap slot in case it switches to bottom-up
-            for (int64_t i = gthread; i < nwords; i += nthreads) R.bits[bn][i] = 0u;
             in_queue = true;
         } else {
             bfs_bottomup_step(a);
@@ -395,7 +469,28 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs_persistent(BfsRun R) {
 
 // ------------------------------------------------------------------ driver
 
+// Bit v of word v/32: vertex v has in-edges.
+__global__ void k_nzin_bits(int64_t n, const int64_t *csc_off, uint32_t *bits) {
+    const int64_t nwords = (n + 31) >> 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t wd = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; wd < nwords; wd += stride) {
+        uint32_t word = 0;
+        const int64_t v0 = wd * 32, v1 = min(n, v0 + 32);
+        int64_t prev = csc_off[v0];
+        for (int64_t v = v0; v < v1; ++v) {
+            const int64_t next = csc_off[v + 1];
+            if (next > prev) word |= 1u << (v - v0);
+            prev = next;
+        }
+        bits[wd] = word;
+    }
+}
+
 void release_bfs_work(gp_graph *g, cudaStream_t s) {
+    if (g->bfs.done_ev) {
+        cudaEventSynchronize(g->bfs.done_ev);
+        cudaEventDestroy(g->bfs.done_ev);
+    }
     if (g->bfs.ctr_host) cudaFreeHost(g->bfs.ctr_host);
     g->bfs.ctr_host = nullptr;
     g->bfs.mem.release(s);
@@ -411,7 +506,13 @@ static int ensure_bfs_work(gp_graph *g, cudaStream_t s) {
     for (int i = 0; i < 2; ++i) {
         GP_TRY(w.mem.alloc(w.queue[i], n, s));
         GP_TRY(w.mem.alloc(w.hchunk[i], hcap, s));
-        GP_TRY(w.mem.alloc(w.bits[i], words, s));
+    }
+    for (int i = 0; i < 3; ++i) GP_TRY(w.mem.alloc(w.bits[i], words, s));
+    GP_TRY(w.mem.alloc(w.unvis, words, s));
+    GP_TRY(w.mem.alloc(w.nzin, words, s));
+    if (g->n > 0) {
+        k_nzin_bits<<<(int)std::min<size_t>((words + 255) / 256, 4096), 256, 0, s>>>(g->n, g->csc_off, w.nzin);
+        GP_CUDA(cudaGetLastError());
     }
     BfsCtr *c = nullptr;
     GP_TRY(w.mem.alloc(c, 3, s));
@@ -433,6 +534,7 @@ static int ensure_bfs_work(gp_graph *g, cudaStream_t s) {
     if (per_sm < 1) return set_error(GP_ERR_UNSUPPORTED, "BFS kernel does not fit on an SM");
     w.grid = per_sm * g->num_sms;
     GP_CUDA(cudaMallocHost(&w.ctr_host, sizeof(BfsSummary) + GP_BFS_MAX_LEVELS * sizeof(BfsLevelStat) + sizeof(GridSync)));
+    GP_CUDA(cudaEventCreateWithFlags(&w.done_ev, cudaEventDisableTiming));
     w.ready = true;
     return GP_OK;
 }
@@ -445,6 +547,18 @@ static int bfs_run(const gp_graph *gc, int32_t src, int mode, const int8_t *dirs
     if (!level_out) return set_error(GP_ERR_INVALID, "gp_bfs: level_out is NULL");
     GP_TRY(ensure_bfs_work(g, s));
     BfsWork &w = g->bfs;
+    char *h = (char *)w.ctr_host;
+    BfsSummary *hs = (BfsSummary *)h;
+    BfsLevelStat *hl = (BfsLevelStat *)(h + sizeof(BfsSummary));
+    GridSync *hsync = (GridSync *)(h + sizeof(BfsSummary) + GP_BFS_MAX_LEVELS * sizeof(BfsLevelStat));
+    if (w.pending) {  // the barrier status of the previous, asynchronous search
+        GP_CUDA(cudaEventSynchronize(w.done_ev));
+        w.pending = false;
+        if (hsync->err) {
+            hsync->err = 0;
+            return set_error(GP_ERR_TIMEOUT, "BFS: a grid barrier wait ran out in the previous asynchronous search");
+        }
+    }
     if (stats) memset(stats, 0, sizeof(*stats));
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (stats) {
@@ -478,8 +592,10 @@ static int bfs_run(const gp_graph *gc, int32_t src, int mode, const int8_t *dirs
     for (int i = 0; i < 2; ++i) {
         R.queue[i] = w.queue[i];
         R.hchunk[i] = w.hchunk[i];
-        R.bits[i] = w.bits[i];
     }
+    for (int i = 0; i < 3; ++i) R.bits[i] = w.bits[i];
+    R.nzin = w.nzin;
+    R.base.unvis = w.unvis;
     R.ctr = (BfsCtr *)w.ctr;
     R.mode = mode;
     R.alpha = g->opt.bfs_alpha;
@@ -504,11 +620,14 @@ static int bfs_run(const gp_graph *gc, int32_t src, int mode, const int8_t *dirs
     }
     if (!lvl_dev) GP_CUDA(cudaMemcpyAsync(level_out, level, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     if (!par_dev) GP_CUDA(cudaMemcpyAsync(parent_out, parent, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    char *h = (char *)w.ctr_host;
-    BfsSummary *hs = (BfsSummary *)h;
-    BfsLevelStat *hl = (BfsLevelStat *)(h + sizeof(BfsSummary));
-    GridSync *hsync = (GridSync *)(h + sizeof(BfsSummary) + GP_BFS_MAX_LEVELS * sizeof(BfsLevelStat));
     GP_CUDA(cudaMemcpyAsync(hsync, w.sync, sizeof(GridSync), cudaMemcpyDeviceToHost, s));
+    if (!stats && lvl_dev && par_dev) {
+        // nothing for the host to read: return without waiting; the barrier
+        // status is checked by the next search on this graph
+        GP_CUDA(cudaEventRecord(w.done_ev, s));
+        w.pending = true;
+        return GP_OK;
+    }
     if (stats) {
         GP_CUDA(cudaMemcpyAsync(hs, w.summary, sizeof(BfsSummary), cudaMemcpyDeviceToHost, s));
         GP_CUDA(cudaMemcpyAsync(hl, w.stats, GP_BFS_MAX_LEVELS * sizeof(BfsLevelStat), cudaMemcpyDeviceToHost, s));

@@ -151,7 +151,9 @@ struct BfsWork {
     bool ready = false;
     int32_t *queue[2] = {nullptr, nullptr};  // light frontier vertices
     int32_t *hchunk[2] = {nullptr, nullptr}; // heavy frontier: indices into the push chunk table
-    uint32_t *bits[2] = {nullptr, nullptr};  // frontier bitmaps
+    uint32_t *bits[3] = {nullptr, nullptr, nullptr};  // frontier bitmaps, a ring: level k in bits[k % 3]
+    uint32_t *unvis = nullptr;               // vertices possibly unvisited with in-edges (bottom-up candidates)
+    uint32_t *nzin = nullptr;                // vertices with in-edges (the initial candidates)
     int32_t *level_dev = nullptr, *parent_dev = nullptr;  // when outputs are host memory
     void *ctr = nullptr;                     // device counters
     void *ctr_host = nullptr;                // pinned mirror of the summary, level stats and barrier word
@@ -160,6 +162,8 @@ struct BfsWork {
     void *sync = nullptr;                    // grid barrier word
     int8_t *dirs = nullptr;                  // forced directions (device copy)
     int grid = 0;                            // blocks of the cooperative launch
+    cudaEvent_t done_ev = nullptr;           // end of the last asynchronous search
+    bool pending = false;                    // its barrier status not yet checked
     Arena mem;
 };
 
@@ -296,7 +300,9 @@ struct GridSync {
 
 constexpr unsigned long long GRID_SPIN_LIMIT = 1ull << 24;  // ~2 s of 128 ns sleeps
 
-__device__ __forceinline__ bool grid_sync(GridSync *gs, unsigned nblocks) {
+// Returns false (and sets gs->err for every block) when a wait runs past
+// `limit` sleeps or another block has already given up.
+__device__ __forceinline__ bool grid_sync(GridSync *gs, unsigned nblocks, unsigned long long limit = GRID_SPIN_LIMIT) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -312,7 +318,7 @@ __device__ __forceinline__ bool grid_sync(GridSync *gs, unsigned nblocks) {
         } else {
             unsigned long long spins = 0;
             while (*vgen == g0) {
-                if (*verr || ++spins > GRID_SPIN_LIMIT) {
+                if (*verr || ++spins > limit) {
                     atomicExch(&gs->err, 1);
                     break;
                 }

@@ -710,6 +710,38 @@ int gp_selftest_narrow(int64_t n, const double *in, float *ours, float *hw, void
     return GP_OK;
 }
 
+// Every block but `absent` enters one grid barrier whose waits give up after
+// `spins` sleeps.
+static __global__ void k_selftest_barrier(GridSync *gs, int absent, unsigned long long spins) {
+    if ((int)blockIdx.x == absent) return;
+    grid_sync(gs, gridDim.x, spins);
+}
+
+int gp_selftest_barrier(int absent, void *stream) {
+    clear_error();
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 0, coop = 0;
+    GP_CUDA(cudaGetDevice(&dev));
+    GP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GP_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) return set_error(GP_ERR_UNSUPPORTED, "gp_selftest_barrier: no cooperative launch on this device");
+    if (absent >= sms) return set_error(GP_ERR_INVALID, "gp_selftest_barrier: block %d outside the grid of %d", absent, sms);
+    GridSync *gs = nullptr;
+    GP_CUDA(cudaMalloc(&gs, sizeof(GridSync)));
+    GridSync host = {};
+    cudaError_t e = cudaMemsetAsync(gs, 0, sizeof(GridSync), s);
+    unsigned long long spins = 1ull << 16;  // a few tens of milliseconds
+    void *args[] = {&gs, &absent, &spins};
+    if (e == cudaSuccess)
+        e = cudaLaunchCooperativeKernel((const void *)k_selftest_barrier, dim3((unsigned)sms), dim3(128), args, 0, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&host, gs, sizeof(GridSync), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(gs);
+    if (e != cudaSuccess) return set_error(GP_ERR_CUDA, "gp_selftest_barrier: %s", cudaGetErrorString(e));
+    if (host.err) return set_error(GP_ERR_TIMEOUT, "gp_selftest_barrier: a grid barrier wait ran out");
+    return GP_OK;
+}
+
 int gp_profile_enable(int on) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_prof_on = on != 0;

@@ -131,3 +131,42 @@ def test_invalid_source(gp):
         assert e.value.status == gp.ERR_INVALID
     with pytest.raises(gp.GpError):
         gp.bfs(G, 0, dirs=[0, 2])
+
+
+def test_async_searches_back_to_back(gp):
+    """Searches enqueued without statistics return before they run; eight of
+    them back to back on one stream, each into its own buffers, then a
+    synchronous one."""
+    import torch
+
+    g = gg.rmat(12, 16, seed=5, symmetrize=False)
+    G = gp.Graph.from_graphgen(g)
+    O = oracle.OracleGraph.from_graph(g)
+    srcs = gg.pick_vertices(g, 8, seed=6)
+    lv = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in srcs]
+    pa = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in srcs]
+    modes = [gp.AUTO, gp.PUSH, gp.PULL, gp.AUTO] * 2
+    for s, l, p, mode in zip(srcs, lv, pa, modes):
+        _, _, st = gp.bfs(G, int(s), mode, level=l, parent=p, want_stats=False)
+        assert st is None
+    torch.cuda.synchronize()
+    for s, l, p in zip(srcs, lv, pa):
+        check(g, O, int(s), l, p)
+    level, parent, st = gp.bfs(G, int(srcs[0]), gp.AUTO)
+    check(g, O, int(srcs[0]), level, parent)
+    assert st["reached"] == int((to_np(level) >= 0).sum())
+
+
+def test_candidate_bitmap_after_top_down_levels(gp):
+    """Bottom-up levels after top-down ones meet vertices that top-down claimed
+    and vertices without in-edges (directed graph with sources-only vertices):
+    every direction sequence gives the oracle's levels."""
+    src_v = np.array([0, 0, 1, 2, 3, 5, 6, 6, 7, 9, 9, 10, 11], dtype=np.int64)
+    dst_v = np.array([1, 2, 3, 4, 4, 6, 7, 8, 8, 10, 3, 11, 12], dtype=np.int64)
+    g = gg.from_edges(40, np.concatenate([src_v, [20, 21]]), np.concatenate([dst_v, [0, 0]]))
+    G = gp.Graph.from_graphgen(g)
+    O = oracle.OracleGraph.from_graph(g)
+    for src in (0, 20, 9, 5):
+        for dirs in ([0, 1], [1, 0], [0, 0, 1], [1, 1, 0, 1], [0, 1, 0, 1, 0]):
+            level, parent, _ = gp.bfs(G, src, dirs=dirs)
+            check(g, O, src, level, parent)

@@ -1,8 +1,10 @@
-"""The library's integer-arithmetic binary64 -> binary32 rounding (the push
-epilogue rounds its FP64 sums with it) against the hardware conversion on the
-same device: identical bits over the binary32 normal range -- random encodings
-across the whole binary64 range, exact ties in both parities, carries into the
-exponent, the overflow edge -- and signed zero below 2^-126."""
+"""Device self-checks.  The library's integer-arithmetic binary64 -> binary32
+rounding (the push epilogue rounds its FP64 sums with it) against the hardware
+conversion on the same device: identical bits over the binary32 normal range --
+random encodings across the whole binary64 range, exact ties in both parities,
+carries into the exponent, the overflow edge -- and signed zero below 2^-126.
+The bounded grid barrier: a missing block makes the others time out with an
+error status instead of hanging."""
 import numpy as np
 import pytest
 
@@ -59,3 +61,22 @@ def test_narrow_rejects_bad_arguments(gp):
     assert lib.gp_selftest_narrow(-1, None, None, None, None) == gp.ERR_INVALID
     assert lib.gp_selftest_narrow(4, None, None, None, None) == gp.ERR_INVALID
     assert lib.gp_selftest_narrow(0, None, None, None, None) == gp.OK
+
+
+def test_grid_barrier_timeout_is_reported_and_context_survives(gp):
+    """A block that never reaches the grid barrier: the others give up after
+    their bounded wait, the call reports GP_ERR_TIMEOUT, and the device context
+    keeps working (a BFS afterwards is correct)."""
+    import graphgen as gg
+    import oracle
+
+    lib = gp.load()
+    assert lib.gp_selftest_barrier(-1, None) == gp.OK
+    assert lib.gp_selftest_barrier(3, None) == gp.ERR_TIMEOUT
+    assert b"ran out" in lib.gp_last_error()
+    assert lib.gp_selftest_barrier(1 << 30, None) == gp.ERR_INVALID
+    assert lib.gp_selftest_barrier(-1, None) == gp.OK
+    g = gg.rmat(10, 8, seed=3)
+    level, _, _ = gp.bfs(gp.Graph.from_graphgen(g), 0, gp.AUTO)
+    ref, _ = oracle.OracleGraph.from_graph(g).bfs(0)
+    assert np.array_equal(level.cpu().numpy(), ref)
