@@ -60,12 +60,14 @@ struct BfsArgs {
     uint32_t *bits_next;   // next frontier bitmap (zero on entry)
     uint32_t *unvis;       // bottom-up candidates; each word owned by one warp of a bottom-up level
     BfsCtr *cur, *nxt;
-    int32_t L;  // level being expanded: new vertices get L + 1
+    int32_t L;           // level being expanded: new vertices get L + 1
+    int32_t make_queue;  // top-down: also build the next frontier's queue
 };
 
-// Append w (newly visited) to the next frontier: light vertices to the queue
-// (warp-aggregated), heavy ones as their chunk ids.  Must be called by all 32
-// lanes together; `take` marks the lanes that append.
+// Count w (newly visited) into the next frontier's statistics and, when the
+// level builds a queue, append it: light vertices to the queue (warp-
+// aggregated), heavy ones as their chunk ids.  Must be called by all 32 lanes
+// together; `take` marks the lanes that append.
 __device__ __forceinline__ void frontier_append(const BfsArgs &a, bool take, int32_t w, unsigned long long &nf,
                                                 unsigned long long &mf, unsigned long long &mu) {
     const int lane = lane_id();
@@ -75,8 +77,9 @@ __device__ __forceinline__ void frontier_append(const BfsArgs &a, bool take, int
         mf += (unsigned long long)dout;
         mu += (unsigned long long)(a.csc_off[w + 1] - a.csc_off[w]);
         nf += 1;
-        r = a.push_rank[w];
+        if (a.make_queue) r = a.push_rank[w];
     }
+    if (!a.make_queue) return;  // uniform
     const bool light = take && r < 0;
     const unsigned bal = __ballot_sync(FULL, light);
     if (bal) {
@@ -138,6 +141,7 @@ __device__ void flush_counters(const BfsArgs &a, unsigned long long nf, unsigned
 // ------------------------------------------------------------------ level steps (device functions)
 
 constexpr int TD_SPLIT = 4;
+constexpr unsigned long long TD_QUEUE_EDGES = 1ull << 14;
 
 // Top-down level: heavy frontier vertices (chunk ids) split over warps, light
 // ones 32 queue entries per warp with a merged edge stream.
@@ -297,18 +301,35 @@ __device__ void bfs_bottomup_step(const BfsArgs &a) {
     flush_counters(a, nf, mf, mu, ex);
 }
 
-// Bitmap -> queue + heavy chunk ids (the counters' q_len/h_len must be zero).
+// Bitmap -> queue + heavy chunk ids (the counters' q_len/h_len must be zero):
+// a warp ranks the set bits of 32 words and appends them 32 at a time.
 __device__ void bits_to_queue_step(const BfsArgs &a) {
+    const int lane = lane_id();
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nwords = (a.n + 31) >> 5;
     unsigned long long nf = 0, mf = 0, mu = 0;  // already counted by the level that made the bitmap
-    for (int64_t wd = warp; wd < nwords; wd += nwarps) {
-        const uint32_t word = a.bits_cur[wd];
-        if (!word) continue;  // uniform across the warp
-        const int32_t v = (int32_t)(wd * 32 + lane_id());
-        const bool take = (word >> lane_id()) & 1u;
-        frontier_append(a, take, v, nf, mf, mu);
+    for (int64_t base = warp * 32; base < nwords; base += nwarps * 32) {
+        const int64_t wd = base + lane;
+        const uint32_t word = wd < nwords ? a.bits_cur[wd] : 0u;
+        const int cnt = __popc(word);
+        const int incl = warp_incl_scan(cnt);
+        const int excl = incl - cnt;
+        const int total = __shfl_sync(FULL, incl, 31);
+        for (int r = 0; r < total; r += 32) {
+            const int id = r + lane;
+            int k = 0;
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1) {
+                const int ek = __shfl_sync(FULL, excl, k + st);
+                if (ek <= id) k += st;
+            }
+            const uint32_t kw = __shfl_sync(FULL, word, k);
+            const int kex = __shfl_sync(FULL, excl, k);
+            const bool take = id < total;
+            const int32_t v = take ? (int32_t)((base + k) * 32 + nth_set_bit(kw, id - kex)) : 0;
+            frontier_append(a, take, v, nf, mf, mu);
+        }
     }
 }
 
@@ -355,40 +376,36 @@ __global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(Bfs
     const int64_t gthread = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int64_t nwords = (n + 31) >> 5;
+    // level/parent, counters, bitmaps and candidates set for frontier 0 = {src}
+    const int32_t src = R.src;
+    const int32_t s_rank = R.base.push_rank[src];
+    const int64_t s_c0 = s_rank >= 0 ? R.base.push_cstart[s_rank] : 0;
+    const int64_t s_c1 = s_rank >= 0 ? R.base.push_cstart[s_rank + 1] : 0;
     for (int64_t v = gthread; v < n; v += nthreads) {
-        R.base.level[v] = -1;
-        if (R.base.parent) R.base.parent[v] = -1;
+        R.base.level[v] = v == src ? 0 : -1;
+        if (R.base.parent) R.base.parent[v] = v == src ? src : -1;
     }
-    if (gthread < 3 * (int64_t)(sizeof(BfsCtr) / sizeof(unsigned long long)))
-        ((unsigned long long *)R.ctr)[gthread] = 0;
+    constexpr int CW = (int)(sizeof(BfsCtr) / sizeof(unsigned long long));
+    if (gthread < 3 * CW) {
+        unsigned long long val = 0;  // ctr[0] describes {src}; ctr[1], ctr[2] start at zero
+        if (gthread == 0) val = s_rank < 0 ? 1 : 0;                                                 // q_len
+        if (gthread == 1) val = (unsigned long long)(s_c1 - s_c0);                                  // h_len
+        if (gthread == 2) val = 1;                                                                  // nf
+        if (gthread == 3) val = (unsigned long long)(R.base.csr_off[src + 1] - R.base.csr_off[src]);  // mf
+        if (gthread == 4) val = (unsigned long long)(R.base.csc_off[src + 1] - R.base.csc_off[src]);  // mu_dec
+        ((unsigned long long *)R.ctr)[gthread] = val;
+    }
+    if (gthread == 0 && s_rank < 0) R.queue[0][0] = src;
+    for (int64_t j = gthread; j < s_c1 - s_c0; j += nthreads) R.hchunk[0][j] = (int32_t)(s_c0 + j);
+    const int64_t sw = src >> 5;
+    const uint32_t sbit = 1u << (src & 31);
     for (int64_t i = gthread; i < nwords; i += nthreads) {
-        R.bits[0][i] = 0u;
+        R.bits[0][i] = i == sw ? sbit : 0u;
         R.bits[1][i] = 0u;
-        R.base.unvis[i] = R.nzin[i];
+        R.base.unvis[i] = R.nzin[i] & (i == sw ? ~sbit : ~0u);
     }
     if (!grid_sync(R.sync, gridDim.x)) return;
     BfsArgs a = R.base;
-    // frontier 0 = {src}, as a queue (counters in ctr[0]) and in bits[0]
-    if (blockIdx.x == 0 && threadIdx.x < 32) {
-        a.nxt = R.ctr;
-        a.queue_next = R.queue[0];
-        a.h_next = R.hchunk[0];
-        unsigned long long nf = 0, mf = 0, mu = 0;
-        const bool take = threadIdx.x == 0;
-        if (take) {
-            a.level[R.src] = 0;
-            if (a.parent) a.parent[R.src] = R.src;
-            R.bits[0][R.src >> 5] = 1u << (R.src & 31);
-            R.base.unvis[R.src >> 5] &= ~(1u << (R.src & 31));
-        }
-        frontier_append(a, take, R.src, nf, mf, mu);
-        if (take) {
-            R.ctr[0].nf = nf;
-            R.ctr[0].mf = mf;
-            R.ctr[0].mu_dec = mu;
-        }
-    }
-    if (!grid_sync(R.sync, gridDim.x)) return;
     volatile BfsCtr *vc = (volatile BfsCtr *)R.ctr;
     unsigned long long nf = vc[0].nf, mf = vc[0].mf;
     long long mu = (long long)R.m - (long long)vc[0].mu_dec;
@@ -396,7 +413,6 @@ __global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(Bfs
     int cur = 0, prev_dir = GP_PUSH, L = 0, switches = 0;
     bool in_queue = true;
     long long reached = 1, examined = 0, edges_reached = (long long)mf;
-    constexpr int CW = (int)(sizeof(BfsCtr) / sizeof(unsigned long long));
     // Counters and bitmaps form rings of three: level L reads slot L%3 (its
     // frontier) and fills slot (L+1)%3; slot (L+2)%3, last used by level L-1, is
     // zeroed during level L's step for level L+1, so no barrier is spent on
@@ -425,6 +441,7 @@ __global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(Bfs
         a.bits_next = R.bits[nxt];
         if (dir == GP_PUSH && !in_queue) {
             BfsArgs c = a;  // the queue form of the current frontier goes to its own slot
+            c.make_queue = 1;
             c.nxt = a.cur;
             c.queue_next = R.queue[L & 1];
             c.h_next = R.hchunk[L & 1];
@@ -434,8 +451,12 @@ __global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(Bfs
         if (gthread < CW) ((unsigned long long *)(R.ctr + spare))[gthread] = 0;
         for (int64_t i = gthread; i < nwords; i += nthreads) R.bits[spare][i] = 0u;
         if (dir == GP_PUSH) {
+            // a queue of the next frontier only when this frontier is small (so
+            // are the appends); otherwise the bitmap alone, compacted later if
+            // another top-down level follows
+            a.make_queue = mf < TD_QUEUE_EDGES;
             bfs_topdown_step(a);
-            in_queue = true;
+            in_queue = a.make_queue != 0;
         } else {
             bfs_bottomup_step(a);
             in_queue = false;
