@@ -424,9 +424,9 @@ __global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(Bfs
         } else if (R.mode == GP_PUSH || R.mode == GP_PULL) {
             dir = R.mode;
         } else if (prev_dir == GP_PUSH) {
-            dir = ((double)mf > (double)(mu > 0 ? mu : 0) / R.alpha) ? GP_PULL : GP_PUSH;
+            dir = ((float)mf * R.alpha > (float)(mu > 0 ? mu : 0)) ? GP_PULL : GP_PUSH;
         } else {
-            dir = ((double)nf < (double)n / R.beta && nf < prev_nf) ? GP_PUSH : GP_PULL;
+            dir = ((float)nf * R.beta < (float)n && nf < prev_nf) ? GP_PUSH : GP_PULL;
         }
         if (L > 0 && dir != prev_dir) ++switches;
         const int nxt = (cur + 1) % 3, spare = (cur + 2) % 3;

@@ -263,7 +263,36 @@ struct ResSum {
     __device__ __forceinline__ void add(float y, float x) { push(fabsf(y - x)); }
     __device__ __forceinline__ float getf() const { return s - c; }
     __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+    // Warp total (valid in every lane): compensated pairwise sums in FP32, one
+    // conversion to FP64 at the end.
+    __device__ __forceinline__ double warp_total() const {
+        float hi = s, lo = -c;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ohi = __shfl_xor_sync(0xffffffffu, hi, o), olo = __shfl_xor_sync(0xffffffffu, lo, o);
+            const float t = hi + ohi;  // error-free: t + e == hi + ohi (Knuth's two-sum)
+            const float bp = t - hi;
+            const float e = (hi - (t - bp)) + (ohi - bp);
+            hi = t;
+            lo = lo + olo + e;
+        }
+        return (double)hi + (double)lo;
+    }
 };
+
+// Block total of per-thread residual sums (valid in thread 0): warp totals
+// from warp_total, then an FP64 sum over the block's warps in warp order.
+__device__ __forceinline__ double block_residual(const ResSum &r, double *smem /* >= 32 entries */) {
+    const double wt = r.warp_total();
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) smem[w] = wt;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < nw; ++i) t += smem[i];
+    return t;
+}
 
 // binary64 -> binary32, round to nearest (ties to even), by integer operations
 // on the IEEE 754 encodings (1 sign, 11/8 exponent bits with bias 1023/127,

@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(256) k_na_sweep(int64_t n, int64_t m, const in
         }
     }
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(&sc->bad, 1u);
-    const double r = block_sum(res.get(), red);
+    const double r = block_residual(res, red);
     if (threadIdx.x == 0) sc->partials[blockIdx.x] = r;
 }
 

@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(512, GP_LIGHT_MIN_BLOCKS) k_pull_light(PrArgs 
             a.c_next[v] = y * c_factor(a, v);
         }
     }
-    const double r = block_sum(res.get(), sm);
+    const double r = block_residual(res, sm);
     if (threadIdx.x == 0) a.partials[blockIdx.x] = r;
 }
 
@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(256) k_push_epilogue(PrArgs a) {
         a.c_next[v] = y * c_factor(a, v);
         if (sizeof(T) != 8) x_reset[v] = 0.f;  // the next sweep accumulates into this buffer
     }
-    const double r = block_sum(res.get(), sm);
+    const double r = block_residual(res, sm);
     if (threadIdx.x == 0) a.partials[blockIdx.x] = r;
 }
 
