@@ -649,7 +649,10 @@ def run_only(args):
         if args.only == "bfs":
             for s in srcs:
                 _, _, st = gp.bfs(G, int(s), gp.AUTO)
-            res = {"levels": st["levels"], "reached": st["reached"]}
+            # the last search's levels: direction, frontier, edges examined, device time
+            res = {"levels": st["levels"], "reached": st["reached"], "init_us": round(st["init_us"], 1),
+                   "level_table": [[d, f, e, round(t, 1)] for d, f, e, t in
+                                   zip(st["direction"], st["frontier"], st["examined"], st["level_us"])]}
         else:
             mode = gp.PULL if args.only == "pr_pull" else gp.PUSH
             _, st = gp.pagerank(G, mode, 0.85, args.sweeps, 0.0, out=out)

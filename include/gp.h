@@ -275,6 +275,8 @@ typedef struct gp_bfs_stats {
     int8_t direction[GP_BFS_MAX_LEVELS]; /* GP_PUSH (top-down) / GP_PULL (bottom-up) per level */
     int64_t frontier[GP_BFS_MAX_LEVELS]; /* frontier size entering each level */
     int64_t examined[GP_BFS_MAX_LEVELS]; /* edges scanned by each level */
+    int32_t init_ns;                     /* device time from kernel start to the first level (global timer) */
+    int32_t level_ns[GP_BFS_MAX_LEVELS]; /* device time of each level, its frontier conversion and barrier included */
 } gp_bfs_stats;
 
 /*

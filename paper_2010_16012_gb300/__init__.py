@@ -64,7 +64,8 @@ class gp_bfs_stats(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int32), ("switches", ctypes.c_int32), ("reached", ctypes.c_int64),
                 ("edges_examined", ctypes.c_int64), ("edges_reached", ctypes.c_int64), ("ms", ctypes.c_float),
                 ("direction", ctypes.c_int8 * BFS_MAX_LEVELS), ("frontier", ctypes.c_int64 * BFS_MAX_LEVELS),
-                ("examined", ctypes.c_int64 * BFS_MAX_LEVELS)]
+                ("examined", ctypes.c_int64 * BFS_MAX_LEVELS), ("init_ns", ctypes.c_int32),
+                ("level_ns", ctypes.c_int32 * BFS_MAX_LEVELS)]
 
 
 class gp_batch_stats(ctypes.Structure):
@@ -372,7 +373,8 @@ def bfs(g: Graph, src: int, mode=AUTO, level=None, parent=None, want_parent=True
     stats = {"levels": st.levels, "switches": st.switches, "reached": st.reached,
              "edges_examined": st.edges_examined, "edges_reached": st.edges_reached, "ms": st.ms,
              "direction": list(st.direction[:L]), "frontier": list(st.frontier[:L]),
-             "examined": list(st.examined[:L])}
+             "examined": list(st.examined[:L]), "init_us": st.init_ns / 1e3,
+             "level_us": [x / 1e3 for x in st.level_ns[:L]]}
     return level, parent, stats
 
 

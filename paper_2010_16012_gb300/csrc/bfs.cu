@@ -337,14 +337,20 @@ __device__ void bits_to_queue_step(const BfsArgs &a) {
 
 struct BfsLevelStat {
     int32_t direction;
-    int32_t pad;
+    int32_t ns;  // device time of the level (global timer, block 0)
     int64_t frontier;
     int64_t examined;
 };
 
 struct BfsSummary {
-    int64_t levels, reached, examined, edges_reached, switches;
+    int64_t levels, reached, examined, edges_reached, switches, init_ns;
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 struct BfsRun {
     BfsArgs base;  // graph arrays, level/parent, chunk table
@@ -372,6 +378,7 @@ constexpr int BFS_THREADS = BFS_WARPS * 32;
 // counters after each barrier), so all blocks take the same direction decision
 // without a host round trip.
 __global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(BfsRun R) {
+    const unsigned long long t_start = global_ns();
     const int64_t n = R.base.n;
     const int64_t gthread = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
@@ -405,6 +412,8 @@ __global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(Bfs
         R.base.unvis[i] = R.nzin[i] & (i == sw ? ~sbit : ~0u);
     }
     if (!grid_sync(R.sync, gridDim.x)) return;
+    unsigned long long t_level = global_ns();
+    const unsigned long long t_init = t_level - t_start;
     BfsArgs a = R.base;
     volatile BfsCtr *vc = (volatile BfsCtr *)R.ctr;
     unsigned long long nf = vc[0].nf, mf = vc[0].mf;
@@ -464,6 +473,9 @@ __global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(Bfs
         if (!grid_sync(R.sync, gridDim.x)) return;
         const unsigned long long nf2 = vc[nxt].nf, mf2 = vc[nxt].mf, mud = vc[nxt].mu_dec, ex = vc[nxt].examined;
         if (gthread == 0 && L < GP_BFS_MAX_LEVELS) {
+            const unsigned long long t = global_ns();
+            R.stats[L].ns = (int32_t)min(t - t_level, 0x7fffffffull);
+            t_level = t;
             R.stats[L].direction = dir;
             R.stats[L].frontier = (int64_t)nf;
             R.stats[L].examined = (int64_t)ex;
@@ -485,6 +497,7 @@ __global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(Bfs
         R.summary->examined = examined;
         R.summary->edges_reached = edges_reached;
         R.summary->switches = switches;
+        R.summary->init_ns = (int64_t)t_init;
     }
 }
 
@@ -664,11 +677,13 @@ static int bfs_run(const gp_graph *gc, int32_t src, int mode, const int8_t *dirs
         stats->edges_examined = hs->examined;
         stats->edges_reached = hs->edges_reached;
         stats->ms = ms;
+        stats->init_ns = (int32_t)std::min<int64_t>(hs->init_ns, INT32_MAX);
         const int L = (int)std::min<int64_t>(hs->levels, GP_BFS_MAX_LEVELS);
         for (int i = 0; i < L; ++i) {
             stats->direction[i] = (int8_t)hl[i].direction;
             stats->frontier[i] = hl[i].frontier;
             stats->examined[i] = hl[i].examined;
+            stats->level_ns[i] = hl[i].ns;
         }
     }
     GP_CUDA(cudaStreamSynchronize(s));

@@ -57,6 +57,44 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(gp.gp_graph_info) == 88
 
 
+def test_struct_layouts_match_c_compiler(tmp_path):
+    """Sizes and field offsets of the binding's ctypes structures equal those the
+    C compiler derives from include/gp.h."""
+    import shutil
+    import subprocess
+
+    import paper_2010_16012_gb300 as gp
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = {"gp_options": gp.gp_options, "gp_pr_stats": gp.gp_pr_stats, "gp_bfs_stats": gp.gp_bfs_stats,
+               "gp_batch_stats": gp.gp_batch_stats, "gp_tune_result": gp.gp_tune_result,
+               "gp_kernel_time": gp.gp_kernel_time, "gp_graph_info": gp.gp_graph_info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gp.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f in cls._fields_:
+            lines.append(f'printf("{name} {f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for line in out:
+        if not line:
+            continue
+        name, field, val = line.split()
+        cls = structs[name]
+        want = ctypes.sizeof(cls) if field == "size" else getattr(cls, field).offset
+        assert int(val) == want, (name, field, int(val), want)
+        seen += 1
+    assert seen > 30
+
+
 def test_host_argument_checks(lib):
     import paper_2010_16012_gb300 as gp
 

@@ -170,3 +170,15 @@ def test_candidate_bitmap_after_top_down_levels(gp):
         for dirs in ([0, 1], [1, 0], [0, 0, 1], [1, 1, 0, 1], [0, 1, 0, 1, 0]):
             level, parent, _ = gp.bfs(G, src, dirs=dirs)
             check(g, O, src, level, parent)
+
+
+def test_level_times_reported(gp):
+    """Per-level device times: one positive entry per level, summing (with the
+    start-up) to no more than the call's event time."""
+    g = gg.rmat(13, 16, seed=8)
+    G = gp.Graph.from_graphgen(g)
+    src = int(gg.pick_vertices(g, 1, seed=9)[0])
+    _, _, st = gp.bfs(G, src, gp.AUTO)
+    assert len(st["level_us"]) == st["levels"] > 1
+    assert all(t > 0 for t in st["level_us"]) and st["init_us"] > 0
+    assert st["init_us"] + sum(st["level_us"]) <= st["ms"] * 1e3 * 1.05 + 5.0
