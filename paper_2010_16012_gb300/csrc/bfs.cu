@@ -62,6 +62,7 @@ struct BfsArgs {
     BfsCtr *cur, *nxt;
     int32_t L;           // level being expanded: new vertices get L + 1
     int32_t make_queue;  // top-down: also build the next frontier's queue
+    int64_t q_len, h_len;  // top-down: lengths of the current frontier's queue and heavy list
 };
 
 // Count w (newly visited) into the next frontier's statistics and, when the
@@ -149,8 +150,7 @@ __device__ void bfs_topdown_step(const BfsArgs &a) {
     const int lane = lane_id();
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t h_len = (int64_t)((volatile BfsCtr *)a.cur)->h_len;
-    const int64_t q_len = (int64_t)((volatile BfsCtr *)a.cur)->q_len;
+    const int64_t h_len = a.h_len, q_len = a.q_len;
     unsigned long long nf = 0, mf = 0, mu = 0, ex = 0;
     // each heavy chunk is split TD_SPLIT ways so a frontier of a few hubs still spreads over many warps
     for (int64_t j = warp; j < h_len * TD_SPLIT; j += nwarps) {
@@ -244,9 +244,10 @@ __device__ void bfs_bottomup_step(const BfsArgs &a) {
         if (total == 0) continue;  // uniform across the warp
         s_found[wib][lane] = 0u;
         __syncwarp();
-        for (int r = 0; r < total; r += 32) {
-            const int id = r + lane;
-            int k = 0;  // the lane (word) whose candidates [excl, incl) hold id
+        // Round r's candidate (vertex and in-edge range) is located and its
+        // offsets loaded during round r - 1, so they arrive while that round scans.
+        auto locate = [&](int id, int &k, int &bit, int64_t &b, int64_t &e) {
+            k = 0;  // the lane (word) whose candidates [excl, incl) hold id
 #pragma unroll
             for (int st = 16; st > 0; st >>= 1) {
                 const int ek = __shfl_sync(FULL, excl, k + st);
@@ -254,11 +255,24 @@ __device__ void bfs_bottomup_step(const BfsArgs &a) {
             }
             const uint32_t kc = __shfl_sync(FULL, cand, k);
             const int kex = __shfl_sync(FULL, excl, k);
+            bit = 0;
+            b = e = 0;
             if (id < total) {
-                const int bit = nth_set_bit(kc, id - kex);
+                bit = nth_set_bit(kc, id - kex);
                 const int64_t v = (base + k) * 32 + bit;
-                const int64_t b = a.csc_off[v], e = a.csc_off[v + 1];
-                const int64_t dout = a.csr_off[v + 1] - a.csr_off[v];
+                b = a.csc_off[v];
+                e = a.csc_off[v + 1];
+            }
+        };
+        int k, bit;
+        int64_t b, e;
+        locate(lane, k, bit, b, e);
+        for (int r = 0; r < total; r += 32) {
+            int kn, bitn;
+            int64_t bn, en;
+            locate(r + 32 + lane, kn, bitn, bn, en);
+            if (r + lane < total) {
+                const int64_t v = (base + k) * 32 + bit;
                 // BU_SCAN in-edges per step: their bitmap probes are independent
                 for (int64_t j = b; j < e; j += BU_SCAN) {
                     int32_t u[BU_SCAN];
@@ -282,13 +296,17 @@ __device__ void bfs_bottomup_step(const BfsArgs &a) {
                         if (a.parent) a.parent[v] = p;
                         atomicOr(&s_found[wib][k], 1u << bit);
                         nf += 1;
-                        mf += (unsigned long long)dout;
+                        mf += (unsigned long long)(a.csr_off == a.csc_off ? e - b : a.csr_off[v + 1] - a.csr_off[v]);
                         mu += (unsigned long long)(e - b);
                         break;
                     }
                     ex += (unsigned long long)(e - j < BU_SCAN ? e - j : BU_SCAN);
                 }
             }
+            k = kn;
+            bit = bitn;
+            b = bn;
+            e = en;
         }
         __syncwarp();
         const uint32_t fw = s_found[wib][lane];
@@ -415,9 +433,26 @@ __global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(Bfs
     unsigned long long t_level = global_ns();
     const unsigned long long t_init = t_level - t_start;
     BfsArgs a = R.base;
+    // counter records are read by one thread per block and shared through
+    // shared memory: every thread loading the same line would queue tens of
+    // thousands of requests on one L2 slice per level
     volatile BfsCtr *vc = (volatile BfsCtr *)R.ctr;
-    unsigned long long nf = vc[0].nf, mf = vc[0].mf;
-    long long mu = (long long)R.m - (long long)vc[0].mu_dec;
+    __shared__ unsigned long long s_ctr[6];
+    auto read_ctr = [&](int slot) {
+        if (threadIdx.x == 0) {
+            s_ctr[0] = vc[slot].q_len;
+            s_ctr[1] = vc[slot].h_len;
+            s_ctr[2] = vc[slot].nf;
+            s_ctr[3] = vc[slot].mf;
+            s_ctr[4] = vc[slot].mu_dec;
+            s_ctr[5] = vc[slot].examined;
+        }
+        __syncthreads();
+    };
+    read_ctr(0);
+    unsigned long long nf = s_ctr[2], mf = s_ctr[3];
+    long long mu = (long long)R.m - (long long)s_ctr[4];
+    int64_t q_len = (int64_t)s_ctr[0], h_len = (int64_t)s_ctr[1];
     unsigned long long prev_nf = 0;
     int cur = 0, prev_dir = GP_PUSH, L = 0, switches = 0;
     bool in_queue = true;
@@ -456,6 +491,9 @@ __global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(Bfs
             c.h_next = R.hchunk[L & 1];
             bits_to_queue_step(c);
             if (!grid_sync(R.sync, gridDim.x)) return;
+            read_ctr(cur);
+            q_len = (int64_t)s_ctr[0];
+            h_len = (int64_t)s_ctr[1];
         }
         if (gthread < CW) ((unsigned long long *)(R.ctr + spare))[gthread] = 0;
         for (int64_t i = gthread; i < nwords; i += nthreads) R.bits[spare][i] = 0u;
@@ -464,6 +502,8 @@ __global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(Bfs
             // are the appends); otherwise the bitmap alone, compacted later if
             // another top-down level follows
             a.make_queue = mf < TD_QUEUE_EDGES;
+            a.q_len = q_len;
+            a.h_len = h_len;
             bfs_topdown_step(a);
             in_queue = a.make_queue != 0;
         } else {
@@ -471,7 +511,10 @@ __global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(Bfs
             in_queue = false;
         }
         if (!grid_sync(R.sync, gridDim.x)) return;
-        const unsigned long long nf2 = vc[nxt].nf, mf2 = vc[nxt].mf, mud = vc[nxt].mu_dec, ex = vc[nxt].examined;
+        read_ctr(nxt);
+        const unsigned long long nf2 = s_ctr[2], mf2 = s_ctr[3], mud = s_ctr[4], ex = s_ctr[5];
+        q_len = (int64_t)s_ctr[0];
+        h_len = (int64_t)s_ctr[1];
         if (gthread == 0 && L < GP_BFS_MAX_LEVELS) {
             const unsigned long long t = global_ns();
             R.stats[L].ns = (int32_t)min(t - t_level, 0x7fffffffull);
