@@ -307,10 +307,14 @@ __global__ void __launch_bounds__(512, GP_LIGHT_MIN_BLOCKS) k_pull_light(PrArgs 
                 int32_t u[LW];
 #pragma unroll
                 for (int q = 0; q < LW; ++q) {
-                    const int eq = base + 32 * q + lane;
-                    const int k = tile_owner(excl, eq);
-                    kx[q] = __shfl_sync(FULL, excl, k);
-                    p[q] = __shfl_sync(FULL, b, k) + (eq - kx[q]);
+                    kx[q] = 0;
+                    p[q] = 0;
+                    if (base + 32 * q < E) {  // uniform: windows past the tile's edges are skipped
+                        const int eq = base + 32 * q + lane;
+                        const int k = tile_owner(excl, eq);
+                        kx[q] = __shfl_sync(FULL, excl, k);
+                        p[q] = __shfl_sync(FULL, b, k) + (eq - kx[q]);
+                    }
                 }
 #pragma unroll
                 for (int q = 0; q < LW; ++q) u[q] = base + 32 * q + lane < E ? ld_idx(idx + p[q]) : 0;
