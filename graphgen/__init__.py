@@ -68,6 +68,7 @@ def _get():
             lib.gg_uniform_weights.argtypes = [c.c_int64, c.c_uint64, f32p, c.c_int]
             lib.gg_normalize_rows.restype = None
             lib.gg_normalize_rows.argtypes = [c.c_int64, i64p, f32p, c.c_int]
+            lib.gg_int_weights.argtypes = [c.c_int64, c.c_uint64, c.c_int32, c.c_int32, f32p, c.c_int]
             lib.gg_pick_vertices.restype = c.c_int64
             lib.gg_pick_vertices.argtypes = [c.c_int64, i64p, c.c_int64, c.c_int64, c.c_uint64, i32p]
             _lib = lib
@@ -123,6 +124,26 @@ class Graph:
         return Graph(self.name + f"+w{seed}", self.n, self.csr_off, self.csr_idx, self.csc_off,
                      self.csc_idx, self.symmetric, w, np.ascontiguousarray(w[perm]),
                      dict(self.meta, weight_seed=seed, normalized=normalize))
+
+
+def with_int_weights(g: Graph, seed: int, lo: int = 1, hi: int = 255, symmetric_weights: bool = False,
+                     nthreads: int = 0) -> Graph:
+    """Copy of the graph with integer-valued weights uniform in [lo, hi] (stored
+    as float32; path sums are exact in FP32 below 2^24).  One draw per CSR edge;
+    with symmetric_weights (symmetric graphs only) the edge u->v takes the draw
+    of its u < v direction, so w(u->v) = w(v->u)."""
+    lib = _get()
+    w = np.empty(g.m, dtype=np.float32)
+    lib.gg_int_weights(g.m, seed, lo, hi, w, nthreads)
+    perm = _transpose_perm(g)
+    if symmetric_weights:
+        if not g.symmetric:
+            raise ValueError("symmetric weights need a symmetric graph")
+        src, dst = g.edges()
+        swap = src > dst  # take the weight of the reverse edge: CSC slot perm maps CSR edge -> reverse
+        w = np.where(swap, w[perm], w).astype(np.float32)
+    return Graph(g.name + f"+iw{seed}", g.n, g.csr_off, g.csr_idx, g.csc_off, g.csc_idx, g.symmetric, w,
+                 np.ascontiguousarray(w[perm]), dict(g.meta, weight_seed=seed, int_weights=(lo, hi)))
 
 
 def _transpose_perm(g: Graph) -> np.ndarray:

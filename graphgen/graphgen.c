@@ -218,6 +218,16 @@ void gg_uniform_weights(int64_t m, uint64_t seed, float *w, int nthreads) {
     }
 }
 
+/* Integer-valued weights uniform in [lo, hi] (one draw per CSR edge), stored as
+ * float: path sums stay exact in FP32 while they are below 2^24. */
+void gg_int_weights(int64_t m, uint64_t seed, int32_t lo, int32_t hi, float *w, int nthreads) {
+    const uint64_t key = gg_key(seed);
+    const uint64_t span = (uint64_t)((int64_t)hi - (int64_t)lo + 1);
+    gg_set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < m; ++e) w[e] = (float)(lo + (int64_t)(gg_draw(key, (uint64_t)e) % span));
+}
+
 /* Scale the weights of every CSR row so that they sum to one (in double, then
  * rounded to float): the column-normalised transition matrix of the input
  * recipe.  Rows without edges are left alone. */

@@ -62,6 +62,10 @@ def _get():
             lib.or_pagerank_adjoint.restype = c.c_int
             lib.or_pagerank_adjoint.argtypes = [vp, c.c_double, vp, vp, c.c_int, c.c_double, vp, vp, vp,
                                                 c.POINTER(c.c_double), c.c_int]
+            lib.or_sssp_dijkstra.restype = c.c_int64
+            lib.or_sssp_dijkstra.argtypes = [vp, c.c_int32, vp, vp]
+            lib.or_sssp_delta.restype = c.c_int64
+            lib.or_sssp_delta.argtypes = [vp, c.c_int32, c.c_double, vp, c.c_int, vp, c.POINTER(c.c_int64)]
             lib.or_max_threads.restype = c.c_int
             lib.or_max_threads.argtypes = []
             _lib = lib
@@ -150,6 +154,25 @@ class OracleGraph:
                                           float(tol), _ptr(lam), _ptr(gs), _ptr(gw), ctypes.byref(r),
                                           int(nthreads))
         return lam, gs, gw, k, r.value
+
+
+    # ------------------------------------------------------------ SSSP
+    def sssp(self, src: int):
+        """Dijkstra (FP64).  Returns (dist float64 with inf unreached, pred int32)."""
+        dist = np.empty(self.n, dtype=np.float64)
+        pred = np.empty(self.n, dtype=np.int32)
+        self._lib.or_sssp_dijkstra(self._h, int(src), _ptr(dist), _ptr(pred))
+        return dist, pred
+
+    def sssp_delta(self, src: int, delta: float, dirs=(PUSH,)):
+        """Delta-Stepping, one direction per relaxation iteration (0 push,
+        1 pull; the last entry repeats).  Returns (dist, iterations, epochs)."""
+        dist = np.empty(self.n, dtype=np.float64)
+        d = np.ascontiguousarray(np.asarray(dirs, dtype=np.int8))
+        ep = ctypes.c_int64(0)
+        it = self._lib.or_sssp_delta(self._h, int(src), float(delta), _ptr(d), int(d.shape[0]), _ptr(dist),
+                                     ctypes.byref(ep))
+        return dist, int(it), ep.value
 
 
 def max_threads() -> int:

@@ -25,6 +25,10 @@
  *     bottom-up (pull: unvisited vertices scan in-edges for a frontier vertex).
  *   - Adjoint of the PageRank fixed point (not in the paper): lambda solves
  *     (I - d P^T) lambda = g; dL/ds = (1-d) lambda; dL/dP_vu = d lambda_v x_u.
+ *   - Single-source shortest paths: Dijkstra (the plain definition, min over
+ *     paths of the weight sum), and the push- and pull-based Delta-Stepping of
+ *     the paper's Section 3 listing, run sequentially with one direction per
+ *     relaxation iteration.
  *
  * Readings of the paper where it is silent or ambiguous (each is a choice the
  * CUDA path makes identically):
@@ -348,6 +352,171 @@ int or_pagerank_adjoint(const or_graph *g, double d, const double *x, const doub
     free(lam);
     free(nxt);
     return k;
+}
+
+/* ------------------------------------------------------------------ SSSP */
+
+/* Weight of input edge e for shortest paths: the stored weight, 1 unweighted. */
+static inline double or_W(const or_graph *g, int64_t e) { return g->w ? g->w[e] : 1.0; }
+
+typedef struct {
+    double key;
+    int32_t v;
+} or_heap_item;
+
+static void or_heap_push(or_heap_item *h, int64_t *len, double key, int32_t v) {
+    int64_t i = (*len)++;
+    while (i > 0) {
+        const int64_t p = (i - 1) / 2;
+        if (h[p].key <= key) break;
+        h[i] = h[p];
+        i = p;
+    }
+    h[i].key = key;
+    h[i].v = v;
+}
+
+static or_heap_item or_heap_pop(or_heap_item *h, int64_t *len) {
+    const or_heap_item top = h[0];
+    const or_heap_item last = h[--(*len)];
+    int64_t i = 0;
+    for (;;) {
+        int64_t c = 2 * i + 1;
+        if (c >= *len) break;
+        if (c + 1 < *len && h[c + 1].key < h[c].key) ++c;
+        if (last.key <= h[c].key) break;
+        h[i] = h[c];
+        i = c;
+    }
+    if (*len > 0) h[i] = last;
+    return top;
+}
+
+/*
+ * Single-source shortest paths, the plain definition: dist[v] = min over paths
+ * r -> ... -> v of the sum of their edge weights, +inf where no path exists.
+ * Textbook Dijkstra with a binary heap and lazy deletion, FP64.  pred
+ * (nullable) receives the predecessor on the shortest path found (pred[r] = r,
+ * -1 unreached).  Weights must be >= 0.  Returns the number of vertices reached.
+ */
+int64_t or_sssp_dijkstra(const or_graph *g, int32_t r, double *dist, int32_t *pred) {
+    const int64_t n = g->n;
+    for (int64_t v = 0; v < n; ++v) {
+        dist[v] = INFINITY;
+        if (pred) pred[v] = -1;
+    }
+    char *done = (char *)calloc((size_t)(n > 0 ? n : 1), 1);
+    or_heap_item *h = (or_heap_item *)malloc((size_t)(g->m + 1) * sizeof(or_heap_item));
+    int64_t len = 0, reached = 0;
+    dist[r] = 0.0;
+    if (pred) pred[r] = r;
+    or_heap_push(h, &len, 0.0, r);
+    while (len > 0) {
+        const or_heap_item it = or_heap_pop(h, &len);
+        const int32_t u = it.v;
+        if (done[u]) continue;
+        done[u] = 1;
+        ++reached;
+        for (int64_t j = g->out_off[u]; j < g->out_off[u + 1]; ++j) {
+            const int32_t v = g->out_idx[j];
+            const double nd = dist[u] + or_W(g, g->out_eid[j]);
+            if (nd < dist[v]) {
+                dist[v] = nd;
+                if (pred) pred[v] = u;
+                or_heap_push(h, &len, nd, v);
+            }
+        }
+    }
+    free(h);
+    free(done);
+    return reached;
+}
+
+static inline int64_t or_bucket(double d, double delta) { return (int64_t)floor(d / delta); }
+
+/*
+ * Delta-Stepping (the paper's push- and pull-based listing), sequential.  Epoch
+ * b handles bucket b = the vertices with dist in [b*delta, (b+1)*delta): its
+ * relaxation iterations repeat until no vertex of bucket b changed.  Active
+ * vertices: every vertex of bucket b in the epoch's first iteration, then the
+ * vertices of bucket b whose distance decreased in the previous iteration.
+ * Relaxation iteration i of the whole run uses dirs[min(i, ndirs-1)]:
+ *   0 push: each active v relaxes its out-edges v->w (dist[w] = min(dist[w],
+ *           dist[v] + W));
+ *   1 pull: each vertex v not settled in an earlier bucket (dist[v] >=
+ *           b*delta, +inf included) takes the minimum of dist[u] + W over its
+ *           in-edges u->v from active u.
+ * The next epoch is the smallest non-empty bucket above b.  Returns the number
+ * of relaxation iterations; *epochs receives the number of epochs.
+ */
+int64_t or_sssp_delta(const or_graph *g, int32_t r, double delta, const int8_t *dirs, int ndirs, double *dist,
+                      int64_t *epochs) {
+    const int64_t n = g->n;
+    char *act = (char *)calloc((size_t)(n > 0 ? n : 1), 1);
+    char *nxt = (char *)calloc((size_t)(n > 0 ? n : 1), 1);
+    for (int64_t v = 0; v < n; ++v) dist[v] = INFINITY;
+    dist[r] = 0.0;
+    int64_t b = 0, it = 0, ep = 0;
+    for (;;) {
+        /* epoch b: every vertex of bucket b is active */
+        int64_t nact = 0;
+        for (int64_t v = 0; v < n; ++v) {
+            act[v] = isfinite(dist[v]) && or_bucket(dist[v], delta) == b;
+            nact += act[v];
+        }
+        ++ep;
+        while (nact > 0) {
+            const int dir = dirs[it < ndirs ? it : ndirs - 1];
+            memset(nxt, 0, (size_t)n);
+            if (dir == 0) {
+                for (int64_t v = 0; v < n; ++v) {
+                    if (!act[v]) continue;
+                    for (int64_t j = g->out_off[v]; j < g->out_off[v + 1]; ++j) {
+                        const int32_t w = g->out_idx[j];
+                        const double nd = dist[v] + or_W(g, g->out_eid[j]);
+                        if (nd < dist[w]) {
+                            dist[w] = nd;
+                            if (or_bucket(nd, delta) == b) nxt[w] = 1;
+                        }
+                    }
+                }
+            } else {
+                for (int64_t v = 0; v < n; ++v) {
+                    if (!(dist[v] >= (double)b * delta)) continue; /* settled in an earlier bucket */
+                    double best = dist[v];
+                    for (int64_t j = g->in_off[v]; j < g->in_off[v + 1]; ++j) {
+                        const int32_t u = g->in_idx[j];
+                        if (!act[u]) continue;
+                        const double nd = dist[u] + or_W(g, g->in_eid[j]);
+                        if (nd < best) best = nd;
+                    }
+                    if (best < dist[v]) {
+                        dist[v] = best;
+                        if (or_bucket(best, delta) == b) nxt[v] = 1;
+                    }
+                }
+            }
+            ++it;
+            char *t = act;
+            act = nxt;
+            nxt = t;
+            nact = 0;
+            for (int64_t v = 0; v < n; ++v) nact += act[v];
+        }
+        /* the next non-empty bucket */
+        int64_t nb = -1;
+        for (int64_t v = 0; v < n; ++v) {
+            if (!isfinite(dist[v])) continue;
+            const int64_t bv = or_bucket(dist[v], delta);
+            if (bv > b && (nb < 0 || bv < nb)) nb = bv;
+        }
+        if (nb < 0) break;
+        b = nb;
+    }
+    free(act);
+    free(nxt);
+    if (epochs) *epochs = ep;
+    return it;
 }
 
 /* Number of OpenMP threads a parallel region gets (1 without OpenMP). */

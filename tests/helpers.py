@@ -175,3 +175,42 @@ def check_levels_by_edges(csr_src, csr_idx, root, level):
     bad = int(lv[root] != 0)
     bad += int(np.count_nonzero((lu >= 0) & ((lh < 0) | (lh > lu + 1))))
     return bad
+
+
+def parse_sssp_cases(path=os.path.join(GOLDEN, "sssp_worked_example.txt")):
+    """(n, src_e, dst_e, w_e, [(src, dist, pred), ...]) from the SSSP fixture."""
+    n, cases, cur = 0, [], None
+    src_e, dst_e, w_e = [], [], []
+    for line in open(path):
+        line = line.split("#", 1)[0].strip()
+        if not line:
+            continue
+        key, *vals = line.split()
+        if key == "n":
+            n = int(vals[0])
+        elif key == "edges":
+            for t in vals:
+                uv, w = t.split(":")
+                u, v = uv.split(">")
+                src_e.append(int(u))
+                dst_e.append(int(v))
+                w_e.append(float(w))
+        elif key == "src":
+            cur = [int(vals[0]), None, None]
+            cases.append(cur)
+        elif key == "dist":
+            cur[1] = [float("inf") if t == "inf" else float(t) for t in vals]
+        elif key == "pred":
+            cur[2] = [int(t) for t in vals]
+    return n, src_e, dst_e, w_e, cases
+
+
+def floyd_warshall_dist(n, src, dst, w):
+    """All-pairs shortest path weights by Floyd-Warshall (min-plus closure), inf if none."""
+    D = np.full((n, n), np.inf)
+    np.fill_diagonal(D, 0.0)
+    for u, v, x in zip(src, dst, w):
+        D[u, v] = min(D[u, v], float(x))
+    for k in range(n):
+        D = np.minimum(D, D[:, k:k + 1] + D[k:k + 1, :])
+    return D

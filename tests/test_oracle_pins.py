@@ -9,7 +9,8 @@ import pytest
 import graphgen as gg
 import oracle
 from helpers import (check_levels_by_edges, check_parents, check_parents_np, dense_pagerank, dense_transition,
-                     edge_sources, floyd_warshall_levels, parse_bfs_case, parse_pagerank_cases)
+                     edge_sources, floyd_warshall_dist, floyd_warshall_levels, parse_bfs_case, parse_pagerank_cases,
+                     parse_sssp_cases)
 
 VARIANTS = [oracle.PUSH, oracle.PULL]
 
@@ -350,3 +351,93 @@ def test_full_size_bfs_checkers_catch_planted_mistakes():
     badp = parent.copy()
     badp[deep] = src
     assert check_parents_np(g.csr_off, g.csr_idx, src, level, badp) > 0
+
+
+# ------------------------------------------------------------------ SSSP (Delta-Stepping, Section 3 listing)
+
+def test_sssp_worked_example():
+    n, s, d, w, cases = parse_sssp_cases()
+    G = oracle.OracleGraph(n, np.array(s), np.array(d), np.array(w, dtype=np.float32))
+    for src, dist, pred in cases:
+        got, p = G.sssp(src)
+        assert np.array_equal(got, np.array(dist)), (src, got)
+        assert list(p) == pred
+        for delta in (1.0, 2.0, 3.5, 100.0):
+            for dirs in ([0], [1], [0, 1], [1, 0, 0]):
+                dd, _, _ = G.sssp_delta(src, delta, dirs)
+                assert np.array_equal(dd, np.array(dist)), (src, delta, dirs)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_sssp_dijkstra_matches_floyd_warshall(seed):
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(2, 11))
+    ne = int(rng.integers(0, 3 * n))
+    u = rng.integers(0, n, size=ne)
+    v = rng.integers(0, n, size=ne)
+    w = rng.integers(0, 10, size=ne).astype(np.float32)  # zero weights and parallel edges included
+    G = oracle.OracleGraph(n, u, v, w)
+    D = floyd_warshall_dist(n, u, v, w)
+    for src in range(n):
+        dist, pred = G.sssp(src)
+        assert np.array_equal(dist, D[src]), (seed, src)
+        for t in range(n):  # every predecessor lies on a shortest path
+            if np.isfinite(dist[t]) and t != src:
+                p = pred[t]
+                assert any(a == p and b == t and dist[p] + x == dist[t] for a, b, x in zip(u, v, w))
+
+
+def test_sssp_unit_weights_are_bfs_levels():
+    g = gg.rmat(9, 8, seed=12, symmetrize=False)
+    G = og(g)
+    for src in gg.pick_vertices(g, 4, seed=13):
+        dist, _ = G.sssp(int(src))
+        lv, _ = G.bfs(int(src))
+        assert np.array_equal(np.where(np.isfinite(dist), dist, -1).astype(np.int64), lv.astype(np.int64))
+
+
+def test_sssp_path_and_star_closed_forms():
+    w = np.array([3, 1, 4, 1, 5, 9, 2, 6], dtype=np.float32)
+    n = len(w) + 1
+    G = oracle.OracleGraph(n, np.arange(n - 1), np.arange(1, n), w)
+    dist, _ = G.sssp(0)
+    assert np.array_equal(dist, np.concatenate([[0.0], np.cumsum(w)]))
+    k = 6  # star: hub 0, leaves 1..k, edges both ways with weights a_i (out) and b_i (in)
+    a = np.arange(1, k + 1, dtype=np.float32)
+    b = 10 * a
+    src = np.concatenate([np.zeros(k, int), np.arange(1, k + 1)])
+    dst = np.concatenate([np.arange(1, k + 1), np.zeros(k, int)])
+    G = oracle.OracleGraph(k + 1, src, dst, np.concatenate([a, b]))
+    d0, _ = G.sssp(0)
+    assert np.array_equal(d0, np.concatenate([[0.0], a]))
+    d3, _ = G.sssp(3)  # leaf 3 -> hub (b_3) -> leaf j (a_j)
+    want = np.concatenate([[b[2]], b[2] + a])
+    want[3] = 0.0
+    assert np.array_equal(d3, want)
+
+
+@pytest.mark.parametrize("delta", [1.0, 7.0, 32.0, 1000.0, 1e9])
+def test_sssp_delta_stepping_equals_dijkstra(delta):
+    """Delta-Stepping reaches the shortest distances for any bucket width and any
+    push/pull sequence (integer weights: sums are exact)."""
+    g = gg.with_int_weights(gg.rmat(8, 8, seed=14, symmetrize=False), seed=15, lo=1, hi=64)
+    G = og(g)
+    rng = np.random.default_rng(16)
+    for src in gg.pick_vertices(g, 3, seed=17):
+        ref, _ = G.sssp(int(src))
+        for dirs in ([0], [1], [0, 1], [1, 0], list(rng.integers(0, 2, size=40))):
+            dist, iters, epochs = G.sssp_delta(int(src), delta, dirs)
+            assert np.array_equal(dist, ref), (delta, dirs)
+            assert iters >= epochs >= 1
+
+
+def test_sssp_delta_epochs_follow_bucket_width():
+    """Unit weights on a path: with delta = 1 every vertex is its own bucket (one
+    epoch per distance); with a huge delta everything is one epoch whose push
+    iterations advance one hop each (Bellman-Ford)."""
+    n = 12
+    G = oracle.OracleGraph(n, np.arange(n - 1), np.arange(1, n), np.ones(n - 1, dtype=np.float32))
+    dist, iters, epochs = G.sssp_delta(0, 1.0, [0])
+    assert epochs == n and np.array_equal(dist, np.arange(n, dtype=np.float64))
+    dist, iters, epochs = G.sssp_delta(0, 1e9, [0])
+    assert epochs == 1 and iters == n  # n - 1 hops, then one iteration that changes nothing
