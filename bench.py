@@ -53,9 +53,11 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--quiet", action="store_true")
     p.add_argument("--no-batched", action="store_true")
-    p.add_argument("--only", choices=["pr_pull", "pr_push", "bfs", "batched"], default=None,
+    p.add_argument("--only", choices=["pr_pull", "pr_push", "bfs", "batched", "sssp"], default=None,
                    help="profiling case: run only this part (fixed --sweeps for PageRank), no contract line")
     p.add_argument("--sweeps", type=int, default=4)
+    p.add_argument("--delta", type=float, default=64.0, help="--only sssp: bucket width")
+    p.add_argument("--mode", choices=["push", "pull", "auto"], default="auto", help="--only sssp: direction mode")
     p.add_argument("--opt", action="append", default=[], metavar="KEY=VALUE",
                    help="gp_options override for the profiling case (repeatable)")
     return p.parse_args(argv)
@@ -628,6 +630,8 @@ def run_only(args):
     if args.only == "batched":
         print(json.dumps({"profile_case": "batched", **run_batched(args)}), flush=True)
         return 0
+    if args.only == "sssp":
+        return run_only_sssp(args)
     g = make_graph(args.scale)
     off = torch.from_numpy(g.csr_off).cuda()
     idx = torch.from_numpy(g.csr_idx).cuda()
@@ -635,7 +639,7 @@ def run_only(args):
     opts = {}
     for kv in args.opt:
         k, v = kv.split("=")
-        opts[k] = float(v) if k.startswith("bfs_") else int(v)
+        opts[k] = float(v) if k.endswith("_alpha") or k.endswith("_beta") else int(v)
     if opts:
         G.set_options(**opts)
     out = torch.empty(g.n, dtype=torch.float32, device="cuda")
@@ -664,6 +668,59 @@ def run_only(args):
     per = {k[0]: round(k[2] / max(k[1], 1), 4) for k in kt}
     print(json.dumps({"profile_case": args.only, "scale": args.scale, "n": g.n, "m": g.m, "opts": opts,
                       "avg_launch_ms": per, **res}), flush=True)
+    return 0
+
+
+def run_only_sssp(args):
+    """Delta-Stepping SSSP on the R-MAT graph with integer weights uniform in
+    [1, 255] (seed 3), from --sources sources (seed 2): traversed edges per
+    second, Graph500 convention (undirected edges of the reached component)."""
+    import torch
+
+    import graphgen as gg
+    import paper_2010_16012_gb300 as gp
+
+    g = gg.with_int_weights(make_graph(args.scale), seed=3, lo=1, hi=255)
+    G = gp.Graph.from_graphgen(g)
+    opts = {}
+    for kv in args.opt:
+        k, v = kv.split("=")
+        opts[k] = float(v) if k.endswith("_alpha") or k.endswith("_beta") else int(v)
+    if opts:
+        G.set_options(**opts)
+    srcs = pick_sources(g, args.sources)
+    mode = {"push": gp.PUSH, "pull": gp.PULL, "auto": gp.AUTO}[args.mode]
+    dist = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    deg = np.diff(g.csr_off)
+    edges, stats = [], []
+    for s in srcs:  # component sizes and iteration counts, outside the timed runs
+        d, _, st = gp.sssp(G, int(s), args.delta, mode, dist=dist, want_pred=False)
+        edges.append(float(deg[np.isfinite(d.cpu().numpy())].sum()) / 2)
+        stats.append(st)
+    for i in range(args.warmup + args.steps):
+        if i == args.warmup:
+            torch.cuda.synchronize()
+            gp.profile_read(reset=True)
+            gp.profile_enable(True)
+        for s in srcs:
+            gp.sssp(G, int(s), args.delta, mode, dist=dist, want_pred=False, want_stats=False)
+    torch.cuda.synchronize()
+    gp.profile_enable(False)
+    kt = {k[0]: k for k in gp.profile_read(reset=True)}
+    k = kt["sssp_persistent"]
+    ms = k[2] / k[1]
+    print(json.dumps({"profile_case": "sssp", "scale": args.scale, "n": g.n, "m": g.m, "weights": "int [1, 255]",
+                      "delta": args.delta, "mode": args.mode, "opts": opts, "sources": len(srcs),
+                      "avg_launch_ms": round(ms, 4), "gteps": round(sum(edges) / (ms * 1e-3 * len(srcs)) / 1e9, 2),
+                      "iterations": round(float(np.mean([s["iterations"] for s in stats])), 1),
+                      "epochs": round(float(np.mean([s["epochs"] for s in stats])), 1),
+                      "pulls": round(float(np.mean([s["pulls"] for s in stats])), 1),
+                      "edges_examined": round(float(np.mean([s["edges_examined"] for s in stats]))),
+                      # the last source: per iteration direction, bucket, active vertices, edges, device time
+                      "init_us": round(stats[-1]["init_us"], 1),
+                      "iter_table": [[d, b, a, e, round(t, 1)] for d, b, a, e, t in
+                                     zip(stats[-1]["direction"], stats[-1]["bucket"], stats[-1]["active"],
+                                         stats[-1]["examined"], stats[-1]["iter_us"])]}), flush=True)
     return 0
 
 

@@ -161,7 +161,9 @@ typedef struct gp_options {
     int32_t push_hot_slots;   /* push PageRank: updates to this many highest in-degree vertices are
                                  summed in shared memory per block, then flushed with one atomic
                                  per vertex and block (0 = off, <= 49152) */
-    int32_t reserved[5];
+    float sssp_alpha;         /* SSSP GP_AUTO: an iteration pulls when the active vertices'
+                                 out-edges times sssp_alpha exceed the unsettled in-edges */
+    int32_t reserved[4];
 } gp_options;
 
 /* Fill *opt with the built-in defaults. */
@@ -312,6 +314,61 @@ int gp_bfs(const gp_graph *g, int32_t src, int mode, int32_t *level_out, int32_t
  * later levels.  Levels do not depend on the choice. */
 int gp_bfs_directed(const gp_graph *g, int32_t src, const int8_t *dirs, int ndirs, int32_t *level_out,
                     int32_t *parent_out, gp_bfs_stats *stats, void *stream);
+
+/* ------------------------------------------------------------------ shortest paths */
+
+#define GP_SSSP_MAX_ITERS 1024
+
+typedef struct gp_sssp_stats {
+    int32_t iterations;     /* relaxation iterations (all epochs) */
+    int32_t epochs;         /* buckets processed */
+    int64_t reached;        /* vertices with a finite distance */
+    int64_t edges_examined; /* edges relaxed (push) or scanned (pull) */
+    int32_t pushes, pulls;  /* iterations by direction */
+    float ms;               /* device time of the call by CUDA events */
+    int32_t init_ns;        /* device time before the first iteration */
+    int8_t direction[GP_SSSP_MAX_ITERS]; /* per iteration (first GP_SSSP_MAX_ITERS): GP_PUSH / GP_PULL */
+    int64_t bucket[GP_SSSP_MAX_ITERS];   /* bucket index (distance / delta) of the iteration's epoch */
+    int64_t active[GP_SSSP_MAX_ITERS];   /* active vertices entering the iteration */
+    int64_t examined[GP_SSSP_MAX_ITERS]; /* edges relaxed or scanned by the iteration */
+    int32_t iter_ns[GP_SSSP_MAX_ITERS];  /* device time of the iteration (global timer) */
+} gp_sssp_stats;
+
+/*
+ * Single-source shortest paths by Delta-Stepping (Section 3, the push- and
+ * pull-based Delta-Stepping listing): epoch b settles the vertices whose
+ * distance lies in [b*delta, (b+1)*delta); within an epoch, relaxation
+ * iterations repeat until no vertex of the bucket improves.
+ *   src         source vertex.
+ *   delta       bucket width (> 0, finite): small widths approach Dijkstra's
+ *               order, huge ones Bellman-Ford's; distances do not depend on it.
+ *   mode        GP_PUSH: every iteration pushes (active vertices relax their
+ *               out-edges with 64-bit atomicMin: O(m l) atomics);
+ *               GP_PULL: every iteration pulls (unsettled vertices take the
+ *               minimum over their in-edges from active vertices; owner-only
+ *               writes, heavy in-lists combined by atomicMin over chunks);
+ *               GP_AUTO: per iteration, pull when the active vertices'
+ *               out-edges times bfs_alpha exceed the in-edges of the unsettled
+ *               vertices, else push.
+ *   dirs, ndirs NULL, or the direction of each iteration (GP_PUSH/GP_PULL,
+ *               dirs[ndirs-1] for all later ones), overriding mode.
+ *   dist_out    float[n] "any": shortest distance, +inf if unreachable.
+ *   pred_out    int32[n] "any" or NULL: the smallest predecessor on a shortest
+ *               path (pred[src] = src, -1 unreachable) -- unique, whatever the
+ *               order of relaxations.  With zero-weight edges two vertices at
+ *               the same distance can be each other's predecessor.
+ *   stats       NULL or filled on return.
+ * Weights: the graph's weights as uploaded (csr_w for out-edges, csc_w for
+ * in-edges; weights must be >= 0, else GP_ERR_INVALID; checked once per graph),
+ * 1 for every edge of an unweighted graph.  FP32 distances: sums along a path
+ * are rounded as they are formed (exact while they are integers below 2^24).
+ * Synchronisation as gp_bfs: with stats == NULL and device outputs the call
+ * only enqueues the search; a grid-barrier timeout is then reported by the next
+ * gp_sssp call on the graph.  GP_ERR_INVALID for a bad source, delta, mode or
+ * direction; GP_ERR_TIMEOUT if a grid barrier wait ran out.
+ */
+int gp_sssp(const gp_graph *g, int32_t src, float delta, int mode, const int8_t *dirs, int ndirs, float *dist_out,
+            int32_t *pred_out, gp_sssp_stats *stats, void *stream);
 
 /* ------------------------------------------------------------------ batches of graphs */
 

@@ -43,7 +43,8 @@ class gp_options(ctypes.Structure):
                 ("poll_interval", ctypes.c_int32), ("pr_auto_mode", ctypes.c_int32),
                 ("bfs_alpha", ctypes.c_float), ("bfs_beta", ctypes.c_float),
                 ("push_fp64_accum", ctypes.c_int32), ("pull_hot_slots", ctypes.c_int32),
-                ("push_hot_slots", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("push_hot_slots", ctypes.c_int32), ("sssp_alpha", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class gp_graph_info(ctypes.Structure):
@@ -66,6 +67,17 @@ class gp_bfs_stats(ctypes.Structure):
                 ("direction", ctypes.c_int8 * BFS_MAX_LEVELS), ("frontier", ctypes.c_int64 * BFS_MAX_LEVELS),
                 ("examined", ctypes.c_int64 * BFS_MAX_LEVELS), ("init_ns", ctypes.c_int32),
                 ("level_ns", ctypes.c_int32 * BFS_MAX_LEVELS)]
+
+
+SSSP_MAX_ITERS = 1024
+
+
+class gp_sssp_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("epochs", ctypes.c_int32), ("reached", ctypes.c_int64),
+                ("edges_examined", ctypes.c_int64), ("pushes", ctypes.c_int32), ("pulls", ctypes.c_int32),
+                ("ms", ctypes.c_float), ("init_ns", ctypes.c_int32), ("direction", ctypes.c_int8 * SSSP_MAX_ITERS),
+                ("bucket", ctypes.c_int64 * SSSP_MAX_ITERS), ("active", ctypes.c_int64 * SSSP_MAX_ITERS),
+                ("examined", ctypes.c_int64 * SSSP_MAX_ITERS), ("iter_ns", ctypes.c_int32 * SSSP_MAX_ITERS)]
 
 
 class gp_batch_stats(ctypes.Structure):
@@ -106,6 +118,8 @@ SIGNATURES = [
     ("gp_bfs", ctypes.c_int, [_VP, _I32, ctypes.c_int, _VP, _VP, ctypes.POINTER(gp_bfs_stats), _VP]),
     ("gp_bfs_directed", ctypes.c_int, [_VP, _I32, _VP, ctypes.c_int, _VP, _VP, ctypes.POINTER(gp_bfs_stats),
                                        _VP]),
+    ("gp_sssp", ctypes.c_int, [_VP, _I32, _F, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP,
+                               ctypes.POINTER(gp_sssp_stats), _VP]),
     ("gp_batch_create", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _VP]),
     ("gp_batch_free", ctypes.c_int, [_VP]),
     ("gp_ppr_batched", ctypes.c_int, [_VP, _VP, _F, ctypes.c_int, _D, ctypes.POINTER(_VP), _VP,
@@ -378,6 +392,30 @@ def bfs(g: Graph, src: int, mode=AUTO, level=None, parent=None, want_parent=True
     return level, parent, stats
 
 
+def sssp(g: Graph, src: int, delta: float, mode=AUTO, dist=None, pred=None, want_pred=True, dirs=None,
+         stream=None, want_stats=True):
+    """gp_sssp.  Returns (dist, pred or None, stats dict or None)."""
+    torch = _torch()
+    if dist is None:
+        dist = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    if pred is None and want_pred:
+        pred = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    st = gp_sssp_stats()
+    d = None if dirs is None else np.ascontiguousarray(np.asarray(dirs, dtype=np.int8))
+    _check(load().gp_sssp(g.handle, int(src), float(delta), int(mode), _ptr(d), 0 if d is None else int(d.shape[0]),
+                          _ptr(dist), _ptr(pred), ctypes.byref(st) if want_stats else None, _stream_ptr(stream)),
+           "gp_sssp")
+    if not want_stats:
+        return dist, pred, None
+    L = min(st.iterations, SSSP_MAX_ITERS)
+    stats = {"iterations": st.iterations, "epochs": st.epochs, "reached": st.reached,
+             "edges_examined": st.edges_examined, "pushes": st.pushes, "pulls": st.pulls, "ms": st.ms,
+             "init_us": st.init_ns / 1e3, "direction": list(st.direction[:L]), "bucket": list(st.bucket[:L]),
+             "active": list(st.active[:L]), "examined": list(st.examined[:L]),
+             "iter_us": [x / 1e3 for x in st.iter_ns[:L]]}
+    return dist, pred, stats
+
+
 class Batch:
     """gp_batch: batched personalised PageRank and multi-source BFS over several graphs."""
 
@@ -430,7 +468,7 @@ class Batch:
 
 
 OPTION_FIELDS = ["pull_light_max", "push_light_max", "chunk_edges", "blocks_per_sm", "poll_interval", "pr_auto_mode",
-                 "bfs_alpha", "bfs_beta", "push_fp64_accum", "pull_hot_slots", "push_hot_slots"]
+                 "bfs_alpha", "bfs_beta", "push_fp64_accum", "pull_hot_slots", "push_hot_slots", "sssp_alpha"]
 
 
 def options_dict(o: gp_options) -> dict:

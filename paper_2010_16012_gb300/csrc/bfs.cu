@@ -109,21 +109,6 @@ __device__ __forceinline__ bool td_claim(const BfsArgs &a, int32_t w, int32_t u)
     return true;
 }
 
-// Position of the j-th (0-based) set bit of x (j < popc(x)).
-__device__ __forceinline__ int nth_set_bit(uint32_t x, int j) {
-    int pos = 0;
-#pragma unroll
-    for (int s = 16; s > 0; s >>= 1) {
-        const int c = __popc(x & ((1u << s) - 1u));
-        if (j >= c) {
-            j -= c;
-            x >>= s;
-            pos += s;
-        }
-    }
-    return pos;
-}
-
 __device__ void flush_counters(const BfsArgs &a, unsigned long long nf, unsigned long long mf, unsigned long long mu,
                                unsigned long long ex) {
     __shared__ unsigned long long sm[32];

@@ -169,6 +169,8 @@ struct BfsWork {
 
 }  // namespace gp
 
+struct gp_sssp_work;  // shortest-path workspace (sssp.cu)
+
 struct gp_graph {
     int device = 0;
     int num_sms = 0;
@@ -186,6 +188,7 @@ struct gp_graph {
     gp::HotSet push_hot;    // shared-memory accumulators of the push scatter
     gp::PrWork pr;
     gp::BfsWork bfs;
+    gp_sssp_work *sssp = nullptr;
     gp::Arena mem;          // copies of the arrays and degree data
     cudaStream_t home = nullptr;
 };
@@ -312,6 +315,21 @@ __device__ __forceinline__ float f64_to_f32_rn(double v) {
     unsigned r = ((unsigned)e8 << 23) | keep;
     if (rest > 0x10000000u || (rest == 0x10000000u && (keep & 1u))) ++r;  // a carry into the exponent is exact
     return __uint_as_float(sign | r);  // a carry out of e8 = 254 gives 0x7f800000: infinity
+}
+
+// Position of the j-th (0-based) set bit of x (j < popc(x)).
+__device__ __forceinline__ int nth_set_bit(uint32_t x, int j) {
+    int pos = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        const int c = __popc(x & ((1u << s) - 1u));
+        if (j >= c) {
+            j -= c;
+            x >>= s;
+            pos += s;
+        }
+    }
+    return pos;
 }
 
 // ------------------------------------------------------------------ grid barrier

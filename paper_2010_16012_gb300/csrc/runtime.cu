@@ -629,6 +629,7 @@ int build_bins(gp_graph *g, BigBins &b, const int64_t *off, int32_t light_max, i
 namespace gp {
 void release_pr_work(gp_graph *g, cudaStream_t s);
 void release_bfs_work(gp_graph *g, cudaStream_t s);
+void release_sssp_work(gp_graph *g, cudaStream_t s);
 }  // namespace gp
 
 using namespace gp;
@@ -688,6 +689,7 @@ int gp_options_default(gp_options *opt) {
     opt->push_fp64_accum = 1;
     opt->pull_hot_slots = 16384;
     opt->push_hot_slots = 16384;
+    opt->sssp_alpha = 1.0f;
     return GP_OK;
 }
 
@@ -941,6 +943,7 @@ int gp_graph_free(gp_graph *g) {
     cudaDeviceSynchronize();
     release_pr_work(g, s);
     release_bfs_work(g, s);
+    release_sssp_work(g, s);
     g->pull_bins.mem.release(s);
     g->push_bins.mem.release(s);
     g->pull_hot.mem.release(s);
@@ -986,7 +989,7 @@ int gp_graph_set_options(gp_graph *g, const gp_options *opt, void *stream) {
     if (opt->pull_light_max < 0 || opt->push_light_max < 0 || opt->pull_light_max > (1 << 20) ||
         opt->push_light_max > (1 << 20) || opt->chunk_edges < 32 || opt->chunk_edges > (1 << 24) ||
         opt->blocks_per_sm < 1 || opt->blocks_per_sm > 32 || opt->poll_interval < 1 ||
-        !(opt->bfs_alpha > 0.f) || !(opt->bfs_beta > 0.f) || opt->pr_auto_mode < -1 || opt->pr_auto_mode > 1 ||
+        !(opt->bfs_alpha > 0.f) || !(opt->bfs_beta > 0.f) || !(opt->sssp_alpha > 0.f) || opt->pr_auto_mode < -1 || opt->pr_auto_mode > 1 ||
         (opt->push_fp64_accum != 0 && opt->push_fp64_accum != 1) || opt->pull_hot_slots < 0 ||
         opt->pull_hot_slots > 49152 || opt->push_hot_slots < 0 || opt->push_hot_slots > 49152)
         return set_error(GP_ERR_INVALID, "gp_graph_set_options: option out of range");
@@ -1003,6 +1006,7 @@ int gp_graph_set_options(gp_graph *g, const gp_options *opt, void *stream) {
         // workspace sizes depend on the grid and the chunk count: rebuild lazily
         release_pr_work(g, s);
         release_bfs_work(g, s);
+        release_sssp_work(g, s);
     }
     if (st != GP_OK) {
         g->opt = old;

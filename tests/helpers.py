@@ -214,3 +214,74 @@ def floyd_warshall_dist(n, src, dst, w):
     for k in range(n):
         D = np.minimum(D, D[:, k:k + 1] + D[k:k + 1, :])
     return D
+
+
+def check_sssp_certificate(csr_off, csr_idx, csr_w, src, dist, pred):
+    """Conditions that make `dist` the exact shortest distances at any size:
+    dist[src] = 0; every edge u->v with finite dist[u] satisfies dist[v] <=
+    dist[u] + w (so no path is shorter than dist: dist is a lower bound); every
+    reached v != src has a tight predecessor edge, dist[v] = dist[pred] + w, and
+    the predecessors lead back to src (so dist[v] is the length of a real path);
+    unreached vertices have dist inf and pred -1.
+    Weights are compared in FP32 as the library forms the sums.  Returns the
+    number of violations."""
+    dist = np.asarray(dist, dtype=np.float32)
+    pred = np.asarray(pred, dtype=np.int64)
+    n = dist.shape[0]
+    deg = np.diff(csr_off)
+    u = np.repeat(np.arange(n, dtype=np.int64), deg)
+    w = np.ones(csr_idx.shape[0], dtype=np.float32) if csr_w is None else np.asarray(csr_w, dtype=np.float32)
+    bad = int(dist[src] != 0) + int(pred[src] != src)
+    fin = np.isfinite(dist[u])
+    relax = (dist[u] + w).astype(np.float32)
+    bad += int(np.count_nonzero(fin & (dist[csr_idx] > relax)))
+    reached = np.isfinite(dist)
+    bad += int(np.count_nonzero(~reached & (pred != -1)))
+    v = np.nonzero(reached)[0]
+    v = v[v != src]
+    p = pred[v]
+    ok = (p >= 0) & (p < n)
+    bad += int(np.count_nonzero(~ok))
+    v, p = v[ok], p[ok]
+    # tight predecessor edge p->v: the slot of v in p's sorted row (vectorised
+    # binary search), whose weight makes dist[p] + w == dist[v]
+    lo, hi = csr_off[p].copy(), csr_off[p + 1].copy()
+    while True:
+        active = lo < hi
+        if not active.any():
+            break
+        mid = (lo + hi) // 2
+        mv = np.where(active, csr_idx[np.minimum(mid, len(csr_idx) - 1)], 0)
+        less = active & (mv < v)
+        lo = np.where(less, mid + 1, lo)
+        hi = np.where(active & ~less, mid, hi)
+    found = (lo < csr_off[p + 1]) & (csr_idx[np.minimum(lo, len(csr_idx) - 1)] == v)
+    wv = w[np.minimum(lo, len(w) - 1)]
+    tight = found & ((dist[p] + wv).astype(np.float32) == dist[v])
+    bad += int(np.count_nonzero(~tight))
+    # the predecessor pointers reach src from every reached vertex (no cycle of
+    # zero-weight tight edges): follow them by pointer doubling
+    hop = np.where(reached, pred, -1)
+    hop[src] = src
+    cur = np.where(reached, hop, -1)
+    for _ in range(int(np.ceil(np.log2(max(n, 2)))) + 1):
+        nxt = np.where(cur >= 0, hop[np.maximum(cur, 0)], -1)
+        cur = nxt
+    bad += int(np.count_nonzero(reached & (cur != src)))
+    return bad
+
+
+def smallest_tight_pred(csr_off, csr_idx, csr_w, src, dist):
+    """For each reached v != src, the smallest u with an edge u->v and dist[u] + w == dist[v] (FP32)."""
+    dist = np.asarray(dist, dtype=np.float32)
+    n = dist.shape[0]
+    u = np.repeat(np.arange(n, dtype=np.int64), np.diff(csr_off))
+    w = np.ones(csr_idx.shape[0], dtype=np.float32) if csr_w is None else np.asarray(csr_w, dtype=np.float32)
+    tight = np.isfinite(dist[u]) & ((dist[u] + w).astype(np.float32) == dist[csr_idx])
+    out = np.full(n, -1, dtype=np.int64)
+    best = np.full(n, np.iinfo(np.int64).max, dtype=np.int64)
+    np.minimum.at(best, csr_idx[tight].astype(np.int64), u[tight])
+    has = best != np.iinfo(np.int64).max
+    out[has] = best[has]
+    out[src] = src
+    return out

@@ -13,7 +13,9 @@ times (options chosen by gp_autotune on the graph itself):
   64 BFS sources per graph in one persistent launch, sampled vectors and
   sources against the oracle;
 - weighted R-MAT scale 20: forward PageRank then the adjoint, against the FP64
-  oracle's adjoint of its own fixed point (1e-4 relative).
+  oracle's adjoint of its own fixed point (1e-4 relative);
+- Delta-Stepping SSSP on R-MAT scale 22 with integer weights: bit-exact against
+  Dijkstra for one source, the shortest-path certificate for three.
 
 The threaded oracle finishes each comparison in seconds on the host cores."""
 import numpy as np
@@ -202,4 +204,26 @@ def test_weighted_rmat20_forward_and_adjoint(gp):
         a = a.cpu().numpy().astype(np.float64)
         rel = np.abs(a - ref).max() / np.abs(ref).max()
         assert rel <= REL, rel
+    G.free()
+
+
+# ---------------------------------------------------------------- SSSP on R-MAT scale 22, integer weights
+
+def test_rmat22_sssp(gp):
+    """Delta-Stepping (AUTO, delta 64) on the benchmark graph with integer
+    weights in [1, 255]: distances bit-exact against Dijkstra for one source,
+    and the shortest-path certificate on every vertex for three."""
+    from helpers import check_sssp_certificate
+
+    g = gg.with_int_weights(gg.rmat(22, 16, seed=1), seed=3, lo=1, hi=255)
+    G = gp.Graph.from_graphgen(g)
+    srcs = gg.pick_vertices(g, 3, seed=2)
+    O = oracle.OracleGraph.from_graph(g)
+    for i, s in enumerate(srcs):
+        dist, pred, st = gp.sssp(G, int(s), 64.0, gp.AUTO)
+        d, p = dist.cpu().numpy(), pred.cpu().numpy()
+        assert check_sssp_certificate(g.csr_off, g.csr_idx, g.csr_w, int(s), d, p) == 0, s
+        if i == 0:
+            ref, _ = O.sssp(int(s))
+            assert np.array_equal(d.astype(np.float64), ref)
     G.free()

@@ -9,8 +9,8 @@ import pytest
 import graphgen as gg
 import oracle
 from helpers import (check_levels_by_edges, check_parents, check_parents_np, dense_pagerank, dense_transition,
-                     edge_sources, floyd_warshall_dist, floyd_warshall_levels, parse_bfs_case, parse_pagerank_cases,
-                     parse_sssp_cases)
+                     check_sssp_certificate, edge_sources, floyd_warshall_dist, floyd_warshall_levels,
+                     parse_bfs_case, parse_pagerank_cases, parse_sssp_cases, smallest_tight_pred)
 
 VARIANTS = [oracle.PUSH, oracle.PULL]
 
@@ -441,3 +441,37 @@ def test_sssp_delta_epochs_follow_bucket_width():
     assert epochs == n and np.array_equal(dist, np.arange(n, dtype=np.float64))
     dist, iters, epochs = G.sssp_delta(0, 1e9, [0])
     assert epochs == 1 and iters == n  # n - 1 hops, then one iteration that changes nothing
+
+
+def test_sssp_certificate_catches_planted_mistakes():
+    """The size-independent shortest-path certificate accepts the oracle's
+    distances and rejects a distance too long, one too short, a wrong
+    predecessor and a reached vertex marked unreachable."""
+    g = gg.with_int_weights(gg.rmat(10, 8, seed=18, symmetrize=False), seed=19, lo=1, hi=20)
+    G = og(g)
+    src = int(gg.pick_vertices(g, 1, seed=20)[0])
+    dist, _ = G.sssp(src)
+    d32 = dist.astype(np.float32)
+    pred = smallest_tight_pred(g.csr_off, g.csr_idx, g.csr_w, src, d32)
+    assert check_sssp_certificate(g.csr_off, g.csr_idx, g.csr_w, src, d32, pred) == 0
+    far = int(np.nanargmax(np.where(np.isfinite(d32), d32, -1)))
+    for delta in (1.0, -1.0):
+        bad = d32.copy()
+        bad[far] += delta
+        assert check_sssp_certificate(g.csr_off, g.csr_idx, g.csr_w, src, bad, pred) > 0
+    badp = pred.copy()
+    badp[far] = src if pred[far] != src else far
+    assert check_sssp_certificate(g.csr_off, g.csr_idx, g.csr_w, src, d32, badp) > 0
+    bad = d32.copy()
+    bad[far] = np.inf
+    assert check_sssp_certificate(g.csr_off, g.csr_idx, g.csr_w, src, bad, pred) > 0
+
+
+def test_smallest_tight_pred_matches_definition():
+    n, s, d, w, cases = parse_sssp_cases()
+    csr = gg.from_edges(n, np.array(s), np.array(d), dedup=False)
+    order = np.lexsort((np.array(d), np.array(s)))
+    wcsr = np.array(w, dtype=np.float32)[order]
+    for src, dist, pred in cases:
+        got = smallest_tight_pred(csr.csr_off, csr.csr_idx, wcsr, src, np.array(dist, dtype=np.float32))
+        assert list(got) == pred
