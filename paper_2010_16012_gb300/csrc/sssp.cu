@@ -105,6 +105,9 @@ __device__ __forceinline__ unsigned long long ss_now() {
     return t;
 }
 
+// Edge indices and weights are streamed with the evict-first hint (__ldcs) so
+// that they do not push the 8-byte keys, gathered at random, out of L2.
+
 struct SsLocal {  // per-thread counter contributions of an iteration
     unsigned long long nact = 0, mact = 0, npend = 0, examined = 0;
 };
@@ -210,8 +213,8 @@ __device__ void ss_push_a(const SsRun &R, const uint32_t *act_cur, uint32_t *act
                 const float odu = __shfl_sync(FULL, du, o);
                 if (eid < E) {
                     const int64_t pos = ob + (eid - oex);
-                    const int32_t w = __ldg(R.csr_idx + pos);
-                    const float wt = R.csr_w ? __ldg(R.csr_w + pos) : 1.f;
+                    const int32_t w = __ldcs(R.csr_idx + pos);
+                    const float wt = R.csr_w ? __ldcs(R.csr_w + pos) : 1.f;
                     ++c.examined;
                     ss_offer(R, act_next, b, odu + wt, ou, w, c);
                 }
@@ -236,8 +239,8 @@ __device__ void ss_push_b(const SsRun &R, uint32_t *act_next, int64_t h_len, uns
 #pragma unroll
             for (int q = 0; q < U; ++q) {
                 const int i = i0 + 32 * q;
-                w[q] = i < ch.len ? __ldg(R.csr_idx + ch.beg + i) : -1;
-                wt[q] = i < ch.len && R.csr_w ? __ldg(R.csr_w + ch.beg + i) : 1.f;
+                w[q] = i < ch.len ? __ldcs(R.csr_idx + ch.beg + i) : -1;
+                wt[q] = i < ch.len && R.csr_w ? __ldcs(R.csr_w + ch.beg + i) : 1.f;
             }
 #pragma unroll
             for (int q = 0; q < U; ++q) seen[q] = w[q] >= 0 ? R.key[w[q]] : 0ull;
@@ -271,10 +274,10 @@ __device__ void ss_pull(const SsRun &R, const uint32_t *act_cur, uint32_t *act_n
         if (!((R.unset[ch.v >> 5] >> (ch.v & 31)) & 1u) || ch.v == R.src) continue;  // uniform: settled
         unsigned long long best = SS_NONE;
         for (int i = lane; i < ch.len; i += 32) {
-            const int32_t u = __ldg(R.csc_idx + ch.beg + i);
+            const int32_t u = __ldcs(R.csc_idx + ch.beg + i);
             ++c.examined;
             if ((act_cur[u >> 5] >> (u & 31)) & 1u) {
-                const float wt = R.csc_w ? __ldg(R.csc_w + ch.beg + i) : 1.f;
+                const float wt = R.csc_w ? __ldcs(R.csc_w + ch.beg + i) : 1.f;
                 const unsigned long long cand = ss_pack(ss_dist(R.key[u]) + wt, (uint32_t)u);
                 best = cand < best ? cand : best;
             }
@@ -307,10 +310,10 @@ __device__ void ss_pull(const SsRun &R, const uint32_t *act_cur, uint32_t *act_n
             unsigned long long best = own;
             const int64_t e = R.csc_off[v + 1];
             for (int64_t p = R.csc_off[v]; p < e; ++p) {
-                const int32_t u = __ldg(R.csc_idx + p);
+                const int32_t u = __ldcs(R.csc_idx + p);
                 ++c.examined;
                 if ((act_cur[u >> 5] >> (u & 31)) & 1u) {
-                    const float wt = R.csc_w ? __ldg(R.csc_w + p) : 1.f;
+                    const float wt = R.csc_w ? __ldcs(R.csc_w + p) : 1.f;
                     const unsigned long long cand = ss_pack(ss_dist(R.key[u]) + wt, (uint32_t)u);
                     best = cand < best ? cand : best;
                 }
