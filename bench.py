@@ -709,9 +709,27 @@ def run_only_sssp(args):
     kt = {k[0]: k for k in gp.profile_read(reset=True)}
     k = kt["sssp_persistent"]
     ms = k[2] / k[1]
+    # compulsory bytes of a search: every examined edge's index and weight (8 B)
+    # and one 8-byte key read per relaxation, over the event-timed search
+    ex = float(np.mean([s["edges_examined"] for s in stats]))
+    peak, peak_kind = measured_peak_gbs()
+    ach = 16.0 * ex / (ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+            "peak_kind": peak_kind, "bytes_per_search": int(16 * ex)}
+    cpu = None
+    if not args.no_cpu_baseline:  # the oracle's Dijkstra on the host cores, one source
+        import oracle
+
+        O = oracle.OracleGraph.from_graph(g)
+        t0 = time.perf_counter()
+        O.sssp(int(srcs[0]))
+        dt = time.perf_counter() - t0
+        cpu = {"kind": "oracle", "what": "Dijkstra (binary heap, FP64), 1 thread, first source",
+               "ms": round(dt * 1e3, 1), "cores": 1, "gteps": round(edges[0] / dt / 1e9, 4)}
     print(json.dumps({"profile_case": "sssp", "scale": args.scale, "n": g.n, "m": g.m, "weights": "int [1, 255]",
                       "delta": args.delta, "mode": args.mode, "opts": opts, "sources": len(srcs),
                       "avg_launch_ms": round(ms, 4), "gteps": round(sum(edges) / (ms * 1e-3 * len(srcs)) / 1e9, 2),
+                      "roofline": roof, "cpu_oracle": cpu,
                       "iterations": round(float(np.mean([s["iterations"] for s in stats])), 1),
                       "epochs": round(float(np.mean([s["epochs"] for s in stats])), 1),
                       "pulls": round(float(np.mean([s["pulls"] for s in stats])), 1),

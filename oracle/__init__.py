@@ -66,6 +66,8 @@ def _get():
             lib.or_sssp_dijkstra.argtypes = [vp, c.c_int32, vp, vp]
             lib.or_sssp_delta.restype = c.c_int64
             lib.or_sssp_delta.argtypes = [vp, c.c_int32, c.c_double, vp, c.c_int, vp, c.POINTER(c.c_int64)]
+            lib.or_triangles.restype = c.c_int64
+            lib.or_triangles.argtypes = [vp, c.c_int, vp, c.c_int]
             lib.or_max_threads.restype = c.c_int
             lib.or_max_threads.argtypes = []
             _lib = lib
@@ -173,6 +175,15 @@ class OracleGraph:
         it = self._lib.or_sssp_delta(self._h, int(src), float(delta), _ptr(d), int(d.shape[0]), _ptr(dist),
                                      ctypes.byref(ep))
         return dist, int(it), ep.value
+
+
+    # ------------------------------------------------------------ triangles
+    def triangles(self, variant: int = PULL, nthreads: int = 1):
+        """NodeIterator triangle counts (the graph must be symmetric, simple).
+        Returns (tc int64[n], total triangles)."""
+        tc = np.empty(self.n, dtype=np.int64)
+        total = self._lib.or_triangles(self._h, int(variant), _ptr(tc), int(nthreads))
+        return tc, int(total)
 
 
 def max_threads() -> int:

@@ -29,6 +29,9 @@
  *     paths of the weight sum), and the push- and pull-based Delta-Stepping of
  *     the paper's Section 3 listing, run sequentially with one direction per
  *     relaxation iteration.
+ *   - Triangle counting (the NodeIterator listing of Section 3): for every v
+ *     and every ordered pair (w1, w2) of v's neighbours with w1 adjacent to
+ *     w2, pull adds one to tc[v], push adds one to tc[w1]; both halve.
  *
  * Readings of the paper where it is silent or ambiguous (each is a choice the
  * CUDA path makes identically):
@@ -517,6 +520,81 @@ int64_t or_sssp_delta(const or_graph *g, int32_t r, double delta, const int8_t *
     free(nxt);
     if (epochs) *epochs = ep;
     return it;
+}
+
+/* ------------------------------------------------------------------ triangle counting */
+
+static int or_cmp_i32(const void *a, const void *b) {
+    const int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* adj(a, b): b is an out-neighbour of a (binary search in a's sorted row of `sorted`). */
+static int or_adj(const or_graph *g, const int32_t *sorted, int32_t a, int32_t b) {
+    int64_t lo = g->out_off[a], hi = g->out_off[a + 1];
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (sorted[mid] < b)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo < g->out_off[a + 1] && sorted[lo] == b;
+}
+
+/*
+ * Triangle counts of a simple undirected graph given as its symmetric directed
+ * version (self-loops skipped): the NodeIterator listing of Section 3, written
+ * out.  For every v, every w1 in N(v) and every w2 in N(v) (w1 != w2, both !=
+ * v): if adj(w1, w2), variant 1 (pull) adds one to tc[v] and variant 0 (push)
+ * adds one to tc[w1].  Every count is halved at the end (each triangle at a
+ * vertex is met as (w1, w2) and as (w2, w1)).  The pull variant runs its outer
+ * loop on nthreads threads (each tc[v] has one writer, so the counts do not
+ * change).  Returns the number of triangles (sum of tc / 3).
+ */
+int64_t or_triangles(const or_graph *g, int variant, int64_t *tc, int nthreads) {
+    const int64_t n = g->n;
+    for (int64_t v = 0; v < n; ++v) tc[v] = 0;
+    or_set_threads(nthreads);
+    /* rows sorted (a copy) so that adj() is a binary search */
+    int32_t *sorted = (int32_t *)malloc((size_t)(g->m > 0 ? g->m : 1) * sizeof(int32_t));
+    memcpy(sorted, g->out_idx, (size_t)g->m * sizeof(int32_t));
+    for (int64_t v = 0; v < n; ++v)
+        qsort(sorted + g->out_off[v], (size_t)(g->out_off[v + 1] - g->out_off[v]), sizeof(int32_t), or_cmp_i32);
+    if (variant == 1) {
+#pragma omp parallel for schedule(dynamic, 64) if (nthreads > 1)
+        for (int64_t v = 0; v < n; ++v) {
+            int64_t c = 0;
+            for (int64_t i = g->out_off[v]; i < g->out_off[v + 1]; ++i) {
+                const int32_t w1 = g->out_idx[i];
+                if (w1 == v) continue;
+                for (int64_t j = g->out_off[v]; j < g->out_off[v + 1]; ++j) {
+                    const int32_t w2 = g->out_idx[j];
+                    if (w2 == v || w2 == w1) continue;
+                    c += or_adj(g, sorted, w1, w2);
+                }
+            }
+            tc[v] = c;
+        }
+    } else {
+        for (int64_t v = 0; v < n; ++v)
+            for (int64_t i = g->out_off[v]; i < g->out_off[v + 1]; ++i) {
+                const int32_t w1 = g->out_idx[i];
+                if (w1 == v) continue;
+                for (int64_t j = g->out_off[v]; j < g->out_off[v + 1]; ++j) {
+                    const int32_t w2 = g->out_idx[j];
+                    if (w2 == v || w2 == w1) continue;
+                    tc[w1] += or_adj(g, sorted, w1, w2);
+                }
+            }
+    }
+    free(sorted);
+    int64_t total = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        tc[v] /= 2;
+        total += tc[v];
+    }
+    return total / 3;
 }
 
 /* Number of OpenMP threads a parallel region gets (1 without OpenMP). */

@@ -475,3 +475,59 @@ def test_smallest_tight_pred_matches_definition():
     for src, dist, pred in cases:
         got = smallest_tight_pred(csr.csr_off, csr.csr_idx, wcsr, src, np.array(dist, dtype=np.float32))
         assert list(got) == pred
+
+
+# ------------------------------------------------------------------ triangle counting (NodeIterator, Section 3 listing)
+
+def brute_triangles(n, u, v):
+    """Per-vertex triangle counts from the adjacency matrix: tc[i] = sum over
+    j < k of A[i,j] A[i,k] A[j,k]; the total is trace(A^3) / 6."""
+    A = np.zeros((n, n), dtype=np.int64)
+    A[u, v] = 1
+    A[v, u] = 1
+    np.fill_diagonal(A, 0)
+    A3 = A @ A @ A
+    return np.diag(A3) // 2, int(np.trace(A3) // 6)
+
+
+@pytest.mark.parametrize("variant", [oracle.PUSH, oracle.PULL])
+@pytest.mark.parametrize("seed", range(6))
+def test_triangles_match_adjacency_cube(variant, seed):
+    rng = np.random.default_rng(700 + seed)
+    n = int(rng.integers(3, 40))
+    g = gg.random_small(n, float(rng.uniform(0.05, 0.6)), seed=700 + seed, directed=False)
+    src, dst = g.edges()
+    tc, total = og(g).triangles(variant)
+    ref, rtot = brute_triangles(n, src, dst)
+    assert np.array_equal(tc, ref) and total == rtot
+
+
+def test_triangles_closed_forms():
+    from math import comb
+
+    for k in (3, 4, 7, 12):  # K_k: every vertex in C(k-1, 2) triangles
+        tc, total = og(gg.complete(k)).triangles(oracle.PULL)
+        assert (tc == comb(k - 1, 2)).all() and total == comb(k, 3)
+    a, b = 5, 7  # complete bipartite: no triangles
+    u = np.repeat(np.arange(a), b)
+    v = np.tile(np.arange(a, a + b), a)
+    tc, total = og(gg.from_edges(a + b, u, v, symmetrize=True)).triangles(oracle.PUSH)
+    assert total == 0 and not tc.any()
+    r = 9  # wheel: hub 0 and a rim cycle 1..r: hub in r triangles, each rim vertex in 2
+    rim = np.arange(1, r + 1)
+    u = np.concatenate([np.zeros(r, int), rim])
+    v = np.concatenate([rim, np.roll(rim, -1)])
+    tc, total = og(gg.from_edges(r + 1, u, v, symmetrize=True)).triangles(oracle.PULL)
+    assert tc[0] == r and (tc[1:] == 2).all() and total == r
+    tc, total = og(gg.binary_tree(100)).triangles(oracle.PULL)  # trees have none
+    assert total == 0
+
+
+def test_triangles_push_equals_pull_and_threads():
+    g = gg.rmat(12, 8, seed=22)
+    G = og(g)
+    a, ta = G.triangles(oracle.PULL, nthreads=1)
+    b, tb = G.triangles(oracle.PUSH)
+    c, tcn = G.triangles(oracle.PULL, nthreads=4)
+    assert np.array_equal(a, b) and np.array_equal(a, c) and ta == tb == tcn > 0
+    assert a.sum() == 3 * ta
