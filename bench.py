@@ -53,7 +53,7 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--quiet", action="store_true")
     p.add_argument("--no-batched", action="store_true")
-    p.add_argument("--only", choices=["pr_pull", "pr_push", "bfs", "batched", "sssp"], default=None,
+    p.add_argument("--only", choices=["pr_pull", "pr_push", "bfs", "batched", "sssp", "tc"], default=None,
                    help="profiling case: run only this part (fixed --sweeps for PageRank), no contract line")
     p.add_argument("--sweeps", type=int, default=4)
     p.add_argument("--delta", type=float, default=64.0, help="--only sssp: bucket width")
@@ -632,6 +632,8 @@ def run_only(args):
         return 0
     if args.only == "sssp":
         return run_only_sssp(args)
+    if args.only == "tc":
+        return run_only_tc(args)
     g = make_graph(args.scale)
     off = torch.from_numpy(g.csr_off).cuda()
     idx = torch.from_numpy(g.csr_idx).cuda()
@@ -739,6 +741,52 @@ def run_only_sssp(args):
                       "iter_table": [[d, b, a, e, round(t, 1)] for d, b, a, e, t in
                                      zip(stats[-1]["direction"], stats[-1]["bucket"], stats[-1]["active"],
                                          stats[-1]["examined"], stats[-1]["iter_us"])]}), flush=True)
+    return 0
+
+
+def run_only_tc(args):
+    """Triangle counting (NodeIterator, push and pull) on the R-MAT graph of
+    --scale: per-vertex counts, ms per run, edges per second; the oracle's
+    threaded pull form timed beside it (unless --no-cpu-baseline)."""
+    import torch
+
+    import paper_2010_16012_gb300 as gp
+
+    g = make_graph(args.scale)
+    G = gp.Graph.from_graphgen(g)
+    opts = {}
+    for kv in args.opt:
+        k, v = kv.split("=")
+        opts[k] = float(v) if k.endswith("_alpha") or k.endswith("_beta") else int(v)
+    if opts:
+        G.set_options(**opts)
+    out = {}
+    counts = {}
+    for name, mode in (("pull", gp.PULL), ("push", gp.PUSH)):
+        tc = torch.empty(g.n, dtype=torch.int64, device="cuda")
+        for _ in range(args.warmup):
+            gp.triangles(G, mode, out=tc)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            _, total, st = gp.triangles(G, mode, out=tc)
+            ms.append(st["ms"])
+        counts[name] = tc.cpu().numpy()
+        t = statistics.median(ms)
+        out[name] = {"ms": round(t, 3), "triangles": total, "probes": st["probes"],
+                     "gteps": round(g.m / (t * 1e-3) / 1e9, 3)}
+    out["push_equals_pull"] = bool(np.array_equal(counts["push"], counts["pull"]))
+    if not args.no_cpu_baseline:
+        import oracle
+
+        O = oracle.OracleGraph.from_graph(g)
+        t0 = time.perf_counter()
+        ref, rtot = O.triangles(oracle.PULL, nthreads=oracle.max_threads())
+        dt = time.perf_counter() - t0
+        out["cpu_oracle"] = {"kind": "oracle", "what": "NodeIterator pull, OpenMP", "cores": oracle.max_threads(),
+                             "ms": round(dt * 1e3, 1), "gteps": round(g.m / dt / 1e9, 4)}
+        out["equals_oracle"] = bool(np.array_equal(counts["pull"], ref))
+    print(json.dumps({"profile_case": "tc", "scale": args.scale, "n": g.n, "m": g.m, "opts": opts, **out}), flush=True)
     return 0
 
 

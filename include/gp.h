@@ -370,6 +370,31 @@ typedef struct gp_sssp_stats {
 int gp_sssp(const gp_graph *g, int32_t src, float delta, int mode, const int8_t *dirs, int ndirs, float *dist_out,
             int32_t *pred_out, gp_sssp_stats *stats, void *stream);
 
+/* ------------------------------------------------------------------ triangle counting */
+
+typedef struct gp_tc_stats {
+    int64_t triangles; /* number of triangles (sum of the counts / 3) */
+    int64_t probes;    /* list elements searched for (shorter list of every ordered edge) */
+    float ms;          /* device time of the call by CUDA events */
+    int32_t mode_used; /* GP_PUSH or GP_PULL */
+} gp_tc_stats;
+
+/*
+ * Per-vertex triangle counts by the NodeIterator of Section 3 (push- and
+ * pull-based Triangle Counting): for every v and every ordered pair (w1, w2) of
+ * v's neighbours with w1 adjacent to w2, GP_PULL adds one to tc[v] (every count
+ * written only by the warp that owns v) and GP_PUSH adds one to tc[w1] with a
+ * fetch-and-add; both halve.  GP_AUTO runs the pull form (no atomics).  The
+ * graph must have been uploaded as symmetric (GP_UPLOAD_SYMMETRIC) and be simple
+ * (no duplicate edges; self-loops are skipped).
+ *   tc_out      int64[n] "any" or NULL: triangles containing each vertex.
+ *   total_out   host int64 or NULL: number of triangles.
+ *   stats       NULL or filled on return.
+ * Waits for completion.  GP_ERR_INVALID for a directed graph, a bad mode or no
+ * output.
+ */
+int gp_triangles(const gp_graph *g, int mode, int64_t *tc_out, int64_t *total_out, gp_tc_stats *stats, void *stream);
+
 /* ------------------------------------------------------------------ batches of graphs */
 
 typedef struct gp_batch gp_batch; /* opaque: a work plan over several uploaded graphs */

@@ -80,6 +80,11 @@ class gp_sssp_stats(ctypes.Structure):
                 ("examined", ctypes.c_int64 * SSSP_MAX_ITERS), ("iter_ns", ctypes.c_int32 * SSSP_MAX_ITERS)]
 
 
+class gp_tc_stats(ctypes.Structure):
+    _fields_ = [("triangles", ctypes.c_int64), ("probes", ctypes.c_int64), ("ms", ctypes.c_float),
+                ("mode_used", ctypes.c_int32)]
+
+
 class gp_batch_stats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int32), ("levels", ctypes.c_int32), ("ms", ctypes.c_float),
                 ("blocks", ctypes.c_int32)]
@@ -120,6 +125,7 @@ SIGNATURES = [
                                        _VP]),
     ("gp_sssp", ctypes.c_int, [_VP, _I32, _F, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP,
                                ctypes.POINTER(gp_sssp_stats), _VP]),
+    ("gp_triangles", ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.POINTER(gp_tc_stats), _VP]),
     ("gp_batch_create", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _VP]),
     ("gp_batch_free", ctypes.c_int, [_VP]),
     ("gp_ppr_batched", ctypes.c_int, [_VP, _VP, _F, ctypes.c_int, _D, ctypes.POINTER(_VP), _VP,
@@ -414,6 +420,19 @@ def sssp(g: Graph, src: int, delta: float, mode=AUTO, dist=None, pred=None, want
              "active": list(st.active[:L]), "examined": list(st.examined[:L]),
              "iter_us": [x / 1e3 for x in st.iter_ns[:L]]}
     return dist, pred, stats
+
+
+def triangles(g: Graph, mode=PULL, out=None, stream=None):
+    """gp_triangles.  Returns (per-vertex counts int64, total, stats dict)."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty(g.n, dtype=torch.int64, device="cuda")
+    total = ctypes.c_int64(0)
+    st = gp_tc_stats()
+    _check(load().gp_triangles(g.handle, int(mode), _ptr(out), ctypes.byref(total), ctypes.byref(st),
+                               _stream_ptr(stream)), "gp_triangles")
+    return out, total.value, {"triangles": st.triangles, "probes": st.probes, "ms": st.ms,
+                              "mode_used": st.mode_used}
 
 
 class Batch:

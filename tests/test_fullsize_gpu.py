@@ -15,7 +15,8 @@ times (options chosen by gp_autotune on the graph itself):
 - weighted R-MAT scale 20: forward PageRank then the adjoint, against the FP64
   oracle's adjoint of its own fixed point (1e-4 relative);
 - Delta-Stepping SSSP on R-MAT scale 22 with integer weights: bit-exact against
-  Dijkstra for one source, the shortest-path certificate for three.
+  Dijkstra for one source, the shortest-path certificate for three;
+- triangle counts on R-MAT scale 16 against the oracle, scale 18 push = pull.
 
 The threaded oracle finishes each comparison in seconds on the host cores."""
 import numpy as np
@@ -226,4 +227,25 @@ def test_rmat22_sssp(gp):
         if i == 0:
             ref, _ = O.sssp(int(s))
             assert np.array_equal(d.astype(np.float64), ref)
+    G.free()
+
+
+# ---------------------------------------------------------------- triangle counting, R-MAT scale 16 and 18
+
+def test_rmat_triangles(gp):
+    """Scale 16 against the oracle vertex by vertex; scale 18 (the measured
+    case) push = pull bit-exact and the counts sum to three times the total."""
+    g = gg.rmat(16, 16, seed=1)
+    G = gp.Graph.from_graphgen(g)
+    ref, rtot = oracle.OracleGraph.from_graph(g).triangles(oracle.PULL, nthreads=NT)
+    for mode in (gp.PULL, gp.PUSH):
+        tc, total, _ = gp.triangles(G, mode)
+        assert np.array_equal(tc.cpu().numpy(), ref) and total == rtot
+    G.free()
+    g = gg.rmat(18, 16, seed=1)
+    G = gp.Graph.from_graphgen(g)
+    a, ta, _ = gp.triangles(G, gp.PULL)
+    b, tb, _ = gp.triangles(G, gp.PUSH)
+    a, b = a.cpu().numpy(), b.cpu().numpy()
+    assert np.array_equal(a, b) and ta == tb and a.sum() == 3 * ta > 0
     G.free()
