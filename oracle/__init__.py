@@ -66,6 +66,8 @@ def _get():
             lib.or_sssp_dijkstra.argtypes = [vp, c.c_int32, vp, vp]
             lib.or_sssp_delta.restype = c.c_int64
             lib.or_sssp_delta.argtypes = [vp, c.c_int32, c.c_double, vp, c.c_int, vp, c.POINTER(c.c_int64)]
+            lib.or_pagerank_fe.restype = c.c_int
+            lib.or_pagerank_fe.argtypes = [vp, c.c_double, c.c_double, c.c_int, vp, vp, c.c_int, vp, vp]
             lib.or_triangles.restype = c.c_int64
             lib.or_triangles.argtypes = [vp, c.c_int, vp, c.c_int]
             lib.or_max_threads.restype = c.c_int
@@ -176,6 +178,19 @@ class OracleGraph:
                                      ctypes.byref(ep))
         return dist, int(it), ep.value
 
+
+    # ------------------------------------------------------------ Frontier-Exploit PageRank
+    def pagerank_fe(self, damping: float = 0.85, eps: float = 1e-9, iters: int = 1000, personalization=None,
+                    dirs=(PULL,)):
+        """Residual-propagation PageRank from a frontier (|r| > eps).  Returns
+        (x, r, iterations)."""
+        x = np.empty(self.n, dtype=np.float64)
+        r = np.empty(self.n, dtype=np.float64)
+        s = None if personalization is None else np.ascontiguousarray(personalization, dtype=np.float64)
+        d = np.ascontiguousarray(np.asarray(dirs, dtype=np.int8))
+        k = self._lib.or_pagerank_fe(self._h, float(damping), float(eps), int(iters), _ptr(s), _ptr(d),
+                                     int(d.shape[0]), _ptr(x), _ptr(r))
+        return x, r, int(k)
 
     # ------------------------------------------------------------ triangles
     def triangles(self, variant: int = PULL, nthreads: int = 1):

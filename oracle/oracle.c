@@ -32,6 +32,9 @@
  *   - Triangle counting (the NodeIterator listing of Section 3): for every v
  *     and every ordered pair (w1, w2) of v's neighbours with w1 adjacent to
  *     w2, pull adds one to tc[v], push adds one to tc[w1]; both halve.
+ *   - Frontier-Exploit PageRank (Section 5's Frontier-Exploit applied to the
+ *     PageRank of Section 3.1): only vertices whose pending change exceeds
+ *     eps propagate it in an iteration (residual form, below).
  *
  * Readings of the paper where it is silent or ambiguous (each is a choice the
  * CUDA path makes identically):
@@ -520,6 +523,74 @@ int64_t or_sssp_delta(const or_graph *g, int32_t r, double delta, const int8_t *
     free(nxt);
     if (epochs) *epochs = ep;
     return it;
+}
+
+/* ------------------------------------------------------------------ Frontier-Exploit PageRank */
+
+/*
+ * PageRank by propagating pending changes (residuals) from a frontier only.
+ * State: ranks x (start 0) and residuals r (start (1-d) s).  Iteration k: the
+ * frontier is F = {u : |r_u| > eps}; every u in F moves its residual into its
+ * rank (x_u += r_u) and sends d * P_vu * r_u to each out-neighbour v, all from
+ * the residuals at the iteration's start (Jacobi):
+ *     r'_v = [v not in F] r_v + d * sum_{u in F, (u->v)} P_vu r_u.
+ * In exact arithmetic x + (I - dP)^-1 r stays equal to the fixed point x*, so
+ * on termination (F empty, every |r_u| <= eps) ||x - x*||_1 <= ||r||_1 / (1-d)
+ * for a column-substochastic P.  Iteration i uses dirs[min(i, ndirs-1)] (0
+ * push: F's vertices scatter over out-edges; 1 pull: every v gathers over
+ * in-edges from F) -- the same sums in another order.  With eps < 0 every
+ * vertex stays in F: the Jacobi iteration from x = 0.  Runs until F is empty or
+ * `iters` iterations; s (nullable) as in or_pagerank.  Returns the iterations
+ * done; r_out (nullable) receives the final residuals.
+ */
+int or_pagerank_fe(const or_graph *g, double d, double eps, int iters, const double *s, const int8_t *dirs, int ndirs,
+                   double *x, double *r_out) {
+    const int64_t n = g->n;
+    double *r = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    double *rn = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    char *act = (char *)malloc((size_t)(n > 0 ? n : 1));
+    for (int64_t v = 0; v < n; ++v) {
+        x[v] = 0.0;
+        r[v] = (1.0 - d) * (s ? s[v] : 1.0 / (double)n);
+    }
+    int k = 0;
+    while (k < iters) {
+        int64_t nf = 0;
+        for (int64_t v = 0; v < n; ++v) {
+            act[v] = eps < 0.0 || fabs(r[v]) > eps;
+            nf += act[v];
+        }
+        if (nf == 0) break;
+        for (int64_t v = 0; v < n; ++v) rn[v] = act[v] ? 0.0 : r[v];
+        if (dirs[k < ndirs ? k : ndirs - 1] == 0) {
+            for (int64_t u = 0; u < n; ++u) {
+                if (!act[u]) continue;
+                for (int64_t j = g->out_off[u]; j < g->out_off[u + 1]; ++j)
+                    rn[g->out_idx[j]] += d * or_P(g, g->out_eid[j], (int32_t)u) * r[u];
+            }
+        } else {
+            for (int64_t v = 0; v < n; ++v) {
+                double acc = 0.0;
+                for (int64_t j = g->in_off[v]; j < g->in_off[v + 1]; ++j) {
+                    const int32_t u = g->in_idx[j];
+                    if (act[u]) acc += or_P(g, g->in_eid[j], u) * r[u];
+                }
+                rn[v] += d * acc;
+            }
+        }
+        for (int64_t u = 0; u < n; ++u)
+            if (act[u]) x[u] += r[u];
+        double *t = r;
+        r = rn;
+        rn = t;
+        ++k;
+    }
+    if (r_out)
+        for (int64_t v = 0; v < n; ++v) r_out[v] = r[v];
+    free(r);
+    free(rn);
+    free(act);
+    return k;
 }
 
 /* ------------------------------------------------------------------ triangle counting */

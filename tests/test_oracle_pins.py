@@ -531,3 +531,60 @@ def test_triangles_push_equals_pull_and_threads():
     c, tcn = G.triangles(oracle.PULL, nthreads=4)
     assert np.array_equal(a, b) and np.array_equal(a, c) and ta == tb == tcn > 0
     assert a.sum() == 3 * ta
+
+
+# ------------------------------------------------------------------ Frontier-Exploit PageRank (residual form)
+
+def test_fe_pagerank_all_active_is_jacobi_from_zero():
+    """eps < 0 keeps every vertex in the frontier: k iterations are k Jacobi
+    sweeps from x = 0 (the plain PageRank iteration, pinned above)."""
+    g = gg.rmat(9, 8, seed=30, symmetrize=False)
+    G = og(g)
+    for k in (1, 2, 7, 20):
+        for dirs in ([0], [1], [0, 1]):
+            x, _, it = G.pagerank_fe(0.85, -1.0, iters=k, dirs=dirs)
+            ref, _, _, _ = G.pagerank(oracle.PULL, 0.85, iters=k, x0=np.zeros(g.n))
+            assert it == k and np.abs(x - ref).max() < 1e-15
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_fe_pagerank_invariant_and_bound(seed):
+    """x + (I - dP)^-1 r equals the fixed point (dense LU) at every stopping
+    point, the error is within ||r||_1 / (1-d), and every final |r_u| <= eps."""
+    rng = np.random.default_rng(800 + seed)
+    n = int(rng.integers(3, 13))
+    g = gg.random_small(n, float(rng.uniform(0.2, 0.7)), seed=800 + seed)
+    src, dst = g.edges()
+    w = None
+    if seed % 2:
+        w = rng.uniform(0.1, 1.0, size=len(src))
+        w = (w / np.bincount(src, weights=w, minlength=n)[src]).astype(np.float32)
+    G = oracle.OracleGraph(n, src, dst, w)
+    P = dense_transition(n, src, dst, w)
+    s = rng.uniform(0.1, 1.0, size=n)
+    s /= s.sum()
+    xs = np.linalg.solve(np.eye(n) - 0.85 * P, 0.15 * s)
+    for eps in (1e-3, 1e-6, 1e-10):
+        for iters in (3, 1000):
+            x, r, it = G.pagerank_fe(0.85, eps, iters=iters, personalization=s,
+                                     dirs=list(rng.integers(0, 2, size=40)))
+            inv = x + np.linalg.solve(np.eye(n) - 0.85 * P, r)
+            np.testing.assert_allclose(inv, xs, rtol=0, atol=1e-13)
+            if iters == 1000:
+                assert np.abs(r).max() <= eps
+                # ||(I - dP)^-1 r||_1 <= ||r||_1 / (1 - d ||P||_1), ||P||_1 the largest column
+                # sum (equality for a column-stochastic P and one-signed r)
+                pn = P.sum(axis=0).max()
+                assert np.abs(x - xs).sum() <= np.abs(r).sum() / (1 - 0.85 * pn) * (1 + 1e-12) + 1e-13
+
+
+def test_fe_pagerank_frontier_shrinks():
+    """On a graph with a fast-converging part and a slow one, later iterations
+    propagate from fewer vertices: the final result is reached with fewer edge
+    visits than full sweeps would take."""
+    g = gg.rmat(10, 8, seed=31, symmetrize=False)
+    G = og(g)
+    x, r, it = G.pagerank_fe(0.85, 1e-9, iters=1000)
+    ref, _, _, _ = G.pagerank(oracle.PULL, 0.85, iters=100000, tol=1e-15)
+    assert np.abs(r).max() <= 1e-9
+    assert np.abs(x - ref).sum() <= np.abs(r).sum() / 0.15 * (1 + 1e-12) + 1e-12
