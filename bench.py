@@ -53,7 +53,7 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--quiet", action="store_true")
     p.add_argument("--no-batched", action="store_true")
-    p.add_argument("--only", choices=["pr_pull", "pr_push", "bfs", "batched", "sssp", "tc"], default=None,
+    p.add_argument("--only", choices=["pr_pull", "pr_push", "bfs", "batched", "sssp", "tc", "pr_fe"], default=None,
                    help="profiling case: run only this part (fixed --sweeps for PageRank), no contract line")
     p.add_argument("--sweeps", type=int, default=4)
     p.add_argument("--delta", type=float, default=64.0, help="--only sssp: bucket width")
@@ -634,6 +634,8 @@ def run_only(args):
         return run_only_sssp(args)
     if args.only == "tc":
         return run_only_tc(args)
+    if args.only == "pr_fe":
+        return run_only_fe(args)
     g = make_graph(args.scale)
     off = torch.from_numpy(g.csr_off).cuda()
     idx = torch.from_numpy(g.csr_idx).cuda()
@@ -741,6 +743,47 @@ def run_only_sssp(args):
                       "iter_table": [[d, b, a, e, round(t, 1)] for d, b, a, e, t in
                                      zip(stats[-1]["direction"], stats[-1]["bucket"], stats[-1]["active"],
                                          stats[-1]["examined"], stats[-1]["iter_us"])]}), flush=True)
+    return 0
+
+
+def run_only_fe(args):
+    """Frontier-Exploit PageRank on the R-MAT graph of --scale for a range of
+    frontier thresholds and each mode: ms per run, iterations, push/pull split,
+    the a-posteriori L1 error bound; beside it the Jacobi pull PageRank to L1
+    tol 1e-7 on the same graph."""
+    import torch
+
+    import paper_2010_16012_gb300 as gp
+
+    g = make_graph(args.scale)
+    off = torch.from_numpy(g.csr_off).cuda()
+    idx = torch.from_numpy(g.csr_idx).cuda()
+    G = gp.Graph(g.n, off, idx, symmetric=True)
+    x = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    rows = []
+    for eps in (1e-9, 1e-10, 1e-11, 1e-12):
+        for name, mode in (("auto", gp.AUTO), ("pull", gp.PULL), ("push", gp.PUSH)):
+            for _ in range(args.warmup):
+                gp.pagerank_fe(G, mode, 0.85, eps=eps, iters=1000, out=x)
+            ms = []
+            for _ in range(args.steps):
+                _, st = gp.pagerank_fe(G, mode, 0.85, eps=eps, iters=1000, out=x)
+                ms.append(st["ms"])
+            rows.append({"eps": eps, "mode": name, "ms": round(statistics.median(ms), 3),
+                         "iterations": st["iterations"], "pushes": st["pushes"], "pulls": st["pulls"],
+                         "edges_examined": int(sum(st["examined"])), "error_bound_l1": st["error_bound"]})
+    for _ in range(args.warmup):
+        gp.pagerank(G, gp.PULL, 0.85, 300, 1e-7, out=x)
+    ms = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _, st = gp.pagerank(G, gp.PULL, 0.85, 300, 1e-7, out=x)
+        torch.cuda.synchronize()
+        ms.append((time.perf_counter() - t0) * 1e3)
+    jac = {"ms": round(statistics.median(ms), 3), "sweeps": st["iters_done"], "residual_l1": st["residual"],
+           "error_bound_l1": st["residual"] * 0.85 / 0.15}
+    print(json.dumps({"profile_case": "pr_fe", "scale": args.scale, "n": g.n, "m": g.m, "runs": rows,
+                      "jacobi_pull_tol_1e-7": jac}), flush=True)
     return 0
 
 

@@ -163,7 +163,9 @@ typedef struct gp_options {
                                  per vertex and block (0 = off, <= 49152) */
     float sssp_alpha;         /* SSSP GP_AUTO: an iteration pulls when the active vertices'
                                  out-edges times sssp_alpha exceed the unsettled in-edges */
-    int32_t reserved[4];
+    float fe_alpha;           /* Frontier-Exploit PageRank GP_AUTO: an iteration pulls when the
+                                 frontier's out-edges times fe_alpha exceed m */
+    int32_t reserved[3];
 } gp_options;
 
 /* Fill *opt with the built-in defaults. */
@@ -314,6 +316,52 @@ int gp_bfs(const gp_graph *g, int32_t src, int mode, int32_t *level_out, int32_t
  * later levels.  Levels do not depend on the choice. */
 int gp_bfs_directed(const gp_graph *g, int32_t src, const int8_t *dirs, int ndirs, int32_t *level_out,
                     int32_t *parent_out, gp_bfs_stats *stats, void *stream);
+
+/* ------------------------------------------------------------------ Frontier-Exploit PageRank */
+
+#define GP_FE_MAX_ITERS 1024
+
+typedef struct gp_fe_stats {
+    int32_t iterations;     /* iterations run */
+    int32_t pushes, pulls;  /* iterations by direction */
+    double residual_l1;     /* ||r||_1 of the residuals left (FP64 sum of the FP32 residuals) */
+    double error_bound;     /* residual_l1 / (1 - damping): bound on ||x - x*||_1 for column-substochastic P */
+    int64_t frontier_left;  /* vertices with |r| > eps when the run stopped (0: converged) */
+    float ms;               /* device time of the call by CUDA events */
+    int32_t init_ns;        /* device time before the first iteration */
+    int8_t direction[GP_FE_MAX_ITERS];  /* per iteration: GP_PUSH / GP_PULL */
+    int64_t frontier[GP_FE_MAX_ITERS];  /* frontier size entering each iteration */
+    int64_t examined[GP_FE_MAX_ITERS];  /* edges scattered (push) or gathered (pull) */
+    int32_t iter_ns[GP_FE_MAX_ITERS];   /* device time of each iteration */
+} gp_fe_stats;
+
+/*
+ * PageRank with Frontier-Exploit (Section 5: only a frontier of vertices works
+ * in an iteration) and Generic-Switch (push or pull per iteration), in residual
+ * form: x starts at 0 and the residuals r at (1-d) s; each iteration the
+ * frontier F = {u : |r_u| > eps} moves its residuals into x and sends
+ * d P_vu r_u to the out-neighbours:
+ *     x_u += r_u (u in F);   r'_v = [v not in F] r_v + d sum_{u in F, u->v} P_vu r_u.
+ * Since x + (I - dP)^-1 r equals the PageRank fixed point throughout, a run that
+ * stops with F empty (converged) is within ||r||_1 / (1 - d) of it in L1
+ * (stats->error_bound; P as in gp_pagerank: 1/deg_out, the weights as given, or
+ * normalised weights).
+ *   mode        GP_PUSH: F scatters over out-edges with FP32 atomics;
+ *               GP_PULL: every vertex gathers over its in-edges from F (owner
+ *               writes, no atomics);
+ *               GP_AUTO: per iteration, pull when F's out-edges times fe_alpha
+ *               exceed m, else push.
+ *   eps         frontier threshold on |r_u| (>= 0); eps < 0 keeps every vertex in
+ *               the frontier: `iters` Jacobi sweeps from x = 0.
+ *   iters       iteration cap.
+ *   dirs, ndirs NULL, or the direction of each iteration (dirs[ndirs-1] after).
+ *   personalization  float[n] "any" or NULL (uniform 1/n).
+ *   ranks_out   float[n] "any": x.
+ * Waits for completion.  GP_ERR_NOT_CONVERGED (ranks written) when the cap is
+ * reached with a non-empty frontier; GP_ERR_INVALID for bad arguments.
+ */
+int gp_pagerank_fe(const gp_graph *g, int mode, float damping, double eps, int iters, const int8_t *dirs, int ndirs,
+                   const float *personalization, float *ranks_out, gp_fe_stats *stats, void *stream);
 
 /* ------------------------------------------------------------------ shortest paths */
 

@@ -43,8 +43,8 @@ class gp_options(ctypes.Structure):
                 ("poll_interval", ctypes.c_int32), ("pr_auto_mode", ctypes.c_int32),
                 ("bfs_alpha", ctypes.c_float), ("bfs_beta", ctypes.c_float),
                 ("push_fp64_accum", ctypes.c_int32), ("pull_hot_slots", ctypes.c_int32),
-                ("push_hot_slots", ctypes.c_int32), ("sssp_alpha", ctypes.c_float),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("push_hot_slots", ctypes.c_int32), ("sssp_alpha", ctypes.c_float), ("fe_alpha", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class gp_graph_info(ctypes.Structure):
@@ -78,6 +78,17 @@ class gp_sssp_stats(ctypes.Structure):
                 ("ms", ctypes.c_float), ("init_ns", ctypes.c_int32), ("direction", ctypes.c_int8 * SSSP_MAX_ITERS),
                 ("bucket", ctypes.c_int64 * SSSP_MAX_ITERS), ("active", ctypes.c_int64 * SSSP_MAX_ITERS),
                 ("examined", ctypes.c_int64 * SSSP_MAX_ITERS), ("iter_ns", ctypes.c_int32 * SSSP_MAX_ITERS)]
+
+
+FE_MAX_ITERS = 1024
+
+
+class gp_fe_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("pushes", ctypes.c_int32), ("pulls", ctypes.c_int32),
+                ("residual_l1", ctypes.c_double), ("error_bound", ctypes.c_double),
+                ("frontier_left", ctypes.c_int64), ("ms", ctypes.c_float), ("init_ns", ctypes.c_int32),
+                ("direction", ctypes.c_int8 * FE_MAX_ITERS), ("frontier", ctypes.c_int64 * FE_MAX_ITERS),
+                ("examined", ctypes.c_int64 * FE_MAX_ITERS), ("iter_ns", ctypes.c_int32 * FE_MAX_ITERS)]
 
 
 class gp_tc_stats(ctypes.Structure):
@@ -125,6 +136,8 @@ SIGNATURES = [
                                        _VP]),
     ("gp_sssp", ctypes.c_int, [_VP, _I32, _F, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP,
                                ctypes.POINTER(gp_sssp_stats), _VP]),
+    ("gp_pagerank_fe", ctypes.c_int, [_VP, ctypes.c_int, _F, _D, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP,
+                                      ctypes.POINTER(gp_fe_stats), _VP]),
     ("gp_triangles", ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.POINTER(gp_tc_stats), _VP]),
     ("gp_batch_create", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _VP]),
     ("gp_batch_free", ctypes.c_int, [_VP]),
@@ -422,6 +435,26 @@ def sssp(g: Graph, src: int, delta: float, mode=AUTO, dist=None, pred=None, want
     return dist, pred, stats
 
 
+def pagerank_fe(g: Graph, mode=AUTO, damping=0.85, eps=1e-9, iters=1000, personalization=None, out=None, dirs=None,
+                stream=None, raise_not_converged=False):
+    """gp_pagerank_fe.  Returns (ranks, stats dict)."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    st = gp_fe_stats()
+    d = None if dirs is None else np.ascontiguousarray(np.asarray(dirs, dtype=np.int8))
+    allow = () if raise_not_converged else (ERR_NOT_CONVERGED,)
+    _check(load().gp_pagerank_fe(g.handle, int(mode), float(damping), float(eps), int(iters), _ptr(d),
+                                 0 if d is None else int(d.shape[0]), _ptr(personalization), _ptr(out),
+                                 ctypes.byref(st), _stream_ptr(stream)), "gp_pagerank_fe", allow)
+    L = min(st.iterations, FE_MAX_ITERS)
+    return out, {"iterations": st.iterations, "pushes": st.pushes, "pulls": st.pulls,
+                 "residual_l1": st.residual_l1, "error_bound": st.error_bound, "frontier_left": st.frontier_left,
+                 "ms": st.ms, "init_us": st.init_ns / 1e3, "direction": list(st.direction[:L]),
+                 "frontier": list(st.frontier[:L]), "examined": list(st.examined[:L]),
+                 "iter_us": [x / 1e3 for x in st.iter_ns[:L]]}
+
+
 def triangles(g: Graph, mode=PULL, out=None, stream=None):
     """gp_triangles.  Returns (per-vertex counts int64, total, stats dict)."""
     torch = _torch()
@@ -487,7 +520,8 @@ class Batch:
 
 
 OPTION_FIELDS = ["pull_light_max", "push_light_max", "chunk_edges", "blocks_per_sm", "poll_interval", "pr_auto_mode",
-                 "bfs_alpha", "bfs_beta", "push_fp64_accum", "pull_hot_slots", "push_hot_slots", "sssp_alpha"]
+                 "bfs_alpha", "bfs_beta", "push_fp64_accum", "pull_hot_slots", "push_hot_slots", "sssp_alpha",
+                 "fe_alpha"]
 
 
 def options_dict(o: gp_options) -> dict:

@@ -170,6 +170,7 @@ struct BfsWork {
 }  // namespace gp
 
 struct gp_sssp_work;  // shortest-path workspace (sssp.cu)
+struct gp_fe_work;    // Frontier-Exploit PageRank workspace (pr_fe.cu)
 
 struct gp_graph {
     int device = 0;
@@ -189,6 +190,7 @@ struct gp_graph {
     gp::PrWork pr;
     gp::BfsWork bfs;
     gp_sssp_work *sssp = nullptr;
+    gp_fe_work *fe = nullptr;
     gp::Arena mem;          // copies of the arrays and degree data
     cudaStream_t home = nullptr;
 };
