@@ -338,7 +338,9 @@ typedef struct gp_fe_stats {
 /*
  * PageRank with Frontier-Exploit (Section 5: only a frontier of vertices works
  * in an iteration) and Generic-Switch (push or pull per iteration), in residual
- * form: x starts at 0 and the residuals r at (1-d) s; each iteration the
+ * form: x starts at s (1/n uniform) and the residuals r at (1-d) s + d P x - x,
+ * the change one PageRank sweep would make (one pull sweep at the start); each
+ * iteration the
  * frontier F = {u : |r_u| > eps} moves its residuals into x and sends
  * d P_vu r_u to the out-neighbours:
  *     x_u += r_u (u in F);   r'_v = [v not in F] r_v + d sum_{u in F, u->v} P_vu r_u.
@@ -352,7 +354,7 @@ typedef struct gp_fe_stats {
  *               GP_AUTO: per iteration, pull when F's out-edges times fe_alpha
  *               exceed m, else push.
  *   eps         frontier threshold on |r_u| (>= 0); eps < 0 keeps every vertex in
- *               the frontier: `iters` Jacobi sweeps from x = 0.
+ *               the frontier: k iterations give the k-th PageRank sweep from s.
  *   iters       iteration cap.
  *   dirs, ndirs NULL, or the direction of each iteration (dirs[ndirs-1] after).
  *   personalization  float[n] "any" or NULL (uniform 1/n).

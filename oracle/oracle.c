@@ -529,19 +529,21 @@ int64_t or_sssp_delta(const or_graph *g, int32_t r, double delta, const int8_t *
 
 /*
  * PageRank by propagating pending changes (residuals) from a frontier only.
- * State: ranks x (start 0) and residuals r (start (1-d) s).  Iteration k: the
- * frontier is F = {u : |r_u| > eps}; every u in F moves its residual into its
- * rank (x_u += r_u) and sends d * P_vu * r_u to each out-neighbour v, all from
- * the residuals at the iteration's start (Jacobi):
+ * State: ranks x and residuals r, starting at x = s (1/n when s is NULL: the
+ * usual start of the iteration) and r = (1-d) s + d P x - x, the change one
+ * PageRank sweep would make.  Iteration k: the frontier is F = {u : |r_u| >
+ * eps}; every u in F moves its residual into its rank (x_u += r_u) and sends
+ * d * P_vu * r_u to each out-neighbour v, all from the residuals at the
+ * iteration's start (Jacobi):
  *     r'_v = [v not in F] r_v + d * sum_{u in F, (u->v)} P_vu r_u.
- * In exact arithmetic x + (I - dP)^-1 r stays equal to the fixed point x*, so
- * on termination (F empty, every |r_u| <= eps) ||x - x*||_1 <= ||r||_1 / (1-d)
- * for a column-substochastic P.  Iteration i uses dirs[min(i, ndirs-1)] (0
- * push: F's vertices scatter over out-edges; 1 pull: every v gathers over
- * in-edges from F) -- the same sums in another order.  With eps < 0 every
- * vertex stays in F: the Jacobi iteration from x = 0.  Runs until F is empty or
- * `iters` iterations; s (nullable) as in or_pagerank.  Returns the iterations
- * done; r_out (nullable) receives the final residuals.
+ * x + (I - dP)^-1 r stays equal to the fixed point x* (it does at the start),
+ * so on termination (F empty, every |r_u| <= eps) ||x - x*||_1 <= ||r||_1 /
+ * (1 - d ||P||_1).  Iteration i uses dirs[min(i, ndirs-1)] (0 push: F's
+ * vertices scatter over out-edges; 1 pull: every v gathers over in-edges from
+ * F) -- the same sums in another order.  With eps < 0 every vertex stays in F:
+ * k iterations give the iterate of k Jacobi sweeps from s.  Runs until F
+ * is empty or `iters` iterations.  Returns the iterations done; r_out
+ * (nullable) receives the final residuals.
  */
 int or_pagerank_fe(const or_graph *g, double d, double eps, int iters, const double *s, const int8_t *dirs, int ndirs,
                    double *x, double *r_out) {
@@ -549,9 +551,14 @@ int or_pagerank_fe(const or_graph *g, double d, double eps, int iters, const dou
     double *r = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
     double *rn = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
     char *act = (char *)malloc((size_t)(n > 0 ? n : 1));
-    for (int64_t v = 0; v < n; ++v) {
-        x[v] = 0.0;
-        r[v] = (1.0 - d) * (s ? s[v] : 1.0 / (double)n);
+    for (int64_t v = 0; v < n; ++v) x[v] = s ? s[v] : 1.0 / (double)n;
+    for (int64_t v = 0; v < n; ++v) { /* r = (1-d) s + d P x - x */
+        double acc = 0.0;
+        for (int64_t j = g->in_off[v]; j < g->in_off[v + 1]; ++j) {
+            const int32_t u = g->in_idx[j];
+            acc += or_P(g, g->in_eid[j], u) * x[u];
+        }
+        r[v] = (1.0 - d) * (s ? s[v] : 1.0 / (double)n) + d * acc - x[v];
     }
     int k = 0;
     while (k < iters) {

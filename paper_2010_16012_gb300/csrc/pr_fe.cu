@@ -3,7 +3,8 @@
 // iteration (Generic-Switch), the whole run in one persistent cooperative
 // launch.
 //
-// Residual form: ranks x start at 0, residuals r at (1-d) s.  Iteration k's
+// Residual form: ranks x start at s (1/n uniform), residuals r at (1-d) s +
+// d P x - x, the change one PageRank sweep would make.  Iteration k's
 // frontier is F = {u : |r_u| > eps}; each u in F moves its residual into x_u
 // and sends d * P_vu * r_u to its out-neighbours, all from the residuals at the
 // iteration's start:  r'_v = [v not in F] r_v + d * sum_{u in F, u->v} P_vu r_u.
@@ -265,22 +266,39 @@ __global__ void __launch_bounds__(FE_THREADS) k_pr_fe(FeRun R) {
             atomicAdd(&nx->res, res);
         }
     };
-    // initial state: x = 0, r = (1-d) s, frontier {|r| > eps}
+    // initial state: x = s (1/n when uniform), r = (1-d) s + d P x - x (the
+    // change one PageRank sweep would make), frontier {|r| > eps}
     for (int64_t i = gthread; i < 3 * CW; i += nthreads) ((unsigned long long *)R.ctr)[i] = 0;
     for (int64_t i = gthread; i < nwords; i += nthreads) {
         R.act[1][i] = 0u;
         R.act[2][i] = 0u;
     }
+    for (int64_t v = gthread; v < n; v += nthreads) {
+        const float xv = R.s ? R.s[v] : 1.f / (float)n;
+        R.x[v] = xv;
+        R.acc[v] = 0.0;
+        R.c[1][v] = xv * R.inv_deg[v];
+    }
+    if (!grid_sync(R.sync, gridDim.x)) return;
+    {
+        unsigned long long ex0 = 0;
+        fe_pull(R, R.c[1], ex0);  // (P x)_v into acc (light) and the chunk sums (heavy)
+    }
+    if (!grid_sync(R.sync, gridDim.x)) return;
     {
         unsigned long long nf = 0, mf = 0;
-        for (int64_t base = (int64_t)(gthread >> 5) * 32; base < n; base += (nthreads >> 5) * 32) {
+        for (int64_t base = (gthread >> 5) * 32; base < n; base += (nthreads >> 5) * 32) {
             const int64_t v = base + lane;
             bool inf = false;
             if (v < n) {
-                const float r0 = (1.f - R.d) * (R.s ? R.s[v] : 1.f / (float)n);
-                R.x[v] = 0.f;
-                R.r[v] = r0;
+                float a = f64_to_f32_rn(R.acc[v]);
                 R.acc[v] = 0.0;
+                const int32_t rk = R.pull_rank[v];
+                if (rk >= 0)
+                    for (int64_t j = R.pull_cstart[rk]; j < R.pull_cstart[rk + 1]; ++j) a += R.part[j];
+                const float sv = R.s ? R.s[v] : 1.f / (float)n;
+                const float r0 = (1.f - R.d) * sv + R.d * a - R.x[v];
+                R.r[v] = r0;
                 inf = R.eps < 0.f ? true : fabsf(r0) > R.eps;
                 R.c[0][v] = inf ? R.d * r0 * R.inv_deg[v] : 0.f;
                 if (inf) {
@@ -293,7 +311,6 @@ __global__ void __launch_bounds__(FE_THREADS) k_pr_fe(FeRun R) {
         }
         nf = block_sum(nf, sm);
         mf = block_sum(mf, sm);
-        if (!grid_sync(R.sync, gridDim.x)) return;  // counters zeroed before they are added to
         if (threadIdx.x == 0) {
             if (nf) atomicAdd(&R.ctr[0].nf, nf);
             if (mf) atomicAdd(&R.ctr[0].mf, mf);

@@ -535,16 +535,22 @@ def test_triangles_push_equals_pull_and_threads():
 
 # ------------------------------------------------------------------ Frontier-Exploit PageRank (residual form)
 
-def test_fe_pagerank_all_active_is_jacobi_from_zero():
-    """eps < 0 keeps every vertex in the frontier: k iterations are k Jacobi
-    sweeps from x = 0 (the plain PageRank iteration, pinned above)."""
+def test_fe_pagerank_all_active_is_jacobi():
+    """eps < 0 keeps every vertex in the frontier: k iterations give the iterate
+    of k Jacobi sweeps from the uniform start (the plain PageRank iteration,
+    pinned above), and from s when personalised."""
     g = gg.rmat(9, 8, seed=30, symmetrize=False)
     G = og(g)
-    for k in (1, 2, 7, 20):
+    s = np.random.default_rng(3).uniform(0.1, 1.0, size=g.n)
+    s /= s.sum()
+    for k in (0, 1, 2, 7, 20):
         for dirs in ([0], [1], [0, 1]):
             x, _, it = G.pagerank_fe(0.85, -1.0, iters=k, dirs=dirs)
-            ref, _, _, _ = G.pagerank(oracle.PULL, 0.85, iters=k, x0=np.zeros(g.n))
+            ref, _, _, _ = G.pagerank(oracle.PULL, 0.85, iters=k) if k else (np.full(g.n, 1.0 / g.n), 0, 0, 0)
             assert it == k and np.abs(x - ref).max() < 1e-15
+            x, _, _ = G.pagerank_fe(0.85, -1.0, iters=k, dirs=dirs, personalization=s)
+            ref = G.pagerank(oracle.PULL, 0.85, iters=k, personalization=s, x0=s)[0] if k else s
+            assert np.abs(x - ref).max() < 1e-15
 
 
 @pytest.mark.parametrize("seed", range(6))

@@ -2,8 +2,8 @@
 
 Tolerances follow from the arithmetic of the residual form:
 - eps < 0 keeps every vertex in the frontier, so k iterations are k Jacobi
-  sweeps from x = 0: max-abs 1e-6 and L1 1e-5 against the oracle, as for
-  PageRank itself;
+  sweeps from the uniform start: max-abs 1e-6 and L1 1e-5 against the oracle,
+  as for PageRank itself;
 - a converged run (empty frontier) is within its own a-posteriori bound
   ||r||_1 / (1 - d) of the FP64 fixed point, plus FP32 rounding (L1 1e-5);
 - against the oracle's run of the same algorithm: within the sum of both
@@ -96,7 +96,7 @@ def test_fe_forced_directions_and_shrinking_frontier(gp):
         assert np.abs(np_(x) - xs).sum() <= st["error_bound"] + ROUND_L1
     x, st = gp.pagerank_fe(G, gp.AUTO, 0.85, eps=1e-9, iters=1000)
     fr = st["frontier"]
-    assert fr[0] == g.n and fr[-1] < fr[0] / 4  # the frontier thins out
+    assert fr[0] > g.n / 2 and fr[-1] < fr[0] / 4  # the frontier thins out
     assert st["pushes"] > 0 and st["pulls"] > 0  # the switch used both directions
 
 
