@@ -68,6 +68,8 @@ def _get():
             lib.or_sssp_delta.argtypes = [vp, c.c_int32, c.c_double, vp, c.c_int, vp, c.POINTER(c.c_int64)]
             lib.or_pagerank_fe.restype = c.c_int
             lib.or_pagerank_fe.argtypes = [vp, c.c_double, c.c_double, c.c_int, vp, vp, c.c_int, vp, vp]
+            lib.or_bc.restype = c.c_int
+            lib.or_bc.argtypes = [vp, vp, c.c_int64, vp]
             lib.or_triangles.restype = c.c_int64
             lib.or_triangles.argtypes = [vp, c.c_int, vp, c.c_int]
             lib.or_max_threads.restype = c.c_int
@@ -191,6 +193,14 @@ class OracleGraph:
         k = self._lib.or_pagerank_fe(self._h, float(damping), float(eps), int(iters), _ptr(s), _ptr(d),
                                      int(d.shape[0]), _ptr(x), _ptr(r))
         return x, r, int(k)
+
+    # ------------------------------------------------------------ betweenness centrality
+    def bc(self, sources):
+        """Brandes betweenness centrality summed over `sources` (FP64)."""
+        src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32))
+        out = np.empty(self.n, dtype=np.float64)
+        self._lib.or_bc(self._h, _ptr(src), int(src.shape[0]), _ptr(out))
+        return out
 
     # ------------------------------------------------------------ triangles
     def triangles(self, variant: int = PULL, nthreads: int = 1):

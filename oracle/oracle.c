@@ -35,6 +35,9 @@
  *   - Frontier-Exploit PageRank (Section 5's Frontier-Exploit applied to the
  *     PageRank of Section 3.1): only vertices whose pending change exceeds
  *     eps propagate it in an iteration (residual form, below).
+ *   - Betweenness centrality (the Brandes scheme of the Section 3 listing):
+ *     per source a BFS counting shortest-path multiplicities, then partial
+ *     centralities accumulated back over the shortest-path DAG.
  *
  * Readings of the paper where it is silent or ambiguous (each is a choice the
  * CUDA path makes identically):
@@ -598,6 +601,63 @@ int or_pagerank_fe(const or_graph *g, double d, double eps, int iters, const dou
     free(rn);
     free(act);
     return k;
+}
+
+/* ------------------------------------------------------------------ betweenness centrality */
+
+/*
+ * Betweenness centrality over the given sources (Brandes; the BC listing of
+ * Section 3): for each source s, a FIFO BFS over out-edges records each
+ * vertex's distance and multiplicity sigma (number of shortest paths from s),
+ * the multiplicity of v being the sum of its predecessors' (in-neighbours one
+ * level closer); then, in order of decreasing distance, each vertex's partial
+ * centrality delta[u] = sum over its successors w (out-neighbours one level
+ * further) of sigma[u] / sigma[w] * (1 + delta[w]); bc[u] += delta[u] for
+ * u != s.  FP64.  bc (n) is overwritten.  Returns 0.
+ */
+int or_bc(const or_graph *g, const int32_t *sources, int64_t nsrc, double *bc) {
+    const int64_t n = g->n;
+    int64_t *dist = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    double *sigma = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    double *delta = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    int32_t *order = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    for (int64_t v = 0; v < n; ++v) bc[v] = 0.0;
+    for (int64_t k = 0; k < nsrc; ++k) {
+        const int32_t src = sources[k];
+        for (int64_t v = 0; v < n; ++v) {
+            dist[v] = -1;
+            sigma[v] = 0.0;
+            delta[v] = 0.0;
+        }
+        dist[src] = 0;
+        sigma[src] = 1.0;
+        int64_t head = 0, tail = 0;
+        order[tail++] = src;
+        while (head < tail) { /* order doubles as the FIFO queue: vertices by distance */
+            const int32_t u = order[head++];
+            for (int64_t j = g->out_off[u]; j < g->out_off[u + 1]; ++j) {
+                const int32_t w = g->out_idx[j];
+                if (dist[w] < 0) {
+                    dist[w] = dist[u] + 1;
+                    order[tail++] = w;
+                }
+                if (dist[w] == dist[u] + 1) sigma[w] += sigma[u];
+            }
+        }
+        for (int64_t i = tail - 1; i >= 0; --i) {
+            const int32_t u = order[i];
+            for (int64_t j = g->out_off[u]; j < g->out_off[u + 1]; ++j) {
+                const int32_t w = g->out_idx[j];
+                if (dist[w] == dist[u] + 1) delta[u] += sigma[u] / sigma[w] * (1.0 + delta[w]);
+            }
+            if (u != src) bc[u] += delta[u];
+        }
+    }
+    free(dist);
+    free(sigma);
+    free(delta);
+    free(order);
+    return 0;
 }
 
 /* ------------------------------------------------------------------ triangle counting */

@@ -594,3 +594,56 @@ def test_fe_pagerank_frontier_shrinks():
     ref, _, _, _ = G.pagerank(oracle.PULL, 0.85, iters=100000, tol=1e-15)
     assert np.abs(r).max() <= 1e-9
     assert np.abs(x - ref).sum() <= np.abs(r).sum() / 0.15 * (1 + 1e-12) + 1e-12
+
+
+# ------------------------------------------------------------------ betweenness centrality (Brandes, Section 3 listing)
+
+def brute_bc(n, u, v, sources):
+    """sum over s in sources, t != s, v not in {s, t} of sigma_st(v) / sigma_st,
+    with distances and path counts from repeated matrix products (unit
+    weights): sigma_st(v) = sigma_sv sigma_vt when d(s,v) + d(v,t) = d(s,t)."""
+    A = np.zeros((n, n), dtype=np.int64)
+    A[u, v] = 1
+    np.fill_diagonal(A, 0)
+    D = np.full((n, n), -1, dtype=np.int64)
+    S = np.zeros((n, n), dtype=np.float64)
+    np.fill_diagonal(D, 0)
+    np.fill_diagonal(S, 1.0)
+    P = np.eye(n, dtype=np.float64)  # number of walks of length k
+    for k in range(1, n):
+        P = P @ A
+        new = (D < 0) & (P > 0)
+        D[new] = k
+        S[new] = P[new]  # first length with a walk: those walks are the shortest paths
+    bc = np.zeros(n)
+    for s in sources:
+        for t in range(n):
+            if t == s or D[s, t] < 0:
+                continue
+            for w in range(n):
+                if w in (s, t) or D[s, w] < 0 or D[w, t] < 0:
+                    continue
+                if D[s, w] + D[w, t] == D[s, t]:
+                    bc[w] += S[s, w] * S[w, t] / S[s, t]
+    return bc
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_bc_matches_path_counting(seed):
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(3, 13))
+    g = gg.random_small(n, float(rng.uniform(0.15, 0.6)), seed=900 + seed, directed=bool(seed % 2))
+    src, dst = g.edges()
+    sources = rng.choice(n, size=int(rng.integers(1, n + 1)), replace=False)
+    np.testing.assert_allclose(og(g).bc(sources), brute_bc(n, src, dst, sources), rtol=1e-12, atol=1e-12)
+
+
+def test_bc_closed_forms():
+    n = 9  # undirected path, all sources: vertex i lies on 2 i (n-1-i) ordered shortest paths
+    bc = og(gg.path(n)).bc(np.arange(n))
+    np.testing.assert_allclose(bc, [2 * i * (n - 1 - i) for i in range(n)], atol=1e-12)
+    k = 7  # star: the hub is on every path between two leaves, (k)(k-1) ordered pairs
+    bc = og(gg.star(k)).bc(np.arange(k + 1))
+    assert bc[0] == k * (k - 1) and not bc[1:].any()
+    bc = og(gg.complete(6)).bc(np.arange(6))  # complete graph: no vertex is between two others
+    assert not bc.any()
