@@ -165,7 +165,9 @@ typedef struct gp_options {
                                  out-edges times sssp_alpha exceed the unsettled in-edges */
     float fe_alpha;           /* Frontier-Exploit PageRank GP_AUTO: an iteration pulls when the
                                  frontier's out-edges times fe_alpha exceed m */
-    int32_t reserved[3];
+    float bc_alpha;           /* betweenness centrality GP_AUTO: a step pulls when the push side's
+                                 edges times bc_alpha exceed the pull side's */
+    int32_t reserved[2];
 } gp_options;
 
 /* Fill *opt with the built-in defaults. */
@@ -398,7 +400,7 @@ typedef struct gp_sssp_stats {
  *               minimum over their in-edges from active vertices; owner-only
  *               writes, heavy in-lists combined by atomicMin over chunks);
  *               GP_AUTO: per iteration, pull when the active vertices'
- *               out-edges times bfs_alpha exceed the in-edges of the unsettled
+ *               out-edges times sssp_alpha exceed the in-edges of the unsettled
  *               vertices, else push.
  *   dirs, ndirs NULL, or the direction of each iteration (GP_PUSH/GP_PULL,
  *               dirs[ndirs-1] for all later ones), overriding mode.
@@ -444,6 +446,68 @@ typedef struct gp_tc_stats {
  * output.
  */
 int gp_triangles(const gp_graph *g, int mode, int64_t *tc_out, int64_t *total_out, gp_tc_stats *stats, void *stream);
+
+/* ------------------------------------------------------------------ betweenness centrality */
+
+#define GP_BC_MAX_STEPS 1024
+
+typedef struct gp_bc_stats {
+    int64_t sources;        /* sources processed */
+    int64_t levels;         /* non-empty BFS levels, summed over the sources */
+    int64_t reached;        /* vertices reached (source included), summed over the sources */
+    int64_t edges_examined; /* adjacency entries read by all steps of all sources */
+    int64_t pushes, pulls;  /* steps by direction, all sources, both phases */
+    float ms;               /* device time of the call by CUDA events */
+    int32_t steps;          /* steps of the first source recorded below */
+    int8_t direction[GP_BC_MAX_STEPS]; /* GP_PUSH / GP_PULL */
+    int8_t phase[GP_BC_MAX_STEPS];     /* 0: forward (path counting), 1: backward (dependencies) */
+    int32_t level[GP_BC_MAX_STEPS];    /* forward: the frontier's level l; backward: the level l
+                                          whose dependencies pass to level l-1 */
+    int64_t frontier[GP_BC_MAX_STEPS]; /* vertices of level l */
+    int64_t examined[GP_BC_MAX_STEPS]; /* adjacency entries read by the step */
+    int32_t step_ns[GP_BC_MAX_STEPS];  /* device time of the step (global timer) */
+} gp_bc_stats;
+
+/*
+ * Betweenness centrality by Brandes' scheme (Section 3, the push- and
+ * pull-based BC listing), summed over a set of sources (all n vertices: the
+ * exact centrality; a sample: the usual estimate up to the factor n / k):
+ *   bc(v) = sum over sources s != v of delta_s(v),
+ *   delta_s(v) = sum over t of sigma_st(v) / sigma_st,
+ * sigma_st the number of shortest s-t paths (edges counted with multiplicity,
+ * unit lengths, out-edges followed) and sigma_st(v) those through v.
+ * Per source a forward phase counts shortest paths level by level (sigma of a
+ * vertex = sum over its predecessors one level closer), then a backward phase
+ * from the deepest level up accumulates the dependencies:
+ *   delta(u) = sigma(u) * sum over successors w of (1 + delta(w)) / sigma(w).
+ *   sources     int32[nsources] "any": source vertices (repeats count again).
+ *   mode        GP_PUSH: every step pushes (forward: frontier vertices add
+ *               their path counts to the next level with FP64 atomics, claiming
+ *               new vertices by CAS; backward: each vertex adds its coefficient
+ *               to its predecessors' sums with FP64 atomics);
+ *               GP_PULL: every step pulls (forward: every unvisited vertex sums
+ *               its predecessors' counts, no early exit; backward: each vertex
+ *               sums its successors' coefficients; owner-only writes, heavy
+ *               lists combined over chunks);
+ *               GP_AUTO: per step, pull when the push side's edges times
+ *               bc_alpha exceed the pull side's (forward: out-edges of the
+ *               frontier against in-edges of the unvisited vertices; backward:
+ *               in-edges of level l against out-edges of level l-1).
+ *   dirs, ndirs NULL, or the direction of each step of every source (forward
+ *               steps first, then backward ones; dirs[ndirs-1] for all later
+ *               ones), overriding mode.
+ *   bc_out      double[n] "any": the centralities (overwritten).  FP64
+ *               throughout (path counts, coefficients, sums); results differ
+ *               from a sequential FP64 evaluation only by summation order.
+ *   stats       NULL or filled on return.
+ * Synchronisation as gp_sssp: with stats == NULL and device memory for
+ * sources and bc_out the call only enqueues the work; a grid-barrier timeout is
+ * then reported by the next gp_bc call on the graph.  GP_ERR_INVALID for a
+ * source outside [0, n), nsources < 0, a bad mode or direction;
+ * GP_ERR_TIMEOUT if a grid barrier wait ran out.
+ */
+int gp_bc(const gp_graph *g, const int32_t *sources, int64_t nsources, int mode, const int8_t *dirs, int ndirs,
+          double *bc_out, gp_bc_stats *stats, void *stream);
 
 /* ------------------------------------------------------------------ batches of graphs */
 

@@ -44,7 +44,7 @@ class gp_options(ctypes.Structure):
                 ("bfs_alpha", ctypes.c_float), ("bfs_beta", ctypes.c_float),
                 ("push_fp64_accum", ctypes.c_int32), ("pull_hot_slots", ctypes.c_int32),
                 ("push_hot_slots", ctypes.c_int32), ("sssp_alpha", ctypes.c_float), ("fe_alpha", ctypes.c_float),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("bc_alpha", ctypes.c_float), ("reserved", ctypes.c_int32 * 2)]
 
 
 class gp_graph_info(ctypes.Structure):
@@ -96,6 +96,18 @@ class gp_tc_stats(ctypes.Structure):
                 ("mode_used", ctypes.c_int32)]
 
 
+BC_MAX_STEPS = 1024
+
+
+class gp_bc_stats(ctypes.Structure):
+    _fields_ = [("sources", ctypes.c_int64), ("levels", ctypes.c_int64), ("reached", ctypes.c_int64),
+                ("edges_examined", ctypes.c_int64), ("pushes", ctypes.c_int64), ("pulls", ctypes.c_int64),
+                ("ms", ctypes.c_float), ("steps", ctypes.c_int32), ("direction", ctypes.c_int8 * BC_MAX_STEPS),
+                ("phase", ctypes.c_int8 * BC_MAX_STEPS), ("level", ctypes.c_int32 * BC_MAX_STEPS),
+                ("frontier", ctypes.c_int64 * BC_MAX_STEPS), ("examined", ctypes.c_int64 * BC_MAX_STEPS),
+                ("step_ns", ctypes.c_int32 * BC_MAX_STEPS)]
+
+
 class gp_batch_stats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int32), ("levels", ctypes.c_int32), ("ms", ctypes.c_float),
                 ("blocks", ctypes.c_int32)]
@@ -139,6 +151,8 @@ SIGNATURES = [
     ("gp_pagerank_fe", ctypes.c_int, [_VP, ctypes.c_int, _F, _D, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP,
                                       ctypes.POINTER(gp_fe_stats), _VP]),
     ("gp_triangles", ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.POINTER(gp_tc_stats), _VP]),
+    ("gp_bc", ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_int, _VP, ctypes.c_int, _VP,
+                             ctypes.POINTER(gp_bc_stats), _VP]),
     ("gp_batch_create", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _VP]),
     ("gp_batch_free", ctypes.c_int, [_VP]),
     ("gp_ppr_batched", ctypes.c_int, [_VP, _VP, _F, ctypes.c_int, _D, ctypes.POINTER(_VP), _VP,
@@ -468,6 +482,33 @@ def triangles(g: Graph, mode=PULL, out=None, stream=None):
                               "mode_used": st.mode_used}
 
 
+def bc(g: Graph, sources, mode=AUTO, dirs=None, out=None, want_stats=True, stream=None):
+    """gp_bc: betweenness centrality summed over `sources` (int32, host array or
+    device tensor).  Returns (FP64 centralities, stats dict or None)."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    if hasattr(sources, "data_ptr"):
+        assert sources.dtype == torch.int32 and sources.is_contiguous()
+        src, nsrc = sources, int(sources.numel())
+    else:
+        src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32))
+        nsrc = int(src.shape[0])
+    d = None if dirs is None else np.ascontiguousarray(np.asarray(dirs, dtype=np.int8))
+    st = gp_bc_stats() if want_stats else None
+    _check(load().gp_bc(g.handle, _ptr(src) if nsrc else None, nsrc, int(mode), _ptr(d),
+                        0 if d is None else int(d.shape[0]), _ptr(out), ctypes.byref(st) if st else None,
+                        _stream_ptr(stream)), "gp_bc")
+    if st is None:
+        return out, None
+    L = st.steps
+    return out, {"sources": st.sources, "levels": st.levels, "reached": st.reached,
+                 "edges_examined": st.edges_examined, "pushes": st.pushes, "pulls": st.pulls, "ms": st.ms,
+                 "steps": L, "direction": list(st.direction[:L]), "phase": list(st.phase[:L]),
+                 "level": list(st.level[:L]), "frontier": list(st.frontier[:L]), "examined": list(st.examined[:L]),
+                 "step_us": [x / 1e3 for x in st.step_ns[:L]]}
+
+
 class Batch:
     """gp_batch: batched personalised PageRank and multi-source BFS over several graphs."""
 
@@ -521,7 +562,7 @@ class Batch:
 
 OPTION_FIELDS = ["pull_light_max", "push_light_max", "chunk_edges", "blocks_per_sm", "poll_interval", "pr_auto_mode",
                  "bfs_alpha", "bfs_beta", "push_fp64_accum", "pull_hot_slots", "push_hot_slots", "sssp_alpha",
-                 "fe_alpha"]
+                 "fe_alpha", "bc_alpha"]
 
 
 def options_dict(o: gp_options) -> dict:

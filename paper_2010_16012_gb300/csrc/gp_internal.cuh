@@ -171,6 +171,7 @@ struct BfsWork {
 
 struct gp_sssp_work;  // shortest-path workspace (sssp.cu)
 struct gp_fe_work;    // Frontier-Exploit PageRank workspace (pr_fe.cu)
+struct gp_bc_work;    // betweenness-centrality workspace (bc.cu)
 
 struct gp_graph {
     int device = 0;
@@ -191,6 +192,7 @@ struct gp_graph {
     gp::BfsWork bfs;
     gp_sssp_work *sssp = nullptr;
     gp_fe_work *fe = nullptr;
+    gp_bc_work *bc = nullptr;
     gp::Arena mem;          // copies of the arrays and degree data
     cudaStream_t home = nullptr;
 };

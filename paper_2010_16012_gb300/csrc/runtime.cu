@@ -631,6 +631,7 @@ void release_pr_work(gp_graph *g, cudaStream_t s);
 void release_bfs_work(gp_graph *g, cudaStream_t s);
 void release_sssp_work(gp_graph *g, cudaStream_t s);
 void release_fe_work(gp_graph *g, cudaStream_t s);
+void release_bc_work(gp_graph *g, cudaStream_t s);
 }  // namespace gp
 
 using namespace gp;
@@ -692,6 +693,7 @@ int gp_options_default(gp_options *opt) {
     opt->push_hot_slots = 16384;
     opt->sssp_alpha = 1.0f;
     opt->fe_alpha = 8.0f;
+    opt->bc_alpha = 1.0f;
     return GP_OK;
 }
 
@@ -947,6 +949,7 @@ int gp_graph_free(gp_graph *g) {
     release_bfs_work(g, s);
     release_sssp_work(g, s);
     release_fe_work(g, s);
+    release_bc_work(g, s);
     g->pull_bins.mem.release(s);
     g->push_bins.mem.release(s);
     g->pull_hot.mem.release(s);
@@ -992,7 +995,7 @@ int gp_graph_set_options(gp_graph *g, const gp_options *opt, void *stream) {
     if (opt->pull_light_max < 0 || opt->push_light_max < 0 || opt->pull_light_max > (1 << 20) ||
         opt->push_light_max > (1 << 20) || opt->chunk_edges < 32 || opt->chunk_edges > (1 << 24) ||
         opt->blocks_per_sm < 1 || opt->blocks_per_sm > 32 || opt->poll_interval < 1 ||
-        !(opt->bfs_alpha > 0.f) || !(opt->bfs_beta > 0.f) || !(opt->sssp_alpha > 0.f) || !(opt->fe_alpha > 0.f) || opt->pr_auto_mode < -1 || opt->pr_auto_mode > 1 ||
+        !(opt->bfs_alpha > 0.f) || !(opt->bfs_beta > 0.f) || !(opt->sssp_alpha > 0.f) || !(opt->fe_alpha > 0.f) || !(opt->bc_alpha > 0.f) || opt->pr_auto_mode < -1 || opt->pr_auto_mode > 1 ||
         (opt->push_fp64_accum != 0 && opt->push_fp64_accum != 1) || opt->pull_hot_slots < 0 ||
         opt->pull_hot_slots > 49152 || opt->push_hot_slots < 0 || opt->push_hot_slots > 49152)
         return set_error(GP_ERR_INVALID, "gp_graph_set_options: option out of range");
@@ -1011,7 +1014,7 @@ int gp_graph_set_options(gp_graph *g, const gp_options *opt, void *stream) {
         release_bfs_work(g, s);
         release_sssp_work(g, s);
         release_fe_work(g, s);
-    release_fe_work(g, s);
+        release_bc_work(g, s);
     }
     if (st != GP_OK) {
         g->opt = old;

@@ -69,7 +69,7 @@ def test_struct_layouts_match_c_compiler(tmp_path):
     if not cc:
         pytest.skip("no C compiler")
     structs = {"gp_options": gp.gp_options, "gp_pr_stats": gp.gp_pr_stats, "gp_bfs_stats": gp.gp_bfs_stats,
-               "gp_batch_stats": gp.gp_batch_stats, "gp_tune_result": gp.gp_tune_result, "gp_sssp_stats": gp.gp_sssp_stats, "gp_tc_stats": gp.gp_tc_stats, "gp_fe_stats": gp.gp_fe_stats,
+               "gp_batch_stats": gp.gp_batch_stats, "gp_tune_result": gp.gp_tune_result, "gp_sssp_stats": gp.gp_sssp_stats, "gp_tc_stats": gp.gp_tc_stats, "gp_fe_stats": gp.gp_fe_stats, "gp_bc_stats": gp.gp_bc_stats,
                "gp_kernel_time": gp.gp_kernel_time, "gp_graph_info": gp.gp_graph_info}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gp.h"', "int main(void) {"]
     for name, cls in structs.items():
