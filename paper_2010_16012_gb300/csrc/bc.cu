@@ -41,6 +41,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "gp_internal.cuh"
 
@@ -48,10 +49,13 @@ namespace gp {
 
 constexpr int BC_THREADS = 512;
 constexpr int64_t BC_BATCH = 4096;  // sources per launch
-constexpr int BC_W = 4;             // 32-edge windows (or list loads) in flight per lane
+constexpr int BC_W = 4;             // 32-edge windows of a merged stream in flight per lane
+constexpr int BC_WL = 8;            // list entries in flight per lane (chunks, medium and light lists)
 constexpr int32_t BC_LIGHT = 32;    // lists up to this: merged warp streams
 constexpr int32_t BC_HUB = 1024;    // lists above this: chunks; between: a warp each
-constexpr int32_t BC_CHUNK = 1024;  // edges per hub chunk
+constexpr int32_t BC_CHUNK = 256;   // edges per hub chunk
+constexpr bool BC_LANE_LIGHT = true;  // pull sums over light lists: a lane per vertex (else merged streams)
+constexpr int BC_G = 8;               // lanes per medium list (32 / BC_G lists per warp at once)
 
 struct BcCtr {  // what one step added
     unsigned long long tail;     // vertices appended to the visit order
@@ -211,51 +215,157 @@ __device__ __forceinline__ double stream_gather(const int32_t *__restrict__ idx,
     return acc;
 }
 
+// Sum of val[u] over the entries u of idx[b, e) set in `bits`, one lane over
+// its own list with BC_W loads in flight.
+__device__ __forceinline__ double lane_gather(const int32_t *__restrict__ idx, int64_t b, int64_t e,
+                                              const uint32_t *bits, const double *val) {
+    double s = 0.0;
+    for (int64_t p = b; p < e; p += BC_WL) {
+        int32_t u[BC_WL];
+        uint32_t wd[BC_WL];
+#pragma unroll
+        for (int q = 0; q < BC_WL; ++q) u[q] = p + q < e ? __ldcs(idx + p + q) : -1;
+#pragma unroll
+        for (int q = 0; q < BC_WL; ++q) wd[q] = u[q] >= 0 ? bits[u[q] >> 5] : 0u;
+#pragma unroll
+        for (int q = 0; q < BC_WL; ++q)
+            if ((wd[q] >> (u[q] & 31)) & 1u) s += val[u[q]];
+    }
+    return s;
+}
+
 // Sum of val[u] over the entries u of idx[b, e) set in `bits`, the warp's
 // lanes striding the list (every lane gets the sum).
 __device__ __forceinline__ double list_gather(const int32_t *__restrict__ idx, int64_t b, int64_t e,
                                               const uint32_t *bits, const double *val) {
     double s = 0.0;
-    for (int64_t i0 = b + lane_id(); i0 < e; i0 += 32 * BC_W) {
-        int32_t u[BC_W];
-        uint32_t wd[BC_W];
+    for (int64_t i0 = b + lane_id(); i0 < e; i0 += 32 * BC_WL) {
+        int32_t u[BC_WL];
+        uint32_t wd[BC_WL];
 #pragma unroll
-        for (int q = 0; q < BC_W; ++q) u[q] = i0 + 32 * q < e ? __ldcs(idx + i0 + 32 * q) : -1;
+        for (int q = 0; q < BC_WL; ++q) u[q] = i0 + 32 * q < e ? __ldcs(idx + i0 + 32 * q) : -1;
 #pragma unroll
-        for (int q = 0; q < BC_W; ++q) wd[q] = u[q] >= 0 ? bits[u[q] >> 5] : 0u;
+        for (int q = 0; q < BC_WL; ++q) wd[q] = u[q] >= 0 ? bits[u[q] >> 5] : 0u;
 #pragma unroll
-        for (int q = 0; q < BC_W; ++q)
+        for (int q = 0; q < BC_WL; ++q)
             if ((wd[q] >> (u[q] & 31)) & 1u) s += val[u[q]];
     }
     return warp_sum(s);
 }
 
-// Apply f(u) to the entries of idx[b, e), the warp's lanes striding the list
-// with BC_W loads in flight.
+// Apply f(u) to the entries of idx[b, e), the warp's lanes striding the list:
+// f gets BC_W entries at a time (-1 past the end), all loads issued.
 template <class F>
 __device__ __forceinline__ void list_each(const int32_t *__restrict__ idx, int64_t b, int64_t e, F f) {
-    for (int64_t i0 = b + lane_id(); i0 < e; i0 += 32 * BC_W) {
-        int32_t u[BC_W];
+    for (int64_t i0 = b + lane_id(); i0 < e; i0 += 32 * BC_WL) {
+        int32_t u[BC_WL];
 #pragma unroll
-        for (int q = 0; q < BC_W; ++q) u[q] = i0 + 32 * q < e ? __ldcs(idx + i0 + 32 * q) : -1;
-#pragma unroll
-        for (int q = 0; q < BC_W; ++q)
-            if (u[q] >= 0) f(u[q]);
+        for (int q = 0; q < BC_WL; ++q) u[q] = i0 + 32 * q < e ? __ldcs(idx + i0 + 32 * q) : -1;
+        f(u);
     }
 }
 
-// Forward, push: edge u->w from the frontier (level l, path count su).  The
-// winner of the claim marks w in the next level's bitmap.
-__device__ __forceinline__ void bc_visit(const BcRun &R, int32_t w, int32_t l1, double su, uint32_t *next_bits) {
-    int32_t d = R.dist[w];
-    if (d == -1) {
-        d = atomicCAS(R.dist + w, -1, l1);
-        if (d == -1) {
-            atomicOr(next_bits + (w >> 5), 1u << (w & 31));
-            d = l1;
+// The lanes of a group of G (aligned) stride one list idx[b, e) each: f gets
+// BC_WL entries at a time (-1 past the end), all loads issued.  Groups finish
+// at different times; f must not use warp-wide operations.
+template <int G, class F>
+__device__ __forceinline__ void group_list_each(const int32_t *__restrict__ idx, int64_t b, int64_t e, F f) {
+    for (int64_t i0 = b + (lane_id() & (G - 1)); i0 < e; i0 += G * BC_WL) {
+        int32_t u[BC_WL];
+#pragma unroll
+        for (int q = 0; q < BC_WL; ++q) u[q] = i0 + G * q < e ? __ldcs(idx + i0 + G * q) : -1;
+        f(u);
+    }
+}
+
+// Sum of val[u] over the entries u of idx[b, e) set in `bits`, per group of G
+// lanes (every lane of the group gets its list's sum).
+template <int G>
+__device__ __forceinline__ double group_gather(const int32_t *__restrict__ idx, int64_t b, int64_t e,
+                                               const uint32_t *bits, const double *val) {
+    double s = 0.0;
+    group_list_each<G>(idx, b, e, [&](const int32_t *u) {
+        uint32_t wd[BC_WL];
+#pragma unroll
+        for (int q = 0; q < BC_WL; ++q) wd[q] = u[q] >= 0 ? bits[u[q] >> 5] : 0u;
+#pragma unroll
+        for (int q = 0; q < BC_WL; ++q)
+            if ((wd[q] >> (u[q] & 31)) & 1u) s += val[u[q]];
+    });
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o, G);
+    return s;
+}
+
+// The items [b, e) of a list, 32/G per warp at once: group g of the warp gets
+// item it or -1 (all lanes call work together).
+template <int G, class F>
+__device__ __forceinline__ void warp_groups_each(long long b, long long e, F work) {
+    const int64_t warp = warp_id_global(), nwarps = warps_total();
+    constexpr int NG = 32 / G;
+    const int g = lane_id() / G;
+    for (long long i0 = b + warp * NG; i0 < e; i0 += nwarps * NG) {
+        const long long it = i0 + g;
+        work(it < e ? it : -1);
+    }
+}
+
+// As warp_select_each, the selected items taken 32/G at a time, one per group
+// of G lanes (-1 for a group without one; all lanes call work together).
+template <int G, class P, class F>
+__device__ __forceinline__ void warp_select_groups(int64_t count, P pred, F work) {
+    const int lane = lane_id();
+    const int64_t warp = warp_id_global(), nwarps = warps_total();
+    constexpr int NG = 32 / G;
+    const int g = lane / G;
+    for (int64_t k0 = 0; warp + nwarps * k0 < count; k0 += 32) {
+        const int64_t i = warp + nwarps * (k0 + lane);
+        const bool sel = i < count && pred(i);
+        unsigned bsel = __ballot_sync(FULL, sel);
+        while (bsel) {
+            // the group's pick: the g-th set bit of bsel (none past the count)
+            unsigned x = bsel;
+            for (int r = 0; r < g && x; ++r) x &= x - 1;
+            const int64_t it = x ? warp + nwarps * (k0 + (__ffs(x) - 1)) : -1;
+            work(it);
+            for (int r = 0; r < NG && bsel; ++r) bsel &= bsel - 1;
         }
     }
-    if (d == l1) atomicAdd(R.sigma + w, su);
+}
+
+// Warp-strided selection: lane i of warp w tests item w + nwarps (k + i) with
+// pred (32 tests per load round, consecutive items on different warps); the
+// selected items are then taken one by one by the whole warp.
+template <class P, class F>
+__device__ __forceinline__ void warp_select_each(int64_t count, P pred, F work) {
+    const int lane = lane_id();
+    const int64_t warp = warp_id_global(), nwarps = warps_total();
+    for (int64_t k0 = 0; warp + nwarps * k0 < count; k0 += 32) {
+        const int64_t i = warp + nwarps * (k0 + lane);
+        const bool sel = i < count && pred(i);
+        for (unsigned bsel = __ballot_sync(FULL, sel); bsel; bsel &= bsel - 1)
+            work(warp + nwarps * (k0 + (__ffs(bsel) - 1)));
+    }
+}
+
+// Forward, push: edges u->w[q], q < N, from the frontier (level l, path counts
+// su[q]; w[q] = -1: none).  An unvisited w is claimed by a CAS on its level (all of
+// them issued before any result is used); the winner marks it in the next
+// level's bitmap; every w at level l+1 gets su added.
+template <int N>
+__device__ __forceinline__ void bc_visit(const BcRun &R, const int32_t *w, const double *su, int32_t l1,
+                                         uint32_t *next_bits) {
+    int32_t d[N], old[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) d[q] = w[q] >= 0 ? R.dist[w[q]] : -2;
+#pragma unroll
+    for (int q = 0; q < N; ++q) old[q] = d[q] == -1 ? atomicCAS(R.dist + w[q], -1, l1) : d[q];
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        const bool won = d[q] == -1 && old[q] == -1;
+        if (won) atomicOr(next_bits + (w[q] >> 5), 1u << (w[q] & 31));
+        if (won || old[q] == l1) atomicAdd(R.sigma + w[q], su[q]);
+    }
 }
 
 __device__ void bc_fwd_push(const BcRun &R, int32_t l, const BcCum &a, const BcCum &b, BcLocal &c) {
@@ -265,21 +375,34 @@ __device__ void bc_fwd_push(const BcRun &R, int32_t l, const BcCum &a, const BcC
     const uint32_t *fb = R.lbits[l & 3];
     uint32_t *nb = R.lbits[l1 & 3];
     // hubs of the frontier: every hub chunk whose vertex is in Q_l
-    for (int64_t j = warp; j < R.n_hub_out; j += nwarps) {
+    warp_select_each(R.n_hub_out, [&](int64_t j) { return bit_of(fb, R.hub_out[j].v); }, [&](int64_t j) {
         const Chunk ch = R.hub_out[j];
-        if (!bit_of(fb, ch.v)) continue;  // uniform
-        const double su = R.sigma[ch.v];
-        list_each(R.csr_idx, ch.beg, ch.beg + ch.len, [&](int32_t w) { bc_visit(R, w, l1, su, nb); });
+        double su[BC_WL];
+        su[0] = R.sigma[ch.v];
+#pragma unroll
+        for (int q = 1; q < BC_WL; ++q) su[q] = su[0];
+        list_each(R.csr_idx, ch.beg, ch.beg + ch.len, [&](const int32_t *w) { bc_visit<BC_WL>(R, w, su, l1, nb); });
         if (lane == 0) c.examined += (unsigned long long)ch.len;
-    }
-    // medium lists: a warp per vertex
-    for (long long i = a.med_out + warp; i < b.med_out; i += nwarps) {
-        const int32_t u = R.med_out[i];
-        const double su = R.sigma[u];
-        const int64_t eb = R.csr_off[u], ee = R.csr_off[u + 1];
-        list_each(R.csr_idx, eb, ee, [&](int32_t w) { bc_visit(R, w, l1, su, nb); });
-        if (lane == 0) c.examined += (unsigned long long)(ee - eb);
-    }
+    });
+    // medium lists: BC_G lanes per vertex when there are enough of them, else a warp each
+    auto med_push = [&](auto gsz) {
+        constexpr int G = decltype(gsz)::value;
+        warp_groups_each<G>(a.med_out, b.med_out, [&](long long i) {
+            if (i < 0) return;
+            const int32_t u = R.med_out[i];
+            double su[BC_WL];
+            su[0] = R.sigma[u];
+#pragma unroll
+            for (int q = 1; q < BC_WL; ++q) su[q] = su[0];
+            const int64_t eb = R.csr_off[u], ee = R.csr_off[u + 1];
+            group_list_each<G>(R.csr_idx, eb, ee, [&](const int32_t *w) { bc_visit<BC_WL>(R, w, su, l1, nb); });
+            if ((lane & (G - 1)) == 0) c.examined += (unsigned long long)(ee - eb);
+        });
+    };
+    if (b.med_out - a.med_out >= (32 / BC_G) * nwarps)
+        med_push(std::integral_constant<int, BC_G>());
+    else
+        med_push(std::integral_constant<int, 32>());
     // light lists: 32 queue entries per warp, their out-edges as one stream
     for (long long base = a.start + warp * 32; base < b.start; base += nwarps * 32) {
         const long long qi = base + lane;
@@ -299,9 +422,7 @@ __device__ void bc_fwd_push(const BcRun &R, int32_t l, const BcCum &a, const BcC
             double s[BC_W];
 #pragma unroll
             for (int q = 0; q < BC_W; ++q) s[q] = __shfl_sync(FULL, su, own[q]);
-#pragma unroll
-            for (int q = 0; q < BC_W; ++q)
-                if (w[q] >= 0) bc_visit(R, w[q], l1, s[q], nb);
+            bc_visit<BC_W>(R, w, s, l1, nb);
         });
         if (lane == 0) c.examined += (unsigned long long)E;
     }
@@ -315,9 +436,8 @@ __device__ void bc_fwd_pull(const BcRun &R, int32_t l, BcLocal &c) {
     uint32_t *nb = R.lbits[l1 & 3];
     // the candidate set (unvis) does not change during the step
     // hub in-lists by chunks, sums added atomically, claimed by CAS
-    for (int64_t j = warp; j < R.n_hub_in; j += nwarps) {
+    warp_select_each(R.n_hub_in, [&](int64_t j) { return bit_of(R.unvis, R.hub_in[j].v); }, [&](int64_t j) {
         const Chunk ch = R.hub_in[j];
-        if (!bit_of(R.unvis, ch.v)) continue;  // uniform
         const double s = list_gather(R.csc_idx, ch.beg, ch.beg + ch.len, fb, R.sigma);
         if (lane == 0) {
             c.examined += (unsigned long long)ch.len;
@@ -326,27 +446,25 @@ __device__ void bc_fwd_pull(const BcRun &R, int32_t l, BcLocal &c) {
                 if (atomicCAS(R.dist + ch.v, -1, l1) == -1) atomicOr(nb + (ch.v >> 5), 1u << (ch.v & 31));
             }
         }
-    }
-    // medium in-lists: a warp per vertex
-    for (int64_t i = warp; i < R.n_med_in_all; i += nwarps) {
-        const int32_t v = R.med_in_all[i];
-        if (!bit_of(R.unvis, v)) continue;  // uniform
-        const int64_t eb = R.csc_off[v], ee = R.csc_off[v + 1];
-        const double s = list_gather(R.csc_idx, eb, ee, fb, R.sigma);
-        if (lane == 0) {
+    });
+    // medium in-lists: BC_G lanes per vertex
+    warp_select_groups<BC_G>(R.n_med_in_all, [&](int64_t i) { return bit_of(R.unvis, R.med_in_all[i]); }, [&](int64_t i) {
+        const int32_t v = i >= 0 ? R.med_in_all[i] : 0;
+        const int64_t eb = i >= 0 ? R.csc_off[v] : 0, ee = i >= 0 ? R.csc_off[v + 1] : 0;
+        const double s = group_gather<BC_G>(R.csc_idx, eb, ee, fb, R.sigma);
+        if (i >= 0 && (lane & (BC_G - 1)) == 0) {
             c.examined += (unsigned long long)(ee - eb);
             if (s > 0.0) {
-                R.sigma[v] = s;  // its own warp: the only writer
+                R.sigma[v] = s;  // its own group: the only writer
                 R.dist[v] = l1;
                 atomicOr(nb + (v >> 5), 1u << (v & 31));
             }
         }
-    }
-    // light in-lists: one candidate word (32 vertices) per warp, as one stream
+    });
+    // light in-lists: one candidate word (32 vertices) at a time per warp, as one stream
     const int64_t nwords = (R.n + 31) >> 5;
-    for (int64_t wd = warp; wd < nwords; wd += nwarps) {
+    warp_select_each(nwords, [&](int64_t wd) { return R.unvis[wd] != 0u; }, [&](int64_t wd) {
         const uint32_t word = R.unvis[wd];
-        if (!word) continue;  // uniform
         const int32_t v = (int32_t)(wd * 32 + lane);
         int deg = 0;
         int64_t eb = 0;
@@ -355,7 +473,8 @@ __device__ void bc_fwd_pull(const BcRun &R, int32_t l, BcLocal &c) {
             const int64_t d = R.csc_off[v + 1] - eb;
             deg = d <= BC_LIGHT ? (int)d : 0;
         }
-        const double s = stream_gather(R.csc_idx, eb, deg, fb, R.sigma);
+        const double s = BC_LANE_LIGHT ? lane_gather(R.csc_idx, eb, eb + deg, fb, R.sigma)
+                                       : stream_gather(R.csc_idx, eb, deg, fb, R.sigma);
         c.examined += (unsigned long long)deg;
         const bool take = deg > 0 && s > 0.0;
         if (take) {
@@ -364,7 +483,7 @@ __device__ void bc_fwd_pull(const BcRun &R, int32_t l, BcLocal &c) {
         }
         const unsigned got = __ballot_sync(FULL, take);
         if (lane == 0 && got) atomicOr(nb + wd, got);
-    }
+    });
 }
 
 // After a forward step: append the vertices of the new level's bitmap to the
@@ -420,24 +539,36 @@ __device__ void bc_bwd_push(const BcRun &R, int32_t l, const BcCum &a, const BcC
     const int64_t warp = warp_id_global(), nwarps = warps_total();
     const uint32_t *qb = R.lbits[l & 3];        // Q_l
     const uint32_t *pb = R.lbits[(l - 1) & 3];  // Q_{l-1}
-    auto scatter_to = [&](int32_t u, double cw) {
-        if (bit_of(pb, u)) atomicAdd(R.S + u, cw);
+    auto scatter_to = [&](const int32_t *u, double cw) {  // BC_WL entries of a list, bitmap loads first
+        uint32_t wd[BC_WL];
+#pragma unroll
+        for (int q = 0; q < BC_WL; ++q) wd[q] = u[q] >= 0 ? pb[u[q] >> 5] : 0u;
+#pragma unroll
+        for (int q = 0; q < BC_WL; ++q)
+            if ((wd[q] >> (u[q] & 31)) & 1u) atomicAdd(R.S + u[q], cw);
     };
     if (scatter) {
-        for (int64_t j = warp; j < R.n_hub_in; j += nwarps) {
+        warp_select_each(R.n_hub_in, [&](int64_t j) { return bit_of(qb, R.hub_in[j].v); }, [&](int64_t j) {
             const Chunk ch = R.hub_in[j];
-            if (!bit_of(qb, ch.v)) continue;  // uniform
             const double cw = 1.0 / R.sigma[ch.v] + R.S[ch.v];
-            list_each(R.csc_idx, ch.beg, ch.beg + ch.len, [&](int32_t u) { scatter_to(u, cw); });
+            list_each(R.csc_idx, ch.beg, ch.beg + ch.len, [&](const int32_t *u) { scatter_to(u, cw); });
             if (lane == 0) c.examined += (unsigned long long)ch.len;
-        }
-        for (long long i = a.med_in + warp; i < b.med_in; i += nwarps) {
-            const int32_t w = R.med_in[i];
-            const double cw = 1.0 / R.sigma[w] + R.S[w];
-            const int64_t eb = R.csc_off[w], ee = R.csc_off[w + 1];
-            list_each(R.csc_idx, eb, ee, [&](int32_t u) { scatter_to(u, cw); });
-            if (lane == 0) c.examined += (unsigned long long)(ee - eb);
-        }
+        });
+        auto med_scatter = [&](auto gsz) {
+            constexpr int G = decltype(gsz)::value;
+            warp_groups_each<G>(a.med_in, b.med_in, [&](long long i) {
+                if (i < 0) return;
+                const int32_t w = R.med_in[i];
+                const double cw = 1.0 / R.sigma[w] + R.S[w];
+                const int64_t eb = R.csc_off[w], ee = R.csc_off[w + 1];
+                group_list_each<G>(R.csc_idx, eb, ee, [&](const int32_t *u) { scatter_to(u, cw); });
+                if ((lane & (G - 1)) == 0) c.examined += (unsigned long long)(ee - eb);
+            });
+        };
+        if (b.med_in - a.med_in >= (32 / BC_G) * nwarps)
+            med_scatter(std::integral_constant<int, BC_G>());
+        else
+            med_scatter(std::integral_constant<int, 32>());
     }
     for (long long base = a.start + warp * 32; base < b.start; base += nwarps * 32) {
         const long long qi = base + lane;
@@ -478,24 +609,30 @@ __device__ void bc_bwd_pull(const BcRun &R, int32_t l, const BcCum &p, const BcC
     const int64_t warp = warp_id_global(), nwarps = warps_total();
     const uint32_t *qb = R.lbits[l & 3];        // Q_l
     const uint32_t *pb = R.lbits[(l - 1) & 3];  // Q_{l-1}
-    for (int64_t j = warp; j < R.n_hub_out; j += nwarps) {
+    warp_select_each(R.n_hub_out, [&](int64_t j) { return bit_of(pb, R.hub_out[j].v); }, [&](int64_t j) {
         const Chunk ch = R.hub_out[j];
-        if (!bit_of(pb, ch.v)) continue;  // uniform
         const double s = list_gather(R.csr_idx, ch.beg, ch.beg + ch.len, qb, R.coef);
         if (lane == 0) {
             c.examined += (unsigned long long)ch.len;
             if (s != 0.0) atomicAdd(R.S + ch.v, s);
         }
-    }
-    for (long long i = p.med_out + warp; i < a.med_out; i += nwarps) {
-        const int32_t u = R.med_out[i];
-        const int64_t eb = R.csr_off[u], ee = R.csr_off[u + 1];
-        const double s = list_gather(R.csr_idx, eb, ee, qb, R.coef);
-        if (lane == 0) {
-            c.examined += (unsigned long long)(ee - eb);
-            R.S[u] = s;  // its own warp: the only writer
-        }
-    }
+    });
+    auto med_gather = [&](auto gsz) {
+        constexpr int G = decltype(gsz)::value;
+        warp_groups_each<G>(p.med_out, a.med_out, [&](long long i) {
+            const int32_t u = i >= 0 ? R.med_out[i] : 0;
+            const int64_t eb = i >= 0 ? R.csr_off[u] : 0, ee = i >= 0 ? R.csr_off[u + 1] : 0;
+            const double s = group_gather<G>(R.csr_idx, eb, ee, qb, R.coef);
+            if (i >= 0 && (lane & (G - 1)) == 0) {
+                c.examined += (unsigned long long)(ee - eb);
+                R.S[u] = s;  // its own group: the only writer
+            }
+        });
+    };
+    if (a.med_out - p.med_out >= (32 / BC_G) * nwarps)
+        med_gather(std::integral_constant<int, BC_G>());
+    else
+        med_gather(std::integral_constant<int, 32>());
     for (long long base = p.start + warp * 32; base < a.start; base += nwarps * 32) {
         const long long qi = base + lane;
         int32_t u = -1;
@@ -508,7 +645,8 @@ __device__ void bc_bwd_pull(const BcRun &R, int32_t l, const BcCum &p, const BcC
             if (d <= BC_LIGHT) deg = (int)d;
             else u = -1;  // medium or hub: done above
         }
-        const double s = stream_gather(R.csr_idx, eb, deg, qb, R.coef);
+        const double s = BC_LANE_LIGHT ? lane_gather(R.csr_idx, eb, eb + deg, qb, R.coef)
+                                       : stream_gather(R.csr_idx, eb, deg, qb, R.coef);
         c.examined += (unsigned long long)deg;
         if (u >= 0) R.S[u] = s;  // its own lane: the only writer
     }
