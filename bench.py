@@ -53,7 +53,7 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--quiet", action="store_true")
     p.add_argument("--no-batched", action="store_true")
-    p.add_argument("--only", choices=["pr_pull", "pr_push", "bfs", "batched", "sssp", "tc", "pr_fe"], default=None,
+    p.add_argument("--only", choices=["pr_pull", "pr_push", "bfs", "batched", "sssp", "tc", "pr_fe", "bc"], default=None,
                    help="profiling case: run only this part (fixed --sweeps for PageRank), no contract line")
     p.add_argument("--sweeps", type=int, default=4)
     p.add_argument("--delta", type=float, default=64.0, help="--only sssp: bucket width")
@@ -634,6 +634,8 @@ def run_only(args):
         return run_only_sssp(args)
     if args.only == "tc":
         return run_only_tc(args)
+    if args.only == "bc":
+        return run_only_bc(args)
     if args.only == "pr_fe":
         return run_only_fe(args)
     g = make_graph(args.scale)
@@ -830,6 +832,67 @@ def run_only_tc(args):
                              "ms": round(dt * 1e3, 1), "gteps": round(g.m / dt / 1e9, 4)}
         out["equals_oracle"] = bool(np.array_equal(counts["pull"], ref))
     print(json.dumps({"profile_case": "tc", "scale": args.scale, "n": g.n, "m": g.m, "opts": opts, **out}), flush=True)
+    return 0
+
+
+def run_only_bc(args):
+    """Betweenness centrality (Brandes, push/pull steps) on the R-MAT graph of
+    --scale from 16 sources per run, each mode: ms per source, the traversed
+    edges per second (m times the sources over the time, the usual rate for
+    BC), adjacency entries examined; the first source's step table; the
+    oracle's sequential Brandes timed on two of the sources and compared
+    (unless --no-cpu-baseline)."""
+    import torch
+
+    import paper_2010_16012_gb300 as gp
+
+    g = make_graph(args.scale)
+    G = gp.Graph.from_graphgen(g)
+    opts = {}
+    for kv in args.opt:
+        k, v = kv.split("=")
+        opts[k] = float(v) if k.endswith("_alpha") or k.endswith("_beta") else int(v)
+    if opts:
+        G.set_options(**opts)
+    src = np.ascontiguousarray(pick_sources(g, 16).astype(np.int32))
+    src_dev = torch.from_numpy(src).cuda()
+    bc = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    out = {}
+    res = {}
+    for name, mode in (("auto", gp.AUTO), ("pull", gp.PULL), ("push", gp.PUSH)):
+        for _ in range(args.warmup):
+            gp.bc(G, src_dev, mode, out=bc)
+        ms = []
+        for _ in range(args.steps):
+            _, st = gp.bc(G, src_dev, mode, out=bc)
+            ms.append(st["ms"])
+        t = statistics.median(ms)
+        res[name] = bc.cpu().numpy()
+        out[name] = {"ms": round(t, 3), "ms_per_source": round(t / len(src), 4),
+                     "gteps": round(g.m * len(src) / (t * 1e-3) / 1e9, 2),
+                     "examined_per_source": int(st["edges_examined"] // len(src)),
+                     "pushes": st["pushes"], "pulls": st["pulls"]}
+        if name == "auto":
+            out["steps_first_source"] = [[p, l, d, f, e, round(u, 1)] for p, l, d, f, e, u in
+                                         zip(st["phase"], st["level"], st["direction"], st["frontier"],
+                                             st["examined"], st["step_us"])]
+    ref = res["auto"]
+    out["max_rel_diff_modes"] = float(max(np.max(np.abs(res[k] - ref) / np.maximum(np.abs(ref), 1e-300))
+                                          for k in ("pull", "push")))
+    if not args.no_cpu_baseline:
+        import oracle
+
+        O = oracle.OracleGraph.from_graph(g)
+        t0 = time.perf_counter()
+        r2 = O.bc(src[:2])
+        dt = time.perf_counter() - t0
+        x2, _ = gp.bc(G, src[:2], gp.AUTO)
+        x2 = x2.cpu().numpy()
+        out["cpu_oracle"] = {"kind": "oracle", "what": "sequential Brandes, 2 sources", "cores": 1,
+                             "ms_per_source": round(dt * 1e3 / 2, 1), "gteps": round(g.m * 2 / dt / 1e9, 4)}
+        out["oracle_max_rel_diff"] = float(np.max(np.abs(x2 - r2) / np.maximum(np.abs(r2), 1e-9 * np.abs(r2).max())))
+    print(json.dumps({"profile_case": "bc", "scale": args.scale, "n": g.n, "m": g.m, "sources": len(src),
+                      "opts": opts, **out}), flush=True)
     return 0
 
 

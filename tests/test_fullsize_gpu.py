@@ -109,6 +109,30 @@ def test_rmat22_bfs_auto(gp, rmat22):
         assert np.array_equal(lv, ref), s
 
 
+def test_rmat22_bc(gp, rmat22):
+    """Betweenness centrality on the benchmark graph: two sources against the
+    oracle's Brandes vertex by vertex; the 16 sources of the measured case
+    through the property that holds at any size -- for one source the
+    dependencies sum to the number of interior vertices of its shortest paths,
+    sum over reached t != s of (d(s,t) - 1) (oracle BFS levels)."""
+    g, G, O, srcs, _ = rmat22
+    two = np.ascontiguousarray(srcs[:2].astype(np.int32))
+    x, _ = gp.bc(G, two, gp.AUTO)
+    ref = O.bc(two)
+    x = x.cpu().numpy()
+    assert np.all(np.abs(x - ref) <= 1e-9 * np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max()))
+    sixteen = np.ascontiguousarray(gg.pick_vertices(g, 16, seed=2).astype(np.int32))
+    want = 0
+    for s in sixteen:
+        lv, _ = O.bfs(int(s))
+        want += int(np.maximum(lv[lv > 0] - 1, 0).sum())
+    for mode in (gp.AUTO, gp.PULL, gp.PUSH):
+        x, st = gp.bc(G, sixteen, mode)
+        total = float(x.sum().item())
+        assert abs(total - want) <= 1e-9 * want, (mode, total, want)
+        assert (x.cpu().numpy() >= 0).all()
+
+
 # ---------------------------------------------------------------- Erdos-Renyi 2^24
 
 @pytest.fixture(scope="module")

@@ -647,3 +647,15 @@ def test_bc_closed_forms():
     assert bc[0] == k * (k - 1) and not bc[1:].any()
     bc = og(gg.complete(6)).bc(np.arange(6))  # complete graph: no vertex is between two others
     assert not bc.any()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_bc_dependency_sum_is_path_interior_count(seed):
+    # for one source the dependencies add up to the interior vertices of one shortest path per target:
+    # sum_v delta_s(v) = sum over reached t != s of (d(s, t) - 1)
+    g = gg.rmat(9, 8, seed=40 + seed, symmetrize=bool(seed % 2))
+    O = og(g)
+    for s in gg.pick_vertices(g, 5, seed=seed):
+        lv, _ = O.bfs(int(s))
+        want = np.maximum(lv[lv > 0] - 1, 0).sum()
+        assert abs(O.bc([int(s)]).sum() - want) <= 1e-9 * max(1, want)
