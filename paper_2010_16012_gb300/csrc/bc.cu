@@ -30,13 +30,14 @@
 // counts their degrees; the backward phase rebuilds Q_{l-2}'s bitmap from the
 // order one step ahead and clears the slot of Q_{l+1}.  Three tiers by the
 // degree of the list a step walks, so that no warp gets far more edges than
-// another: light lists (<= BC_LIGHT) are walked 32 vertices per warp as one
-// merged edge stream (four 32-edge windows in flight, per-vertex sums by
-// segmented warp scans); medium lists (<= BC_HUB) one warp per vertex, from
-// per-level lists the compaction writes; hub lists are cut into chunks that
-// every step scans, taking those whose vertex is in the step's set.  Per-step counters are deltas in a
-// ring of three records (the next one zeroed a step ahead); every block keeps
-// the cumulative values.  Per vertex: level (int32), sigma, S and c (FP64), bc
+// another: light lists (<= BC_LIGHT) are summed one lane per vertex (pull) or
+// walked 32 vertices per warp as one merged edge stream (push, four 32-edge
+// windows in flight); medium lists (<= BC_HUB) by groups of BC_G lanes, or a
+// warp each when a level has few of them, from per-level lists the compaction
+// writes; hub lists are cut into chunks that every step scans, taking those
+// whose vertex is in the step's set.  Per-step counters are deltas in a ring of
+// three records (the next one zeroed a step ahead); every block keeps the
+// cumulative values.  Per vertex: level (int32), sigma, S and c (FP64), bc
 // (FP64); all reset for the visited vertices after each source.
 #include <algorithm>
 #include <cmath>
@@ -54,8 +55,8 @@ constexpr int BC_WL = 8;            // list entries in flight per lane (chunks, 
 constexpr int32_t BC_LIGHT = 32;    // lists up to this: merged warp streams
 constexpr int32_t BC_HUB = 1024;    // lists above this: chunks; between: a warp each
 constexpr int32_t BC_CHUNK = 256;   // edges per hub chunk
-constexpr bool BC_LANE_LIGHT = true;  // pull sums over light lists: a lane per vertex (else merged streams)
 constexpr int BC_G = 8;               // lanes per medium list (32 / BC_G lists per warp at once)
+constexpr int BC_HOT = 256;           // backward push: targets summed in shared memory per block
 
 struct BcCtr {  // what one step added
     unsigned long long tail;     // vertices appended to the visit order
@@ -90,6 +91,9 @@ struct BcRun {
     const int32_t *csr_idx, *csc_idx;
     const Chunk *hub_out, *hub_in;  // chunks of the lists above BC_HUB
     int64_t n_hub_out, n_hub_in;
+    const int32_t *csc_enc;         // CSC indices, the BC_HOT largest out-degrees as HOT_BIT | slot
+    const int32_t *hot_id;          // [nhot] vertex of each slot
+    int32_t nhot;
     const int32_t *med_in_all;      // every vertex with a medium in-list
     int64_t n_med_in_all;
     int32_t *dist;
@@ -175,44 +179,6 @@ __device__ __forceinline__ int warp_stream(const int32_t *__restrict__ idx, int6
         f(base, u, own, excl, incl);
     }
     return E;
-}
-
-// Per-vertex sums over a window of 32 edges (lanes in edge order, owners
-// non-decreasing): lane k gets the sum of the values of its own vertex's edges
-// in the window starting at virtual edge wb.
-__device__ __forceinline__ double window_sum(double v, int o, int wb, int excl, int incl, int deg) {
-    const int lane = lane_id();
-    const int oex = __shfl_sync(FULL, excl, o);
-    const int head = max(oex, wb) - wb;  // first lane of this lane's segment
-#pragma unroll
-    for (int st = 1; st < 32; st <<= 1) {
-        const double t = __shfl_up_sync(FULL, v, st);
-        if (lane - st >= head) v += t;
-    }
-    const bool has = deg > 0 && excl < wb + 32 && incl > wb;
-    const int tail = has ? min(incl, wb + 32) - wb - 1 : 0;
-    const double seg = __shfl_sync(FULL, v, tail);
-    return has ? seg : 0.0;
-}
-
-// Sum of val[u] over the neighbours u set in `bits`, for each lane's vertex of a
-// merged edge stream.
-__device__ __forceinline__ double stream_gather(const int32_t *__restrict__ idx, int64_t eb, int deg,
-                                                const uint32_t *bits, const double *val) {
-    double acc = 0.0;
-    warp_stream(idx, eb, deg, [&](int base, const int32_t *u, const int *own, int excl, int incl) {
-        uint32_t wd[BC_W];
-        double v[BC_W];
-#pragma unroll
-        for (int q = 0; q < BC_W; ++q) wd[q] = u[q] >= 0 ? bits[u[q] >> 5] : 0u;
-#pragma unroll
-        for (int q = 0; q < BC_W; ++q) v[q] = ((wd[q] >> (u[q] & 31)) & 1u) ? val[u[q]] : 0.0;
-        const int E = __shfl_sync(FULL, incl, 31);
-#pragma unroll
-        for (int q = 0; q < BC_W; ++q)
-            if (base + 32 * q < E) acc += window_sum(v[q], own[q], base + 32 * q, excl, incl, deg);  // uniform test
-    });
-    return acc;
 }
 
 // Sum of val[u] over the entries u of idx[b, e) set in `bits`, one lane over
@@ -473,8 +439,7 @@ __device__ void bc_fwd_pull(const BcRun &R, int32_t l, BcLocal &c) {
             const int64_t d = R.csc_off[v + 1] - eb;
             deg = d <= BC_LIGHT ? (int)d : 0;
         }
-        const double s = BC_LANE_LIGHT ? lane_gather(R.csc_idx, eb, eb + deg, fb, R.sigma)
-                                       : stream_gather(R.csc_idx, eb, deg, fb, R.sigma);
+        const double s = lane_gather(R.csc_idx, eb, eb + deg, fb, R.sigma);
         c.examined += (unsigned long long)deg;
         const bool take = deg > 0 && s > 0.0;
         if (take) {
@@ -532,26 +497,44 @@ __device__ void bc_compact(const BcRun &R, const uint32_t *bits, BcCtr *nx, cons
 
 // Backward step l: finish the vertices of Q_l (bc += sigma S; c = 1/sigma + S,
 // stored when `store_coef`) and, when `scatter`, add c to S of their
-// in-neighbours in Q_{l-1}.
+// in-neighbours in Q_{l-1}.  The scatter walks the hot-encoded CSC: the targets
+// of largest out-degree (most updated) are summed in the block's shared memory
+// `acc` and added to S once per block at the end, the others with FP64 RED.
 __device__ void bc_bwd_push(const BcRun &R, int32_t l, const BcCum &a, const BcCum &b, bool scatter, bool store_coef,
-                            BcLocal &c) {
+                            double *acc, BcLocal &c) {
     const int lane = lane_id();
     const int64_t warp = warp_id_global(), nwarps = warps_total();
     const uint32_t *qb = R.lbits[l & 3];        // Q_l
     const uint32_t *pb = R.lbits[(l - 1) & 3];  // Q_{l-1}
-    auto scatter_to = [&](const int32_t *u, double cw) {  // BC_WL entries of a list, bitmap loads first
-        uint32_t wd[BC_WL];
+    // N entries u[q] of the encoded CSC (-1: none) receive cw[q] when in Q_{l-1}
+    auto scatter_n = [&](auto nn, const int32_t *u, const double *cw) {
+        constexpr int N = decltype(nn)::value;
+        int32_t v[N];
+        uint32_t wd[N];
 #pragma unroll
-        for (int q = 0; q < BC_WL; ++q) wd[q] = u[q] >= 0 ? pb[u[q] >> 5] : 0u;
+        for (int q = 0; q < N; ++q) v[q] = u[q] < -1 ? R.hot_id[u[q] & 0x7fffffff] : u[q];
 #pragma unroll
-        for (int q = 0; q < BC_WL; ++q)
-            if ((wd[q] >> (u[q] & 31)) & 1u) atomicAdd(R.S + u[q], cw);
+        for (int q = 0; q < N; ++q) wd[q] = v[q] >= 0 ? pb[v[q] >> 5] : 0u;
+#pragma unroll
+        for (int q = 0; q < N; ++q)
+            if ((wd[q] >> (v[q] & 31)) & 1u) {
+                if (u[q] < -1)
+                    atomicAdd(acc + (u[q] & 0x7fffffff), cw[q]);
+                else
+                    atomicAdd(R.S + v[q], cw[q]);
+            }
     };
     if (scatter) {
+        for (int i = threadIdx.x; i < R.nhot; i += blockDim.x) acc[i] = 0.0;
+        __syncthreads();
         warp_select_each(R.n_hub_in, [&](int64_t j) { return bit_of(qb, R.hub_in[j].v); }, [&](int64_t j) {
             const Chunk ch = R.hub_in[j];
-            const double cw = 1.0 / R.sigma[ch.v] + R.S[ch.v];
-            list_each(R.csc_idx, ch.beg, ch.beg + ch.len, [&](const int32_t *u) { scatter_to(u, cw); });
+            double cw[BC_WL];
+            cw[0] = 1.0 / R.sigma[ch.v] + R.S[ch.v];
+#pragma unroll
+            for (int q = 1; q < BC_WL; ++q) cw[q] = cw[0];
+            list_each(R.csc_enc, ch.beg, ch.beg + ch.len,
+                      [&](const int32_t *u) { scatter_n(std::integral_constant<int, BC_WL>(), u, cw); });
             if (lane == 0) c.examined += (unsigned long long)ch.len;
         });
         auto med_scatter = [&](auto gsz) {
@@ -559,9 +542,13 @@ __device__ void bc_bwd_push(const BcRun &R, int32_t l, const BcCum &a, const BcC
             warp_groups_each<G>(a.med_in, b.med_in, [&](long long i) {
                 if (i < 0) return;
                 const int32_t w = R.med_in[i];
-                const double cw = 1.0 / R.sigma[w] + R.S[w];
+                double cw[BC_WL];
+                cw[0] = 1.0 / R.sigma[w] + R.S[w];
+#pragma unroll
+                for (int q = 1; q < BC_WL; ++q) cw[q] = cw[0];
                 const int64_t eb = R.csc_off[w], ee = R.csc_off[w + 1];
-                group_list_each<G>(R.csc_idx, eb, ee, [&](const int32_t *u) { scatter_to(u, cw); });
+                group_list_each<G>(R.csc_enc, eb, ee,
+                                   [&](const int32_t *u) { scatter_n(std::integral_constant<int, BC_WL>(), u, cw); });
                 if ((lane & (G - 1)) == 0) c.examined += (unsigned long long)(ee - eb);
             });
         };
@@ -586,19 +573,18 @@ __device__ void bc_bwd_push(const BcRun &R, int32_t l, const BcCum &a, const BcC
             deg = scatter && d <= BC_LIGHT ? (int)d : 0;
         }
         if (!scatter) continue;  // uniform
-        const int E = warp_stream(R.csc_idx, eb, deg, [&](int, const int32_t *u, const int *own, int, int) {
-            uint32_t wd[BC_W];
+        const int E = warp_stream(R.csc_enc, eb, deg, [&](int, const int32_t *u, const int *own, int, int) {
             double cv[BC_W];
 #pragma unroll
-            for (int q = 0; q < BC_W; ++q) {
-                wd[q] = u[q] >= 0 ? pb[u[q] >> 5] : 0u;
-                cv[q] = __shfl_sync(FULL, cw, own[q]);
-            }
-#pragma unroll
-            for (int q = 0; q < BC_W; ++q)
-                if ((wd[q] >> (u[q] & 31)) & 1u) atomicAdd(R.S + u[q], cv[q]);
+            for (int q = 0; q < BC_W; ++q) cv[q] = __shfl_sync(FULL, cw, own[q]);
+            scatter_n(std::integral_constant<int, BC_W>(), u, cv);
         });
         if (lane == 0) c.examined += (unsigned long long)E;
+    }
+    if (scatter) {  // the block's sums of the hot targets, once per block
+        __syncthreads();
+        for (int i = threadIdx.x; i < R.nhot; i += blockDim.x)
+            if (acc[i] != 0.0) atomicAdd(R.S + R.hot_id[i], acc[i]);
     }
 }
 
@@ -645,8 +631,7 @@ __device__ void bc_bwd_pull(const BcRun &R, int32_t l, const BcCum &p, const BcC
             if (d <= BC_LIGHT) deg = (int)d;
             else u = -1;  // medium or hub: done above
         }
-        const double s = BC_LANE_LIGHT ? lane_gather(R.csr_idx, eb, eb + deg, qb, R.coef)
-                                       : stream_gather(R.csr_idx, eb, deg, qb, R.coef);
+        const double s = lane_gather(R.csr_idx, eb, eb + deg, qb, R.coef);
         c.examined += (unsigned long long)deg;
         if (u >= 0) R.S[u] = s;  // its own lane: the only writer
     }
@@ -684,6 +669,7 @@ __global__ void __launch_bounds__(BC_THREADS, 2) k_bc_persistent(BcRun R) {
     const int64_t nwords = (R.n + 31) >> 5;
     constexpr int CW = (int)(sizeof(BcCtr) / sizeof(unsigned long long));
     __shared__ unsigned long long s_c[CW];
+    __shared__ double s_acc[BC_HOT];  // backward push: the block's sums of the hot targets
     auto read_ctr = [&](int slot) {  // one thread per block reads, the block shares
         if (threadIdx.x < CW) s_c[threadIdx.x] = ((volatile unsigned long long *)(R.ctr + slot))[threadIdx.x];
         __syncthreads();
@@ -799,9 +785,9 @@ __global__ void __launch_bounds__(BC_THREADS, 2) k_bc_persistent(BcRun R) {
             if (lb >= 2) bc_mark(R, bc_load_lev(R.lev + lb - 2).start, p.start, R.lbits[(lb - 2) & 3]);
             BcLocal c;
             if (dir == GP_PUSH) {
-                bc_bwd_push(R, lb, a, b, true, false, c);
+                bc_bwd_push(R, lb, a, b, true, false, s_acc, c);
             } else {
-                bc_bwd_push(R, lb, a, b, false, true, c);
+                bc_bwd_push(R, lb, a, b, false, true, s_acc, c);
                 if (!grid_sync(R.sync, gridDim.x)) return;
                 bc_bwd_pull(R, lb, p, a, c);
             }
@@ -858,6 +844,7 @@ struct gp_bc_work {
     int32_t *med_in_all = nullptr;  // every vertex with a medium in-list
     int64_t n_med_in_all = 0;
     BigBins hub_out, hub_in;  // lists above BC_HUB cut into BC_CHUNK-edge chunks
+    HotSet hot;               // the BC_HOT largest out-degrees, CSC encoded
     double *sigma = nullptr, *S = nullptr, *coef = nullptr, *bc = nullptr;
     uint32_t *unvis = nullptr, *nzin = nullptr;
     uint32_t *lbits[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -889,6 +876,7 @@ void release_bc_work(gp_graph *g, cudaStream_t s) {
     g->bc->src_mem.release(s);
     g->bc->hub_out.mem.release(s);
     g->bc->hub_in.mem.release(s);
+    g->bc->hot.mem.release(s);
     delete g->bc;
     g->bc = nullptr;
 }
@@ -907,6 +895,7 @@ static int ensure_bc_work(gp_graph *g, cudaStream_t s) {
     GP_TRY(w.mem.alloc(w.med_in, n, s));
     GP_TRY(build_bins(g, w.hub_out, g->csr_off, BC_HUB, BC_CHUNK, s));
     GP_TRY(build_bins(g, w.hub_in, g->csc_off, BC_HUB, BC_CHUNK, s));
+    GP_TRY(build_hot(g, w.hot, BC_HOT, g->csr_off, g->csc_idx, s));
     GP_TRY(select_by_degree(g->csc_off, g->n, BC_LIGHT + 1, BC_HUB, w.mem, w.med_in_all, w.n_med_in_all, INT64_MAX,
                             nullptr, s));
     GP_TRY(w.mem.alloc(w.sigma, n, s));
@@ -1011,6 +1000,9 @@ extern "C" int gp_bc(const gp_graph *gc, const int32_t *sources, int64_t nsource
     R.csc_off = g->csc_off;
     R.csr_idx = g->csr_idx;
     R.csc_idx = g->csc_idx;
+    R.csc_enc = w.hot.nhot > 0 ? w.hot.enc_idx : g->csc_idx;
+    R.hot_id = w.hot.hot_id;
+    R.nhot = (int32_t)w.hot.nhot;
     R.med_in_all = w.med_in_all;
     R.n_med_in_all = w.n_med_in_all;
     R.med_out = w.med_out;

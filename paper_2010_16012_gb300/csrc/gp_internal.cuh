@@ -201,6 +201,10 @@ namespace gp {
 
 int build_bins(gp_graph *g, BigBins &b, const int64_t *off, int32_t light_max, int32_t chunk_edges,
                cudaStream_t s);
+// The `slots` vertices of largest degree by sel_off, and enc_src (an index array
+// of m entries) with each of them replaced by HOT_BIT | slot.
+int build_hot(gp_graph *g, HotSet &h, int32_t slots, const int64_t *sel_off, const int32_t *enc_src,
+              cudaStream_t s);
 int build_pull_hot(gp_graph *g, int32_t slots, cudaStream_t s);
 int build_push_hot(gp_graph *g, int32_t slots, cudaStream_t s);
 int select_by_degree(const int64_t *off, int64_t n, int64_t lo, int64_t hi, Arena &mem, int32_t *&list,

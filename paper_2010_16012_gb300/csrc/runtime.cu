@@ -484,8 +484,8 @@ __global__ void k_encode_hot(const int32_t *idx, int64_t m, const int32_t *slot,
 // Picks the `slots` vertices with the largest degree by `sel_off` (ties: lowest
 // ids), builds the copy of `enc_src` (an index array of the graph) with those
 // vertices encoded as HOT_BIT | slot, and the slot -> vertex table.
-static int build_hot(gp_graph *g, HotSet &h, int32_t slots, const int64_t *sel_off, const int32_t *enc_src,
-                     cudaStream_t s) {
+int build_hot(gp_graph *g, HotSet &h, int32_t slots, const int64_t *sel_off, const int32_t *enc_src,
+              cudaStream_t s) {
     h.mem.release(s);
     h = HotSet();
     h.slots = slots;
