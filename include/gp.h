@@ -635,6 +635,35 @@ int gp_selftest_narrow(int64_t n, const double *in, float *ours, float *hw, void
  * Waits for completion.  GP_ERR_INVALID for absent >= the SM count. */
 int gp_selftest_barrier(int absent, void *stream);
 
+/* ------------------------------------------------------------------ memory-system rates */
+
+#define GP_PROBE_GATHER_GLOBAL 0     /* random 4-byte loads from an L2-resident 16 MB array */
+#define GP_PROBE_GATHER_SHARED 1     /* random 4-byte loads from the block's shared memory (64 KB) */
+#define GP_PROBE_GATHER_CLUSTER 2    /* random 4-byte loads across an 8-block cluster's shared memory */
+#define GP_PROBE_RED_F64 3           /* random FP64 atomic adds, result unused, into an L2-resident array */
+#define GP_PROBE_RED_F32 4           /* the same in FP32 */
+#define GP_PROBE_ATOM_SHARED_F64 5   /* random FP64 atomic adds into an 8K-entry shared-memory table */
+#define GP_PROBE_ATOM_SHARED_F32 6   /* the same in FP32 */
+#define GP_PROBE_KINDS 7
+
+/*
+ * Rate of one memory operation on this device: 2 blocks x 1024 threads per SM,
+ * each thread issuing `iters` operations at addresses from a hash of its index
+ * (not in the paper: the ceilings that bound its sweeps, gathers and scatters).
+ *   kind        one of GP_PROBE_*.
+ *   iters       operations per thread (>= 1, <= 65536).
+ *   rate_out    host double: operations per second (whole device), from CUDA
+ *               events around the launch.
+ *   check_out   host double or NULL: for the add kinds, the sum of the target
+ *               table after the launch (equals the number of operations, each
+ *               adds 1); for the loads, the sum of what was read (0: the table
+ *               is zero).
+ * Allocates and frees its own scratch memory.  Waits for completion.
+ * GP_ERR_INVALID for a bad kind or iters; GP_ERR_UNSUPPORTED when the device
+ * cannot launch 8-block clusters of the cluster kind.
+ */
+int gp_probe_rates(int kind, int iters, double *rate_out, double *check_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -151,6 +151,8 @@ SIGNATURES = [
     ("gp_pagerank_fe", ctypes.c_int, [_VP, ctypes.c_int, _F, _D, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP,
                                       ctypes.POINTER(gp_fe_stats), _VP]),
     ("gp_triangles", ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.POINTER(gp_tc_stats), _VP]),
+    ("gp_probe_rates", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), _VP]),
     ("gp_bc", ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_int, _VP, ctypes.c_int, _VP,
                              ctypes.POINTER(gp_bc_stats), _VP]),
     ("gp_batch_create", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _VP]),
@@ -507,6 +509,21 @@ def bc(g: Graph, sources, mode=AUTO, dirs=None, out=None, want_stats=True, strea
                  "steps": L, "direction": list(st.direction[:L]), "phase": list(st.phase[:L]),
                  "level": list(st.level[:L]), "frontier": list(st.frontier[:L]), "examined": list(st.examined[:L]),
                  "step_us": [x / 1e3 for x in st.step_ns[:L]]}
+
+
+PROBE_KINDS = {"gather_global": 0, "gather_shared": 1, "gather_cluster": 2, "red_f64": 3, "red_f32": 4,
+               "atom_shared_f64": 5, "atom_shared_f32": 6}
+
+
+def probe_rates(kind, iters=1024, stream=None):
+    """gp_probe_rates: (operations per second, check value) of one memory
+    operation kind (a key of PROBE_KINDS or its number)."""
+    k = PROBE_KINDS[kind] if isinstance(kind, str) else int(kind)
+    rate = ctypes.c_double(0.0)
+    chk = ctypes.c_double(0.0)
+    _check(load().gp_probe_rates(k, int(iters), ctypes.byref(rate), ctypes.byref(chk), _stream_ptr(stream)),
+           "gp_probe_rates")
+    return rate.value, chk.value
 
 
 class Batch:
