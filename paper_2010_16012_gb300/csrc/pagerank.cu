@@ -12,12 +12,12 @@
 //                    one warp per chunk, coalesced index loads, warp tree sum
 //                    (Section 4's CREW binary merge-tree) into a per-chunk slot.
 //   k_pull_light  -- blocks [0, light_blocks): one warp per tile of 32
-//                    consecutive vertices; the tile's light in-edges are one
-//                    contiguous stream walked 32 edges at a time, each lane
-//                    finds the vertex owning its edge, and a segmented warp
-//                    scan forms per-vertex sums.  Blocks after that: one thread
-//                    per big vertex adds its chunk slots.  Every vertex's
-//                    y, c' = y*inv_deg and |y - x| are written by its owner.
+//                    consecutive vertices; each lane sums its own light
+//                    vertex's in-list with 8 loads in flight (no shuffles: the
+//                    kernel is issue-bound, and light lists are short).  Blocks
+//                    after that: one thread per big vertex adds its chunk
+//                    slots.  Every vertex's y, c' = y*inv_deg and |y - x| are
+//                    written by its owner.
 // Push (scatter with atomics; Section 4.1: O(Lm) write conflicts):
 //   k_push_scatter   -- each source adds d*c[u]*w_uv into y[v] for its
 //                       out-edges with FP32 atomicAdd (RED), big sources in
@@ -217,6 +217,9 @@ __global__ void __launch_bounds__(1024) k_pull_big(PrArgs a) {
     }
 }
 
+#ifndef GP_LIGHT_MIN_BLOCKS
+#define GP_LIGHT_MIN_BLOCKS 3
+#endif
 // Owner lane of virtual edge `eid` in a tile: the last lane k with excl[k] <= eid
 // (zero-degree lanes share their successor's excl, so the last one is non-empty).
 __device__ __forceinline__ int tile_owner(int excl, int eid) {
@@ -229,29 +232,7 @@ __device__ __forceinline__ int tile_owner(int excl, int eid) {
     return k;
 }
 
-// Sum of the lanes of `val` that belong to the same vertex in this 32-edge
-// window, delivered to that vertex's own lane (segmented warp scan).
-__device__ __forceinline__ float window_segment_sum(float val, int kex, int base, int deg, int excl, int incl) {
-    const int lane = lane_id();
-    const int head = max(kex, base) - base;
-#pragma unroll
-    for (int s = 1; s < 32; s <<= 1) {
-        const float tv = __shfl_up_sync(FULL, val, s);
-        if (lane - s >= head) val += tv;
-    }
-    const bool has = deg > 0 && excl < base + 32 && incl > base;
-    const int tail = has ? min(incl, base + 32) - base - 1 : 0;
-    const float seg = __shfl_sync(FULL, val, tail);
-    return has ? seg : 0.f;
-}
-
-#ifndef GP_LIGHT_WINDOWS
-#define GP_LIGHT_WINDOWS 4
-#endif
-#ifndef GP_LIGHT_MIN_BLOCKS
-#define GP_LIGHT_MIN_BLOCKS 3
-#endif
-constexpr int LW = GP_LIGHT_WINDOWS;  // 32-edge windows in flight per step of the light tiles
+constexpr int LIGHT_UNROLL = 8;  // in-edges of a light vertex in flight per lane
 
 template <bool W, bool HOT>
 __global__ void __launch_bounds__(512, GP_LIGHT_MIN_BLOCKS) k_pull_light(PrArgs a) {
@@ -295,41 +276,24 @@ __global__ void __launch_bounds__(512, GP_LIGHT_MIN_BLOCKS) k_pull_light(PrArgs 
             }
             const int64_t dd = e - b;
             const bool big = dd > a.light_max;
-            const int deg = big ? 0 : (int)dd;
-            const int incl = warp_incl_scan(deg);
-            const int excl = incl - deg;
-            const int E = __shfl_sync(FULL, incl, 31);
+            // a light vertex's own lane sums its in-list, LIGHT_UNROLL loads in flight
+            const int64_t e1 = big ? b : e;
             float acc = 0.f;
-            for (int base = 0; base < E; base += 32 * LW) {
-                // LW 32-edge windows per step: all index loads, then all gathers, then the sums
-                int kx[LW];
-                int64_t p[LW];
-                int32_t u[LW];
+            for (int64_t p0 = b; p0 < e1; p0 += LIGHT_UNROLL) {
+                int32_t u[LIGHT_UNROLL];
+                float f[LIGHT_UNROLL];
 #pragma unroll
-                for (int q = 0; q < LW; ++q) {
-                    kx[q] = 0;
-                    p[q] = 0;
-                    if (base + 32 * q < E) {  // uniform: windows past the tile's edges are skipped
-                        const int eq = base + 32 * q + lane;
-                        const int k = tile_owner(excl, eq);
-                        kx[q] = __shfl_sync(FULL, excl, k);
-                        p[q] = __shfl_sync(FULL, b, k) + (eq - kx[q]);
-                    }
-                }
+                for (int q = 0; q < LIGHT_UNROLL; ++q) u[q] = p0 + q < e1 ? ld_idx(idx + p0 + q) : 0;
 #pragma unroll
-                for (int q = 0; q < LW; ++q) u[q] = base + 32 * q + lane < E ? ld_idx(idx + p[q]) : 0;
-                float f[LW];
-#pragma unroll
-                for (int q = 0; q < LW; ++q) {
+                for (int q = 0; q < LIGHT_UNROLL; ++q) {
                     f[q] = 0.f;
-                    if (base + 32 * q + lane < E) {
+                    if (p0 + q < e1) {
                         f[q] = gather_c<HOT>(c, sh_hot, u[q]);
-                        if (W) f[q] *= __ldg(wv + p[q]);
+                        if (W) f[q] *= __ldg(wv + p0 + q);
                     }
                 }
 #pragma unroll
-                for (int q = 0; q < LW; ++q)
-                    if (base + 32 * q < E) acc += window_segment_sum(f[q], kx[q], base + 32 * q, deg, excl, incl);
+                for (int q = 0; q < LIGHT_UNROLL; ++q) acc += f[q];
             }
             if (v < n && !big) {
                 const float y = base_v + a.d * (ps * acc);
