@@ -181,3 +181,17 @@ def test_bc_bad_input(gp):
         gp.bc(G, torch.tensor([0, G.n + 5], dtype=torch.int32, device="cuda"), gp.AUTO)
     x, _ = gp.bc(G, [0, 1], gp.AUTO)  # the graph stays usable
     close(x.cpu().numpy(), oracle.OracleGraph.from_graph(gg.rmat(8, 8, seed=12)).bc([0, 1]))
+
+
+def test_bc_async_error_reported_by_next_call(gp):
+    import torch
+
+    g = gg.rmat(9, 8, seed=13)
+    G = gp.Graph.from_graphgen(g)
+    out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    bad = torch.tensor([1, g.n + 3], dtype=torch.int32, device="cuda")
+    gp.bc(G, bad, gp.AUTO, out=out, want_stats=False)  # enqueued: the kernel finds the bad source
+    with pytest.raises(gp.GpError, match="previous asynchronous"):
+        gp.bc(G, [0], gp.AUTO)
+    x, _ = gp.bc(G, [0, 1], gp.AUTO)  # and the graph works afterwards
+    close(x.cpu().numpy(), oracle.OracleGraph.from_graph(g).bc([0, 1]))
