@@ -659,3 +659,52 @@ def test_bc_dependency_sum_is_path_interior_count(seed):
         lv, _ = O.bfs(int(s))
         want = np.maximum(lv[lv > 0] - 1, 0).sum()
         assert abs(O.bc([int(s)]).sum() - want) <= 1e-9 * max(1, want)
+
+
+def _brandes_py(off, idx, n, s, variant=""):
+    """Brandes for one source in plain Python, with a planted mistake on request:
+    'no_one' drops the 1 of (1 + delta), 'ratio' inverts sigma_u / sigma_w,
+    'self' adds the source's own dependency."""
+    from collections import deque
+    dist = [-1] * n
+    sigma = [0.0] * n
+    dist[s], sigma[s] = 0, 1.0
+    order, q = [], deque([s])
+    while q:
+        u = q.popleft()
+        order.append(u)
+        for w in idx[off[u]:off[u + 1]]:
+            if dist[w] < 0:
+                dist[w] = dist[u] + 1
+                q.append(w)
+            if dist[w] == dist[u] + 1:
+                sigma[w] += sigma[u]
+    delta = [0.0] * n
+    bc = np.zeros(n)
+    for u in reversed(order):
+        for w in idx[off[u]:off[u + 1]]:
+            if dist[w] == dist[u] + 1:
+                r = sigma[w] / sigma[u] if variant == "ratio" else sigma[u] / sigma[w]
+                delta[u] += r * ((0.0 if variant == "no_one" else 1.0) + delta[w])
+        if u != s or variant == "self":
+            bc[u] += delta[u]
+    return bc, dist
+
+
+@pytest.mark.parametrize("variant", ["no_one", "ratio", "self"])
+def test_bc_dependency_sum_check_catches_planted_mistakes(variant):
+    # the full-size BC test checks sum_v bc(v) = sum_t (d(s,t) - 1) per source; this pins that the
+    # check rejects the plausible mistakes in the accumulation, while the correct form passes it
+    g = gg.rmat(8, 8, seed=5)
+    off, idx = list(g.csr_off), list(g.csr_idx)
+    O = og(g)
+    caught = False
+    for s in gg.pick_vertices(g, 6, seed=1):
+        good, dist = _brandes_py(off, idx, g.n, int(s))
+        d = np.array(dist)
+        want = np.maximum(d[d > 0] - 1, 0).sum()
+        assert abs(good.sum() - want) <= 1e-9 * max(1, want)
+        np.testing.assert_allclose(good, O.bc([int(s)]), rtol=1e-12, atol=1e-12)
+        bad, _ = _brandes_py(off, idx, g.n, int(s), variant)
+        caught |= abs(bad.sum() - want) > 1e-6 * max(1, want)
+    assert caught, variant
