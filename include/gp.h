@@ -33,7 +33,10 @@
  *    GP_UPLOAD_COPY are read in place and must stay alive and unchanged until
  *    gp_graph_free.  Library-owned device memory (degree arrays, vertex bins,
  *    queues, bitmaps, partial sums) is obtained from the allocator registered
- *    with gp_set_allocator (default: cudaMallocAsync/cudaFreeAsync).
+ *    with gp_set_allocator (default: stream-ordered allocation from a memory
+ *    pool of the library's own per device, which keeps freed memory for reuse
+ *    rather than returning it to the driver; cudaMallocAsync where the device
+ *    has no pool support).
  *  - Graph layout (Section 2.2): neighbours of each vertex form one contiguous
  *    array; n+1 offsets (int64) mark where each vertex's list begins.  CSR
  *    lists out-neighbours (row u = heads of u->v; what push walks), CSC lists
@@ -88,7 +91,8 @@ int gp_version(void);
  * pointer of at least `bytes` bytes aligned to 256 bytes, usable in stream
  * order on `stream`, or NULL on failure (the call then fails with GP_ERR_OOM).
  * free releases it in stream order.  Passing NULL for both restores the
- * default (cudaMallocAsync / cudaFreeAsync).  Applies to later allocations
+ * default (the library's own pool, stream-ordered, freed memory kept for
+ * reuse).  Applies to later allocations
  * only; memory is always released with the callbacks that allocated it. */
 typedef void *(*gp_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*gp_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);

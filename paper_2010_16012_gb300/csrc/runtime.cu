@@ -42,6 +42,46 @@ static gp_alloc_fn g_alloc = nullptr;
 static gp_free_fn g_free = nullptr;
 static void *g_alloc_ctx = nullptr;
 
+// Without a registered allocator, workspace comes from a memory pool of the
+// library's own per device, which keeps freed memory for reuse (release
+// threshold: no limit) instead of returning it to the driver at every stream
+// synchronisation: a graph uploaded again (same sizes) then costs no new
+// mappings.  Process-local; nullptr where the device has no pool support.
+constexpr int GP_MAX_DEVICES = 64;
+static cudaMemPool_t g_pool[GP_MAX_DEVICES];
+static bool g_pool_tried[GP_MAX_DEVICES];
+
+static cudaMemPool_t lib_pool() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= GP_MAX_DEVICES) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (!g_pool_tried[dev]) {
+        g_pool_tried[dev] = true;
+        int ok = 0;
+        cudaDeviceGetAttribute(&ok, cudaDevAttrMemoryPoolsSupported, dev);
+        cudaMemPool_t pool = nullptr;
+        if (ok) {
+            cudaMemPoolProps props;
+            memset(&props, 0, sizeof(props));
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+                unsigned long long keep = ~0ull;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            } else {
+                pool = nullptr;
+            }
+        }
+        cudaGetLastError();
+        g_pool[dev] = pool;
+    }
+    return g_pool[dev];
+}
+
 int dev_alloc(DevBuf &b, size_t bytes, cudaStream_t s) {
     gp_alloc_fn fn;
     gp_free_fn ffn;
@@ -58,7 +98,8 @@ int dev_alloc(DevBuf &b, size_t bytes, cudaStream_t s) {
         p = fn(bytes, (void *)s, ctx);
         if (!p) return set_error(GP_ERR_OOM, "allocator callback returned NULL for %zu bytes", bytes);
     } else {
-        cudaError_t e = cudaMallocAsync(&p, bytes, s);
+        cudaMemPool_t pool = lib_pool();
+        cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMallocAsync(&p, bytes, s);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
             return set_error(GP_ERR_OOM, "cudaMallocAsync(%zu) failed: %s", bytes, cudaGetErrorString(e));
