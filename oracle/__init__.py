@@ -62,6 +62,8 @@ def _get():
             lib.or_pagerank_adjoint.restype = c.c_int
             lib.or_pagerank_adjoint.argtypes = [vp, c.c_double, vp, vp, c.c_int, c.c_double, vp, vp, vp,
                                                 c.POINTER(c.c_double), c.c_int]
+            lib.or_pagerank_adjoint_raw.restype = c.c_int
+            lib.or_pagerank_adjoint_raw.argtypes = [vp, c.c_double, vp, vp, c.c_int, c.c_double, vp, vp, vp, vp]
             lib.or_sssp_dijkstra.restype = c.c_int64
             lib.or_sssp_dijkstra.argtypes = [vp, c.c_int32, vp, vp]
             lib.or_sssp_delta.restype = c.c_int64
@@ -161,6 +163,19 @@ class OracleGraph:
                                           int(nthreads))
         return lam, gs, gw, k, r.value
 
+    def pagerank_adjoint_raw(self, g, damping: float = 0.85, personalization=None, iters: int = 100000,
+                             tol: float = 1e-14):
+        """Gradient of L = g.x* with respect to the RAW weights this graph was
+        built with, normalised per source inside (P_vu = W_uv / S_u).  Returns
+        (x*, lambda, grad_s, grad_W in input edge order, converged)."""
+        n, m = self.n, self.m
+        x, lam, gs = (np.empty(n, dtype=np.float64) for _ in range(3))
+        gW = np.empty(m, dtype=np.float64)
+        s = None if personalization is None else np.ascontiguousarray(personalization, dtype=np.float64)
+        ga = np.ascontiguousarray(g, dtype=np.float64)
+        rc = self._lib.or_pagerank_adjoint_raw(self._h, float(damping), _ptr(s), _ptr(ga), int(iters), float(tol),
+                                               _ptr(x), _ptr(lam), _ptr(gs), _ptr(gW))
+        return x, lam, gs, gW, rc == 0
 
     # ------------------------------------------------------------ SSSP
     def sssp(self, src: int):

@@ -25,6 +25,8 @@
  *     bottom-up (pull: unvisited vertices scan in-edges for a frontier vertex).
  *   - Adjoint of the PageRank fixed point (not in the paper): lambda solves
  *     (I - d P^T) lambda = g; dL/ds = (1-d) lambda; dL/dP_vu = d lambda_v x_u.
+ *     With raw weights normalised inside (P_vu = W_uv / S_u), the chain rule
+ *     through the normalisation gives dL/dW_uv (or_pagerank_adjoint_raw).
  *   - Single-source shortest paths: Dijkstra (the plain definition, min over
  *     paths of the weight sum), and the push- and pull-based Delta-Stepping of
  *     the paper's Section 3 listing, run sequentially with one direction per
@@ -361,6 +363,91 @@ int or_pagerank_adjoint(const or_graph *g, double d, const double *x, const doub
     free(lam);
     free(nxt);
     return k;
+}
+
+/*
+ * Gradient with respect to RAW edge weights that are normalised inside the
+ * function (not in the paper; the weighted form of the Section 3.1 iteration
+ * with P_vu = W_uv / S_u, S_u = sum over u's out-edges of W).  The graph's
+ * stored weights are read as the raw W here, not as P.  In order:
+ *   1. S_u = sum_{(u->k)} W_uk; P_vu = W_uv / S_u per edge (S_u > 0 whenever
+ *      u has an out-edge, since weights are positive);
+ *   2. x* = the fixed point x = (1-d) s + d P x (Jacobi sweeps from 1/n until
+ *      the L1 change is below tol, at most `iters`);
+ *   3. lambda solves (I - d P^T) lambda = g (Jacobi from g, same stop rule);
+ *   4. dL/dP_vu = d lambda_v x*_u, and through P_ku = W_uk / S_u (every entry
+ *      of u's column depends on W_uv through S_u):
+ *        dL/dW_uv = sum_k dL/dP_ku dP_ku/dW_uv
+ *                 = d x*_u (lambda_v - sum_{(u->k)} P_ku lambda_k) / S_u;
+ *      dL/ds_v = (1-d) lambda_v.
+ * s is uniform 1/n when NULL.  Outputs x (the fixed point), lambda, grad_s and
+ * grad_W (input edge order).  Returns 0 when both iterations reached tol.
+ */
+int or_pagerank_adjoint_raw(const or_graph *g, double d, const double *s, const double *gv, int iters, double tol,
+                            double *x, double *lambda, double *grad_s, double *grad_W) {
+    const int64_t n = g->n, m = g->m;
+    double *S = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *P = (double *)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+    double *a = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    double *b = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    /* step 1 */
+    for (int64_t u = 0; u < n; ++u)
+        for (int64_t j = g->out_off[u]; j < g->out_off[u + 1]; ++j) S[u] += g->w ? g->w[g->out_eid[j]] : 1.0;
+    for (int64_t u = 0; u < n; ++u)
+        for (int64_t j = g->out_off[u]; j < g->out_off[u + 1]; ++j)
+            P[g->out_eid[j]] = (g->w ? g->w[g->out_eid[j]] : 1.0) / S[u];
+    /* step 2: pull sweeps y[v] = (1-d) s[v] + d sum_{(u->v)} P_vu x[u] */
+    int ok = 1;
+    for (int64_t v = 0; v < n; ++v) a[v] = 1.0 / (double)n;
+    int k = 0;
+    double r = INFINITY;
+    while (k < iters && !(r < tol)) {
+        for (int64_t v = 0; v < n; ++v) {
+            double acc = 0.0;
+            for (int64_t j = g->in_off[v]; j < g->in_off[v + 1]; ++j) acc += P[g->in_eid[j]] * a[g->in_idx[j]];
+            b[v] = (1.0 - d) * (s ? s[v] : 1.0 / (double)n) + d * acc;
+        }
+        r = 0.0;
+        for (int64_t v = 0; v < n; ++v) r += fabs(b[v] - a[v]);
+        double *t = a;
+        a = b;
+        b = t;
+        ++k;
+    }
+    if (!(r < tol)) ok = 0;
+    memcpy(x, a, (size_t)n * sizeof(double));
+    /* step 3: lambda_u = g_u + d sum_{(u->v)} P_vu lambda_v */
+    for (int64_t v = 0; v < n; ++v) a[v] = gv[v];
+    k = 0;
+    r = INFINITY;
+    while (k < iters && !(r < tol)) {
+        for (int64_t u = 0; u < n; ++u) {
+            double acc = 0.0;
+            for (int64_t j = g->out_off[u]; j < g->out_off[u + 1]; ++j) acc += P[g->out_eid[j]] * a[g->out_idx[j]];
+            b[u] = gv[u] + d * acc;
+        }
+        r = 0.0;
+        for (int64_t v = 0; v < n; ++v) r += fabs(b[v] - a[v]);
+        double *t = a;
+        a = b;
+        b = t;
+        ++k;
+    }
+    if (!(r < tol)) ok = 0;
+    memcpy(lambda, a, (size_t)n * sizeof(double));
+    /* step 4 */
+    for (int64_t v = 0; v < n; ++v) grad_s[v] = (1.0 - d) * lambda[v];
+    for (int64_t u = 0; u < n; ++u) {
+        double mean = 0.0; /* sum_k P_ku lambda_k over u's out-edges */
+        for (int64_t j = g->out_off[u]; j < g->out_off[u + 1]; ++j) mean += P[g->out_eid[j]] * lambda[g->out_idx[j]];
+        for (int64_t j = g->out_off[u]; j < g->out_off[u + 1]; ++j)
+            grad_W[g->out_eid[j]] = d * x[u] * (lambda[g->out_idx[j]] - mean) / S[u];
+    }
+    free(S);
+    free(P);
+    free(a);
+    free(b);
+    return ok ? 0 : 1;
 }
 
 /* ------------------------------------------------------------------ SSSP */

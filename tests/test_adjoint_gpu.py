@@ -78,26 +78,25 @@ def test_adjoint_host_buffers(gp):
 
 
 def test_raw_weight_gradient_with_normalize(gp):
-    """GP_UPLOAD_NORMALIZE: dL/dw_uv = (dL/dP_vu - sum_k P_ku dL/dP_ku) / S_u (chain rule
-    through P = w / S applied to the oracle's dL/dP)."""
+    """GP_UPLOAD_NORMALIZE: the gradient with respect to the raw weights (P = W / S
+    normalised inside) against the oracle's own raw-weight adjoint, which is
+    pinned on CPU by forward-mode LU derivatives and renormalising finite
+    differences."""
     import torch
 
     g = gg.rmat(9, 8, seed=7, symmetrize=False).with_weights(8, normalize=False)
     G = gp.Graph.from_graphgen(g, normalize=True)
-    src, dst = g.edges()
-    w = g.csr_w.astype(np.float64)
-    S = np.bincount(src, weights=w, minlength=g.n)
-    P = w / S[src]
-    O = oracle.OracleGraph(g.n, src, dst, P)
-    x = fixed_point(O)
+    O = oracle.OracleGraph.from_graph(g)  # raw weights; the oracle normalises them itself
     gvec = np.random.default_rng(2).normal(size=g.n)
-    _, _, gP, _, _ = O.pagerank_adjoint(x, gvec, 0.85)
-    mean_term = np.bincount(src, weights=P * gP, minlength=g.n)
-    gw_ref = (gP - mean_term[src]) / S[src]
-    gw, _, _ = gp.pagerank_backward(G, torch.from_numpy(x.astype(np.float32)).cuda(),
-                                    torch.from_numpy(gvec.astype(np.float32)).cuda(), iters=2000, tol=1e-9,
-                                    want_personalization=False)
+    x, _, gs_ref, gw_ref, conv = O.pagerank_adjoint_raw(gvec, 0.85)
+    assert conv
+    gw, gs, _ = gp.pagerank_backward(G, torch.from_numpy(x.astype(np.float32)).cuda(),
+                                     torch.from_numpy(gvec.astype(np.float32)).cuda(), iters=2000, tol=1e-9)
     assert rel_err(gw, gw_ref) <= REL, rel_err(gw, gw_ref)
+    assert rel_err(gs, gs_ref) <= REL, rel_err(gs, gs_ref)
+    # the forward pass of the normalised upload reaches the oracle's fixed point
+    xg, st = gp.pagerank(G, gp.PULL, 0.85, 1000, 1e-9)
+    assert st["converged"] and float(np.abs(xg.cpu().numpy().astype(np.float64) - x).max()) <= 1e-6
 
 
 def test_finite_differences_scale10(gp):
@@ -167,3 +166,27 @@ def test_autograd_function(gp):
     O2 = oracle.OracleGraph(g.n, src, dst, w2.cpu().numpy())
     xr2 = fixed_point(O2)
     assert np.abs(x2.detach().cpu().numpy() - xr2).max() < 1e-6
+
+
+def test_autograd_graphs_sharing_one_graph(gp):
+    """Two forward passes with different weights on one Graph, then the first
+    one's backward: its gradient is taken at its own weights."""
+    import torch
+
+    g = gg.rmat(9, 8, seed=41, symmetrize=False).with_weights(42)
+    perm = torch.from_numpy(gg._transpose_perm(g)).cuda()
+    G = gp.Graph.from_graphgen(g)
+    src, dst = g.edges()
+    coef = torch.from_numpy(np.random.default_rng(5).normal(size=g.n).astype(np.float32)).cuda()
+    w1 = torch.from_numpy(g.csr_w.copy()).cuda().requires_grad_(True)
+    w2_host = (g.csr_w * np.random.default_rng(6).uniform(0.2, 1.0, size=g.m)).astype(np.float32)
+    w2 = torch.from_numpy(w2_host).cuda().requires_grad_(True)
+    x1 = gp.pagerank_autograd(G, w1, None, csc_perm=perm, iters=1000, tol=1e-9, adj_tol=1e-9)
+    x2 = gp.pagerank_autograd(G, w2, None, csc_perm=perm, iters=1000, tol=1e-9, adj_tol=1e-9)
+    (coef * x1).sum().backward()
+    (coef * x2).sum().backward()
+    for w, wh in ((w1, g.csr_w), (w2, w2_host)):
+        O = oracle.OracleGraph(g.n, src, dst, wh)
+        xr = fixed_point(O)
+        _, _, gw_ref, _, _ = O.pagerank_adjoint(xr, coef.cpu().numpy().astype(np.float64), 0.85)
+        assert rel_err(w.grad, gw_ref) <= REL

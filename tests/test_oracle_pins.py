@@ -327,6 +327,75 @@ def test_adjoint_finite_differences():
         assert abs(fd - gs[vtx]) <= 1e-7 * max(1.0, abs(fd))
 
 
+@pytest.mark.parametrize("seed", range(8))
+def test_adjoint_raw_weights_forward_mode(seed):
+    """Raw weights normalised inside (P = W / S): the oracle's reverse-mode
+    gradient against forward-mode derivatives from LU solves.  For each edge
+    e = (u -> v) the tangent of P is (E_v - P[:, u]) / S_u in column u only,
+    and dx = (I - dP)^-1 d (dP) x; dL = g . dx.  Graphs of n <= 12 with dangling
+    vertices, self-loops, a repeated edge and a personalisation vector."""
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(2, 13))
+    mask = rng.random((n, n)) < 0.35
+    mask[int(rng.integers(n))] = False  # one dangling source
+    u, v = np.nonzero(mask)
+    if len(u):  # a parallel copy of one edge: S and P must count both
+        k = int(rng.integers(len(u)))
+        u, v = np.append(u, u[k]), np.append(v, v[k])
+    W = rng.uniform(0.1, 2.0, size=len(u))
+    d = float(rng.uniform(0.6, 0.9))
+    s = rng.random(n)
+    s /= s.sum()
+    gvec = rng.normal(size=n)
+    G = oracle.OracleGraph(n, u, v, W)
+    x, lam, gs, gW, conv = G.pagerank_adjoint_raw(gvec, d, personalization=s)
+    assert conv
+    A = np.zeros((n, n))
+    np.add.at(A, (v, u), W)
+    S = A.sum(axis=0)
+    P = np.divide(A, S, out=np.zeros_like(A), where=S > 0)
+    M = np.eye(n) - d * P
+    x_ref = np.linalg.solve(M, (1 - d) * s)
+    np.testing.assert_allclose(x, x_ref, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(lam, np.linalg.solve(M.T, gvec), rtol=0, atol=1e-11)
+    np.testing.assert_allclose(gs, (1 - d) * np.linalg.solve(M.T, gvec), rtol=0, atol=1e-11)
+    for e in range(len(u)):
+        dP = np.zeros((n, n))
+        dP[:, u[e]] = -P[:, u[e]] / S[u[e]]
+        dP[v[e], u[e]] += 1.0 / S[u[e]]
+        dx = np.linalg.solve(M, d * dP @ x_ref)
+        assert abs(gW[e] - gvec @ dx) <= 1e-11, (e, gW[e], gvec @ dx)
+
+
+def test_adjoint_raw_weights_finite_differences():
+    """Central differences (h = 1e-4) of L = g . x*(W / S) where every
+    perturbation of a raw weight is renormalised inside the loss, through an
+    FP64 dense solve, on an R-MAT scale-6 graph with raw weights in (0, 1]."""
+    g = gg.rmat(6, 8, seed=13, symmetrize=False).with_weights(14, normalize=False)
+    src, dst = g.edges()
+    W = g.csr_w.astype(np.float64)
+    d = 0.85
+    rng = np.random.default_rng(15)
+    gvec = rng.normal(size=g.n)
+
+    def loss(Wv):
+        S = np.bincount(src, weights=Wv, minlength=g.n)
+        P = np.zeros((g.n, g.n))
+        np.add.at(P, (dst, src), Wv / S[src])
+        return float(gvec @ np.linalg.solve(np.eye(g.n) - d * P, np.full(g.n, (1 - d) / g.n)))
+
+    G = oracle.OracleGraph(g.n, src, dst, g.csr_w)
+    _, _, _, gW, conv = G.pagerank_adjoint_raw(gvec, d)
+    assert conv
+    h = 1e-4
+    for e in rng.choice(g.m, size=16, replace=False):
+        Wp, Wm = W.copy(), W.copy()
+        Wp[e] += h
+        Wm[e] -= h
+        fd = (loss(Wp) - loss(Wm)) / (2 * h)
+        assert abs(fd - gW[e]) <= 1e-7 * max(1.0, abs(fd)), (e, fd, gW[e])
+
+
 def test_full_size_bfs_checkers_catch_planted_mistakes():
     """The level/parent rules used at full size accept the oracle's BFS and
     reject each kind of planted mistake (a level one too deep, one too shallow,
