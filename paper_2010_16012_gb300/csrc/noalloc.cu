@@ -96,6 +96,17 @@ __global__ void __launch_bounds__(256) k_na_sweep(int64_t n, int64_t m, const in
                 b = e = 0;
             }
         }
+        // The 32-bit scan below is exact while the tile's degrees sum to at most
+        // m (< 2^31), which monotone offsets guarantee.  Offsets that rise and
+        // fall pass the per-vertex check yet can sum past 2^31, so the tile's
+        // total is formed in 64 bits first and a tile above m is skipped.
+        int64_t tile_sum = e - b;
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) tile_sum += __shfl_xor_sync(FULL, tile_sum, st);
+        if (tile_sum > m) {
+            bad = true;
+            b = e = 0;
+        }
         const int deg = (int)(e - b);
         const int incl = warp_incl_scan(deg);
         const int excl = incl - deg;
