@@ -53,7 +53,7 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--quiet", action="store_true")
     p.add_argument("--no-batched", action="store_true")
-    p.add_argument("--only", choices=["pr_pull", "pr_push", "bfs", "batched", "sssp", "tc", "pr_fe", "bc", "probes"], default=None,
+    p.add_argument("--only", choices=["pr_pull", "pr_push", "bfs", "batched", "sssp", "tc", "pr_fe", "bc"], default=None,
                    help="profiling case: run only this part (fixed --sweeps for PageRank), no contract line")
     p.add_argument("--sweeps", type=int, default=4)
     p.add_argument("--delta", type=float, default=64.0, help="--only sssp: bucket width")
@@ -667,8 +667,6 @@ def run_only(args):
         return run_only_tc(args)
     if args.only == "bc":
         return run_only_bc(args)
-    if args.only == "probes":
-        return run_only_probes(args)
     if args.only == "pr_fe":
         return run_only_fe(args)
     g = make_graph(args.scale)
@@ -865,27 +863,6 @@ def run_only_tc(args):
                              "ms": round(dt * 1e3, 1), "gteps": round(g.m / dt / 1e9, 4)}
         out["equals_oracle"] = bool(np.array_equal(counts["pull"], ref))
     print(json.dumps({"profile_case": "tc", "scale": args.scale, "n": g.n, "m": g.m, "opts": opts, **out}), flush=True)
-    return 0
-
-
-def run_only_probes(args):
-    """Rates of the memory operations the kernels are built from (gp_probe_rates):
-    random 4-byte gathers from L2, shared memory and a cluster's distributed
-    shared memory; random FP64/FP32 atomic adds into L2 and into shared memory.
-    Best of --steps runs after --warmup, G operations per second."""
-    import paper_2010_16012_gb300 as gp
-
-    out = {}
-    for name in gp.PROBE_KINDS:
-        iters = 2048 if name.startswith("gather") else 1024
-        for _ in range(max(1, args.warmup)):
-            gp.probe_rates(name, iters)
-        best = 0.0
-        for _ in range(max(1, args.steps)):
-            r, _ = gp.probe_rates(name, iters)
-            best = max(best, r)
-        out[name] = round(best / 1e9, 1)
-    print(json.dumps({"profile_case": "probes", "unit": "G operations/s", **out}), flush=True)
     return 0
 
 

@@ -92,11 +92,24 @@ int gp_version(void);
  * order on `stream`, or NULL on failure (the call then fails with GP_ERR_OOM).
  * free releases it in stream order.  Passing NULL for both restores the
  * default (the library's own pool, stream-ordered, freed memory kept for
- * reuse).  Applies to later allocations
+ * reuse until gp_pool_trim).  Applies to later allocations
  * only; memory is always released with the callbacks that allocated it. */
 typedef void *(*gp_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*gp_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 int gp_set_allocator(gp_alloc_fn alloc, gp_free_fn free_fn, void *ctx);
+
+/* The library's default pool (one per device, created on first use) keeps the
+ * memory that gp_graph_free and the entry points' temporary buffers give back,
+ * so the next upload of a graph of the same size maps nothing new; that memory
+ * stays held by the library, unusable by other allocators in the process
+ * (PyTorch's included), until it is trimmed.  gp_pool_usage reports, for the
+ * current device, the bytes the pool holds from the driver (reserved) and the
+ * bytes handed out and not yet freed (used); both are 0 before first use.
+ * gp_pool_trim synchronises the current device, then returns held memory to
+ * the driver until at most keep_bytes stay reserved (memory in use is never
+ * released).  Neither touches memory of a registered allocator (gp_set_allocator). */
+int gp_pool_usage(int64_t *reserved_bytes, int64_t *used_bytes);
+int gp_pool_trim(int64_t keep_bytes);
 
 /* ------------------------------------------------------------------ graph */
 
@@ -226,7 +239,9 @@ typedef struct gp_pr_stats {
  * FP64; iteration stops at the first sweep where it is below tol, or after
  * `iters` sweeps (then GP_ERR_NOT_CONVERGED, with the last iterate written).
  * tol = 0 runs exactly `iters` sweeps and returns GP_OK.
- *   mode            GP_PUSH (scatter, FP32 atomicAdd), GP_PULL (gather, no atomics) or GP_AUTO.
+ *   mode            GP_PUSH (scatter with atomics: FP64 reductions in L2 by default,
+ *                   FP32 atomicAdd with push_fp64_accum = 0), GP_PULL (gather, no
+ *                   atomics) or GP_AUTO.
  *   damping         in (0, 1).
  *   iters           >= 1.
  *   personalization float[n] "any" or NULL (uniform 1/n): the teleport vector s.
@@ -354,7 +369,7 @@ typedef struct gp_fe_stats {
  * stops with F empty (converged) is within ||r||_1 / (1 - d) of it in L1
  * (stats->error_bound; P as in gp_pagerank: 1/deg_out, the weights as given, or
  * normalised weights).
- *   mode        GP_PUSH: F scatters over out-edges with FP32 atomics;
+ *   mode        GP_PUSH: F scatters over out-edges with FP64 atomic adds in L2;
  *               GP_PULL: every vertex gathers over its in-edges from F (owner
  *               writes, no atomics);
  *               GP_AUTO: per iteration, pull when F's out-edges times fe_alpha
@@ -638,35 +653,6 @@ int gp_selftest_narrow(int64_t n, const double *in, float *ours, float *hw, void
  * return, and the call returns GP_ERR_TIMEOUT with the device context intact.
  * Waits for completion.  GP_ERR_INVALID for absent >= the SM count. */
 int gp_selftest_barrier(int absent, void *stream);
-
-/* ------------------------------------------------------------------ memory-system rates */
-
-#define GP_PROBE_GATHER_GLOBAL 0     /* random 4-byte loads from an L2-resident 16 MB array */
-#define GP_PROBE_GATHER_SHARED 1     /* random 4-byte loads from the block's shared memory (64 KB) */
-#define GP_PROBE_GATHER_CLUSTER 2    /* random 4-byte loads across an 8-block cluster's shared memory */
-#define GP_PROBE_RED_F64 3           /* random FP64 atomic adds, result unused, into an L2-resident array */
-#define GP_PROBE_RED_F32 4           /* the same in FP32 */
-#define GP_PROBE_ATOM_SHARED_F64 5   /* random FP64 atomic adds into an 8K-entry shared-memory table */
-#define GP_PROBE_ATOM_SHARED_F32 6   /* the same in FP32 */
-#define GP_PROBE_KINDS 7
-
-/*
- * Rate of one memory operation on this device: 2 blocks x 1024 threads per SM,
- * each thread issuing `iters` operations at addresses from a hash of its index
- * (not in the paper: the ceilings that bound its sweeps, gathers and scatters).
- *   kind        one of GP_PROBE_*.
- *   iters       operations per thread (>= 1, <= 65536).
- *   rate_out    host double: operations per second (whole device), from CUDA
- *               events around the launch.
- *   check_out   host double or NULL: for the add kinds, the sum of the target
- *               table after the launch (equals the number of operations, each
- *               adds 1); for the loads, the sum of what was read (0: the table
- *               is zero).
- * Allocates and frees its own scratch memory.  Waits for completion.
- * GP_ERR_INVALID for a bad kind or iters; GP_ERR_UNSUPPORTED when the device
- * cannot launch 8-block clusters of the cluster kind.
- */
-int gp_probe_rates(int kind, int iters, double *rate_out, double *check_out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -132,6 +132,8 @@ SIGNATURES = [
     ("gp_last_error", ctypes.c_char_p, []),
     ("gp_version", ctypes.c_int, []),
     ("gp_set_allocator", ctypes.c_int, [ALLOC_FN, FREE_FN, _VP]),
+    ("gp_pool_usage", ctypes.c_int, [ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    ("gp_pool_trim", ctypes.c_int, [_I64]),
     ("gp_graph_upload", ctypes.c_int, [ctypes.POINTER(_VP), _I64, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _U, _VP]),
     ("gp_graph_free", ctypes.c_int, [_VP]),
     ("gp_graph_info_get", ctypes.c_int, [_VP, ctypes.POINTER(gp_graph_info)]),
@@ -151,8 +153,6 @@ SIGNATURES = [
     ("gp_pagerank_fe", ctypes.c_int, [_VP, ctypes.c_int, _F, _D, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP,
                                       ctypes.POINTER(gp_fe_stats), _VP]),
     ("gp_triangles", ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.POINTER(gp_tc_stats), _VP]),
-    ("gp_probe_rates", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
-                                      ctypes.POINTER(ctypes.c_double), _VP]),
     ("gp_bc", ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_int, _VP, ctypes.c_int, _VP,
                              ctypes.POINTER(gp_bc_stats), _VP]),
     ("gp_batch_create", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _VP]),
@@ -358,9 +358,11 @@ def _autograd_function():
 
         @staticmethod
         def forward(ctx, csr_w, personalization, graph, csc_perm, damping, iters, tol, mode, adj_iters, adj_tol):
+            ctx.weights = None
             if csr_w is not None:
                 csc_w = None if csc_perm is None else csr_w.detach().index_select(0, csc_perm).contiguous()
-                graph.set_weights(csr_w.detach().contiguous(), csc_w)
+                ctx.weights = (csr_w.detach().contiguous(), csc_w)
+                graph.set_weights(*ctx.weights)
             s = None if personalization is None else personalization.detach().contiguous()
             x, _ = pagerank(graph, mode, damping, iters, tol, personalization=s)
             ctx.graph = graph
@@ -374,6 +376,8 @@ def _autograd_function():
         def backward(ctx, grad_x):
             (x,) = ctx.saved_tensors
             damping, mode, adj_iters, adj_tol = ctx.cfg
+            if ctx.weights is not None:  # another forward may have repointed the shared graph since
+                ctx.graph.set_weights(*ctx.weights)
             gw, gs, _ = pagerank_backward(ctx.graph, x, grad_x.contiguous().float(), mode, damping, adj_iters, adj_tol,
                                           want_weights=ctx.has_w, want_personalization=ctx.has_s)
             return gw, gs, None, None, None, None, None, None, None, None
@@ -384,8 +388,15 @@ def _autograd_function():
 def pagerank_autograd(graph: Graph, csr_w=None, personalization=None, csc_perm=None, damping=0.85, iters=1000,
                       tol=1e-7, mode=PULL, adj_iters=1000, adj_tol=1e-7):
     """Differentiable PageRank: gradients flow to the CSR edge weights `csr_w`
-    (the graph's weights are replaced by them; `csc_perm[j]` = CSR position of
-    CSC slot j for non-symmetric graphs) and to the personalization vector."""
+    (`csc_perm[j]` = CSR position of CSC slot j for non-symmetric graphs) and to
+    the personalization vector.
+
+    The graph's weights are replaced in place: after the call `graph` points at
+    copies of `csr_w` (and its CSC permutation) made by this forward pass, for
+    later gp_pagerank calls too.  Backward points the graph at its own forward's
+    weights again before the adjoint, so several autograd graphs may share one
+    Graph and run their backward passes in any order, provided they are used
+    from one host thread at a time."""
     global _PRF
     if _PRF is None:
         _PRF = _autograd_function()
@@ -511,19 +522,18 @@ def bc(g: Graph, sources, mode=AUTO, dirs=None, out=None, want_stats=True, strea
                  "step_us": [x / 1e3 for x in st.step_ns[:L]]}
 
 
-PROBE_KINDS = {"gather_global": 0, "gather_shared": 1, "gather_cluster": 2, "red_f64": 3, "red_f32": 4,
-               "atom_shared_f64": 5, "atom_shared_f32": 6}
+def pool_usage():
+    """gp_pool_usage: (reserved, used) bytes of the library's default memory pool
+    on the current device."""
+    r, u = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load().gp_pool_usage(ctypes.byref(r), ctypes.byref(u)), "gp_pool_usage")
+    return r.value, u.value
 
 
-def probe_rates(kind, iters=1024, stream=None):
-    """gp_probe_rates: (operations per second, check value) of one memory
-    operation kind (a key of PROBE_KINDS or its number)."""
-    k = PROBE_KINDS[kind] if isinstance(kind, str) else int(kind)
-    rate = ctypes.c_double(0.0)
-    chk = ctypes.c_double(0.0)
-    _check(load().gp_probe_rates(k, int(iters), ctypes.byref(rate), ctypes.byref(chk), _stream_ptr(stream)),
-           "gp_probe_rates")
-    return rate.value, chk.value
+def pool_trim(keep_bytes=0):
+    """gp_pool_trim: return the pool's unused memory to the driver, keeping at
+    most keep_bytes reserved."""
+    _check(load().gp_pool_trim(int(keep_bytes)), "gp_pool_trim")
 
 
 class Batch:

@@ -718,6 +718,44 @@ int gp_set_allocator(gp_alloc_fn alloc, gp_free_fn free_fn, void *ctx) {
     return GP_OK;
 }
 
+int gp_pool_usage(int64_t *reserved_bytes, int64_t *used_bytes) {
+    clear_error();
+    if (!reserved_bytes || !used_bytes) return set_error(GP_ERR_INVALID, "gp_pool_usage: NULL output");
+    *reserved_bytes = 0;
+    *used_bytes = 0;
+    int dev = 0;
+    GP_CUDA(cudaGetDevice(&dev));
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        if (dev >= 0 && dev < GP_MAX_DEVICES && g_pool_tried[dev]) pool = g_pool[dev];
+    }
+    if (!pool) return GP_OK;  // never used on this device (or no pool support)
+    unsigned long long r = 0, u = 0;
+    GP_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r));
+    GP_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u));
+    *reserved_bytes = (int64_t)r;
+    *used_bytes = (int64_t)u;
+    return GP_OK;
+}
+
+int gp_pool_trim(int64_t keep_bytes) {
+    clear_error();
+    if (keep_bytes < 0) return set_error(GP_ERR_INVALID, "gp_pool_trim: keep_bytes %lld < 0", (long long)keep_bytes);
+    int dev = 0;
+    GP_CUDA(cudaGetDevice(&dev));
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        if (dev >= 0 && dev < GP_MAX_DEVICES && g_pool_tried[dev]) pool = g_pool[dev];
+    }
+    if (!pool) return GP_OK;
+    // frees enqueued on streams complete before the trim sees them
+    GP_CUDA(cudaDeviceSynchronize());
+    GP_CUDA(cudaMemPoolTrimTo(pool, (size_t)keep_bytes));
+    return GP_OK;
+}
+
 int gp_options_default(gp_options *opt) {
     if (!opt) return set_error(GP_ERR_INVALID, "gp_options_default: NULL");
     memset(opt, 0, sizeof(*opt));
