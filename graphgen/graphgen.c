@@ -105,6 +105,18 @@ void gg_er_edges(int64_t n, int64_t ne, uint64_t seed, int32_t *src, int32_t *ds
     }
 }
 
+/* The calling OpenMP thread's share [lo, hi) of [0, n) (all of it outside a
+ * parallel region). */
+static void gg_thread_range(int64_t n, int64_t *lo, int64_t *hi) {
+#ifdef _OPENMP
+    const int64_t t = omp_get_thread_num(), T = omp_get_num_threads();
+#else
+    const int64_t t = 0, T = 1;
+#endif
+    *lo = n * t / T;
+    *hi = n * (t + 1) / T;
+}
+
 static int gg_cmp_i32(const void *x, const void *y) {
     const int32_t a = *(const int32_t *)x, b = *(const int32_t *)y;
     return (a > b) - (a < b);
@@ -141,20 +153,33 @@ int64_t gg_build_csr(int64_t n, int64_t ne, const int32_t *src, const int32_t *d
         if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n) return -1;
     int64_t *cnt = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     if (!cnt) return -1;
-    for (int64_t e = 0; e < ne; ++e) {
-        const int32_t u = src[e], v = dst[e];
-        if (drop_self && u == v) continue;
-        cnt[u]++;
-        if (symmetrize) cnt[v]++;
+    /* Counting sort by row.  Each thread owns a contiguous range of rows and
+     * scans the whole edge list in order, touching only its own rows, so a
+     * row's entries arrive in edge order whatever the thread count. */
+#pragma omp parallel
+    {
+        int64_t lo = 0, hi = n;
+        gg_thread_range(n, &lo, &hi);
+        for (int64_t e = 0; e < ne; ++e) {
+            const int32_t u = src[e], v = dst[e];
+            if (drop_self && u == v) continue;
+            if (u >= lo && u < hi) cnt[u]++;
+            if (symmetrize && v >= lo && v < hi) cnt[v]++;
+        }
     }
     off[0] = 0;
     for (int64_t v = 0; v < n; ++v) off[v + 1] = off[v] + cnt[v];
     for (int64_t v = 0; v < n; ++v) cnt[v] = off[v];
-    for (int64_t e = 0; e < ne; ++e) {
-        const int32_t u = src[e], v = dst[e];
-        if (drop_self && u == v) continue;
-        idx[cnt[u]++] = v;
-        if (symmetrize) idx[cnt[v]++] = u;
+#pragma omp parallel
+    {
+        int64_t lo = 0, hi = n;
+        gg_thread_range(n, &lo, &hi);
+        for (int64_t e = 0; e < ne; ++e) {
+            const int32_t u = src[e], v = dst[e];
+            if (drop_self && u == v) continue;
+            if (u >= lo && u < hi) idx[cnt[u]++] = v;
+            if (symmetrize && v >= lo && v < hi) idx[cnt[v]++] = u;
+        }
     }
     /* sort (and dedup) every row in place; cnt[v] becomes the kept length */
 #pragma omp parallel for schedule(dynamic, 1024)
@@ -192,16 +217,30 @@ void gg_transpose(int64_t n, const int64_t *off, const int32_t *idx, const float
                   int32_t *tidx, float *tw, int64_t *perm) {
     const int64_t m = off[n];
     int64_t *cnt = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
-    for (int64_t e = 0; e < m; ++e) cnt[idx[e]]++;
+    /* as in gg_build_csr: each thread owns a range of columns and scans all rows in order */
+#pragma omp parallel
+    {
+        int64_t lo = 0, hi = n;
+        gg_thread_range(n, &lo, &hi);
+        for (int64_t e = 0; e < m; ++e)
+            if (idx[e] >= lo && idx[e] < hi) cnt[idx[e]]++;
+    }
     toff[0] = 0;
     for (int64_t v = 0; v < n; ++v) toff[v + 1] = toff[v] + cnt[v];
     for (int64_t v = 0; v < n; ++v) cnt[v] = toff[v];
-    for (int64_t u = 0; u < n; ++u) {
-        for (int64_t e = off[u]; e < off[u + 1]; ++e) {
-            const int64_t slot = cnt[idx[e]]++;
-            tidx[slot] = (int32_t)u;
-            if (w && tw) tw[slot] = w[e];
-            if (perm) perm[slot] = e;
+#pragma omp parallel
+    {
+        int64_t lo = 0, hi = n;
+        gg_thread_range(n, &lo, &hi);
+        for (int64_t u = 0; u < n; ++u) {
+            for (int64_t e = off[u]; e < off[u + 1]; ++e) {
+                const int32_t v = idx[e];
+                if (v < lo || v >= hi) continue;
+                const int64_t slot = cnt[v]++;
+                tidx[slot] = (int32_t)u;
+                if (w && tw) tw[slot] = w[e];
+                if (perm) perm[slot] = e;
+            }
         }
     }
     free(cnt);
