@@ -53,6 +53,7 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--quiet", action="store_true")
     p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-legs", action="store_true", help="skip the per-configuration push/pull legs")
     p.add_argument("--only", choices=["pr_pull", "pr_push", "bfs", "batched", "sssp", "tc", "pr_fe", "bc"], default=None,
                    help="profiling case: run only this part (fixed --sweeps for PageRank), no contract line")
     p.add_argument("--sweeps", type=int, default=4)
@@ -428,11 +429,181 @@ def run_ours(args, dist: Dist):
            "gpu_launches": launches, "kernels": kernels[:14], "clocks": clk}
     if not args.no_e2e:
         out["e2e"] = run_e2e(args, g, srcs, dist, tuned_opts)
+    if not args.no_legs:
+        out["legs"] = run_legs(args, g, srcs, tuned_opts)
     if not args.no_batched:
         out["batched"] = run_batched(args)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(g, srcs, args)
     return out
+
+
+# ------------------------------------------------------------------ per-config legs (push against pull)
+
+def pr_sweep_bytes(g, mode: int, weighted: bool = False) -> int:
+    """Compulsory bytes of one PageRank sweep.  Pull: CSC indices, offsets, c
+    read, y written, x read for the residual, inv_deg read, c' written = 4m +
+    28n (+8).  Push: CSR indices, offsets, c read, y initialised, residual (x and
+    y read) = 4m + 24n (+8); its m updates are L2 reductions, not HBM traffic.
+    Weighted sweeps also read one float per edge."""
+    base = 4 * g.m + (28 if mode == 1 else 24) * g.n + 8
+    return base + (4 * g.m if weighted else 0)
+
+
+def _events_ms(fn, repeats: int) -> list:
+    """CUDA-event time of each of `repeats` calls of fn on the current stream."""
+    import torch
+
+    out = []
+    for _ in range(repeats):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def pr_leg(gp, g, G, mode: int, sweeps: int, peak: float, repeats: int = 3, tol: float = 0.0, weighted=False):
+    """PageRank in one direction: CUDA-event time of the call (host polls
+    included) and the library's per-kernel device time, GTEPS (m per sweep) and
+    the fraction of the measured HBM peak on the compulsory bytes."""
+    import torch
+
+    out = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    res = {}
+    gp.pagerank(G, mode, 0.85, sweeps, tol, out=out)  # warm-up (workspace, hot sets)
+    gp.profile_read(reset=True)
+    gp.profile_enable(True)
+    ms = _events_ms(lambda: res.update(gp.pagerank(G, mode, 0.85, sweeps, tol, out=out)[1]), repeats)
+    gp.profile_enable(False)
+    kt = gp.profile_read(reset=True)
+    k = res["iters_done"]
+    kms = sum(x[2] for x in kt) / repeats
+    by = pr_sweep_bytes(g, mode, weighted) * k
+    t = statistics.median(ms)
+    return {"sweeps": k, "ms": round(t, 3), "gteps": round(g.m * k / t / 1e6, 2),
+            "hbm_frac": round(by / (t * 1e-3) / 1e9 / peak, 4), "kernel_ms": round(kms, 3),
+            "kernel_hbm_frac": round(by / (kms * 1e-3) / 1e9 / peak, 4) if kms else None,
+            "bytes_per_sweep": pr_sweep_bytes(g, mode, weighted), "converged": bool(res["converged"])}
+
+
+def bfs_leg(gp, g, G, srcs, mode: int, peak: float, undirected: bool, repeats: int = 3):
+    """Searches from every source in one direction mode, enqueued back to back
+    (statistics from a first, untimed pass).  GTEPS: undirected edges of the
+    reached component (Graph500) or, for a directed graph, out-edges of the
+    reached vertices, over the time; also the adjacency entries examined per
+    second and the fraction of the HBM peak on the per-level compulsory bytes."""
+    import torch
+
+    n = g.n
+    level = torch.empty(n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    n_in = int(np.count_nonzero(np.diff(g.csc_off)))
+    edges = examined = by = 0.0
+    levels = switches = 0
+    for s in srcs:
+        _, _, st = gp.bfs(G, int(s), mode, level=level, parent=parent)
+        edges += st["edges_reached"] / (2 if undirected else 1)
+        examined += st["edges_examined"]
+        levels += st["levels"]
+        switches += st["switches"]
+        seen = 0
+        fr = st["frontier"] + [0]
+        for L, d in enumerate(st["direction"]):
+            seen += fr[L]
+            by += bfs_level_bytes(n, d, fr[L], st["examined"][L], n_in - seen, fr[L + 1])[1]
+
+    def run():
+        for s in srcs:
+            gp.bfs(G, int(s), mode, level=level, parent=parent, want_stats=False)
+
+    t = statistics.median(_events_ms(run, repeats))
+    return {"sources": len(srcs), "ms_per_search": round(t / len(srcs), 4), "gteps": round(edges / t / 1e6, 2),
+            "examined_per_s_g": round(examined / t / 1e6, 2), "levels_per_search": round(levels / len(srcs), 2),
+            "switches_per_search": round(switches / len(srcs), 2),
+            "hbm_frac": round(by / (t * 1e-3) / 1e9 / peak, 4)}
+
+
+def run_legs(args, g2, srcs2, tuned_opts):
+    """The metric's push-against-pull comparison on every configuration that
+    fits one GPU, outside the timed step (each leg timed on its own):
+      C1  R-MAT scale 14 (seed 1): PageRank push and pull, exactly 20 sweeps
+          from 1/n; BFS from vertex 0 top-down, bottom-up and switching;
+      C2  R-MAT scale 22: BFS from the 64 step sources forced top-down,
+          forced bottom-up and switching;
+      C3  directed Erdos-Renyi G(2^24, 16*2^24 draws) (seed 3): PageRank pull
+          and push, 20 sweeps; BFS top-down and bottom-up from 16 sources with
+          out-degree > 0 (seed 4);
+      C5  weighted R-MAT scale 20 (seed 8, weights U(0,1] seed 9, normalised
+          per source): forward PageRank to L1 tol 1e-10 (cap 300) and the
+          adjoint for L = g.x, g ~ N(0,1) (seed 10), to the same tolerance."""
+    import torch
+
+    import graphgen as gg
+    import paper_2010_16012_gb300 as gp
+
+    peak, _ = measured_peak_gbs()
+    legs = {}
+    # C2: forced directions from the step's sources
+    G = gp.Graph.from_graphgen(g2)
+    G.set_options(**tuned_opts)
+    legs["c2_bfs"] = {name: bfs_leg(gp, g2, G, srcs2, mode, peak, True, repeats=2)
+                      for name, mode in (("top_down", gp.PUSH), ("bottom_up", gp.PULL), ("auto", gp.AUTO))}
+    G.free()
+    # C1
+    t = time.time()
+    g1 = gg.rmat(14, 16, seed=1)
+    G = gp.Graph.from_graphgen(g1)
+    gp.autotune(G, gp.TUNE_ALL, sources=np.array([0], dtype=np.int32))
+    c1 = {"n": g1.n, "m": g1.m}
+    for name, mode in (("pr_pull", gp.PULL), ("pr_push", gp.PUSH)):
+        c1[name] = pr_leg(gp, g1, G, mode, 20, peak, repeats=5)
+    src0 = np.array([0] * 20, dtype=np.int32)  # 20 searches from vertex 0, back to back
+    c1["bfs_v0"] = {name: bfs_leg(gp, g1, G, src0, mode, peak, True)
+                    for name, mode in (("top_down", gp.PUSH), ("bottom_up", gp.PULL), ("auto", gp.AUTO))}
+    G.free()
+    legs["c1_rmat14"] = c1
+    log(f"[bench] leg C1 done ({time.time() - t:.1f}s)")
+    # C3
+    t = time.time()
+    g3 = gg.erdos_renyi(1 << 24, 16 << 24, seed=3)
+    G = gp.Graph.from_graphgen(g3)
+    s3 = gg.pick_vertices(g3, 16, seed=4)
+    gp.autotune(G, gp.TUNE_ALL, sources=s3[:4])
+    c3 = {"n": g3.n, "m": g3.m, "gen_s": round(time.time() - t, 1)}
+    for name, mode in (("pr_pull", gp.PULL), ("pr_push", gp.PUSH)):
+        c3[name] = pr_leg(gp, g3, G, mode, 20, peak)
+    c3["bfs"] = {name: bfs_leg(gp, g3, G, s3, mode, peak, False, repeats=2)
+                 for name, mode in (("top_down", gp.PUSH), ("bottom_up", gp.PULL), ("auto", gp.AUTO))}
+    G.free()
+    del g3
+    legs["c3_er24"] = c3
+    log(f"[bench] leg C3 done ({time.time() - t:.1f}s)")
+    # C5
+    t = time.time()
+    g5 = gg.rmat(20, 16, seed=8).with_weights(9)
+    G = gp.Graph.from_graphgen(g5)
+    gvec = torch.from_numpy(np.random.default_rng(10).normal(size=g5.n).astype(np.float32)).cuda()
+    fwd = pr_leg(gp, g5, G, gp.PULL, 300, peak, tol=1e-10, weighted=True)
+    x, _ = gp.pagerank(G, gp.PULL, 0.85, 300, 1e-10)
+    res = {}
+    gp.pagerank_backward(G, x, gvec, iters=300, tol=1e-10)
+    ms = statistics.median(_events_ms(lambda: res.update(gp.pagerank_backward(G, x, gvec, iters=300,
+                                                                                tol=1e-10)[2]), 3))
+    k = res["iters_done"]
+    # per adjoint iteration one weighted transposed sweep; then dL/dP over every
+    # edge (indices read, gradient written) and dL/ds
+    by = pr_sweep_bytes(g5, gp.PULL, True) * k + 8 * g5.m + 8 * (g5.n + 1) + 12 * g5.n
+    legs["c5_adjoint_rmat20"] = {
+        "n": g5.n, "m": g5.m, "forward": fwd,
+        "backward": {"iters": k, "converged": bool(res["converged"]), "ms": round(ms, 3),
+                     "gteps": round(g5.m * k / ms / 1e6, 2), "hbm_frac": round(by / (ms * 1e-3) / 1e9 / peak, 4)}}
+    G.free()
+    log(f"[bench] leg C5 done ({time.time() - t:.1f}s)")
+    return legs
 
 
 def run_e2e(args, g, srcs, dist: Dist, tuned_opts=None):
@@ -495,7 +666,7 @@ def run_e2e(args, g, srcs, dist: Dist, tuned_opts=None):
 
     step()
     torch.cuda.synchronize()
-    steps = max(1, min(args.steps, 3))
+    steps = args.steps
     dist.barrier()
     t0 = time.perf_counter()
     tot = 0.0
@@ -532,15 +703,42 @@ def oracle_sample(g, srcs, O, sweeps: int, nsrc: int, threads: int):
 
 
 def cpu_baseline(g, srcs, args):
+    """The oracle on the host cores, on a bounded sample of the step's workload
+    (the headline figure, GTEPS over the whole sample), with per-operation
+    figures: the pull sweep on all cores and on one thread, the push sweep and
+    the FIFO BFS on one thread (the oracle's push and BFS are sequential), on
+    the step's graph and on R-MAT scale 14."""
+    import graphgen as gg
     import oracle
 
     threads = oracle.max_threads()
     O = oracle.OracleGraph.from_graph(g)
     sweeps, nsrc = 8, 2
     edges, sec = oracle_sample(g, srcs, O, sweeps, nsrc, threads)
+    per_op = {}
+    for gname, gg_, O_, s_ in (("rmat22", g, O, srcs[:2]), ("rmat14", None, None, None)):
+        if gg_ is None:
+            gg_ = gg.rmat(14, 16, seed=1)
+            O_ = oracle.OracleGraph.from_graph(gg_)
+            s_ = np.array([0], dtype=np.int32)
+        reps = 1 if gname == "rmat22" else 20
+        for key, var, th, k in (("pull_sweep_all_cores", oracle.PULL, threads, 4),
+                                ("pull_sweep_1_thread", oracle.PULL, 1, 1), ("push_sweep_1_thread", oracle.PUSH, 1, 1)):
+            t = time.perf_counter()
+            for _ in range(reps):
+                O_.pagerank(var, 0.85, iters=k, nthreads=th)
+            per_op[f"{gname}_{key}_gteps"] = round(gg_.m * k * reps / (time.perf_counter() - t) / 1e9, 5)
+        t = time.perf_counter()
+        be = 0.0
+        for _ in range(reps):
+            for src in s_:
+                lv, _ = O_.bfs(int(src))
+                be += float(gg_.out_degree()[lv >= 0].sum()) / 2
+        per_op[f"{gname}_bfs_fifo_1_thread_gteps"] = round(be / (time.perf_counter() - t) / 1e9, 5)
     return {"value": round(edges / sec / 1e9, 5), "unit": "GTEPS", "cores": threads, "kind": "oracle",
             "sample": f"{sweeps} pull PageRank sweeps ({threads} threads) + 1 push sweep (1 thread) + FIFO BFS "
-                      f"from {nsrc} of the sources, on the full scale-{args.scale} graph; {sec:.1f} s"}
+                      f"from {nsrc} of the sources, on the full scale-{args.scale} graph; {sec:.1f} s",
+            "per_op": per_op}
 
 
 def run_reference(args, dist: Dist):
@@ -592,7 +790,7 @@ def run_batched(args, graphs_scales=None):
     import graphgen as gg
     import paper_2010_16012_gb300 as gp
 
-    K, NSRC, SAMPLE = 256, 64, 4
+    K, NSRC, SAMPLE, REPS = 256, 64, 16, 3
     graphs, scales = graphs_scales or batched_workload()
     G = [gp.Graph.from_graphgen(g) for g in graphs]
     B = gp.Batch(G, k_ppr=K)
@@ -601,12 +799,15 @@ def run_batched(args, graphs_scales=None):
     B.ppr(seeds, iters=1000, tol=1e-6)  # captures the CUDA graph
     B.msbfs(srcs)
     torch.cuda.synchronize()
-    t = time.perf_counter()
-    outs, done, st = B.ppr(seeds, iters=1000, tol=1e-6)
-    ppr_batched_s = time.perf_counter() - t
-    t = time.perf_counter()
-    louts, bst = B.msbfs(srcs)
-    bfs_batched_s = time.perf_counter() - t
+    tp, tb = [], []
+    for _ in range(REPS):
+        t = time.perf_counter()
+        outs, done, st = B.ppr(seeds, iters=1000, tol=1e-6)
+        tp.append(time.perf_counter() - t)
+        t = time.perf_counter()
+        louts, bst = B.msbfs(srcs)
+        tb.append(time.perf_counter() - t)
+    ppr_batched_s, bfs_batched_s = statistics.median(tp), statistics.median(tb)
     # one at a time, on a sample
     e = [torch.zeros(g.n, device="cuda") for g in graphs]
     x = [torch.empty(g.n, device="cuda") for g in graphs]
@@ -620,20 +821,23 @@ def run_batched(args, graphs_scales=None):
     for i in range(len(graphs)):
         for j in range(SAMPLE):
             ev[i][j][int(seeds[i, j])] = 1.0
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    for i in range(len(graphs)):
-        for j in range(SAMPLE):
-            gp.pagerank(G[i], gp.PULL, 0.85, 1000, 1e-6, personalization=ev[i][j], out=xs[i][j])
-    torch.cuda.synchronize()
-    ppr_serial_s = (time.perf_counter() - t) * K / SAMPLE
+    ts, tsb = [], []
+    for _ in range(REPS):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for i in range(len(graphs)):
+            for j in range(SAMPLE):
+                gp.pagerank(G[i], gp.PULL, 0.85, 1000, 1e-6, personalization=ev[i][j], out=xs[i][j])
+        torch.cuda.synchronize()
+        ts.append((time.perf_counter() - t) * K / SAMPLE)
+        t = time.perf_counter()
+        for i in range(len(graphs)):
+            for j in range(SAMPLE):
+                gp.bfs(G[i], int(srcs[i, j]), gp.AUTO, level=lv[i], want_parent=False)
+        torch.cuda.synchronize()
+        tsb.append((time.perf_counter() - t) * NSRC / SAMPLE)
+    ppr_serial_s, bfs_serial_s = statistics.median(ts), statistics.median(tsb)
     max_err = max(float((xs[i][j] - outs[i][:, j]).abs().max()) for i in range(len(graphs)) for j in range(SAMPLE))
-    t = time.perf_counter()
-    for i in range(len(graphs)):
-        for j in range(SAMPLE):
-            gp.bfs(G[i], int(srcs[i, j]), gp.AUTO, level=lv[i], want_parent=False)
-    torch.cuda.synchronize()
-    bfs_serial_s = (time.perf_counter() - t) * NSRC / SAMPLE
     nvec = len(graphs) * K
     edges = sum(g.m * int(done[i].sum()) for i, g in enumerate(graphs))
     B.free()
@@ -647,7 +851,9 @@ def run_batched(args, graphs_scales=None):
             "bfs_sources": len(graphs) * NSRC, "bfs_batched_ms": round(bfs_batched_s * 1e3, 2),
             "bfs_serial_ms_extrapolated": round(bfs_serial_s * 1e3, 1),
             "bfs_speedup": round(bfs_serial_s / bfs_batched_s, 2), "bfs_levels": bst["levels"],
-            "serial_sample_per_graph": SAMPLE}
+            "serial_sample_per_graph": SAMPLE, "repeats": REPS,
+            "ppr_batched_ms_all": [round(x * 1e3, 2) for x in tp],
+            "ppr_serial_ms_all": [round(x * 1e3, 1) for x in ts]}
 
 
 def run_only(args):

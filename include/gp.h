@@ -288,6 +288,9 @@ int gp_graph_set_weights(gp_graph *g, const float *csr_w, const float *csc_w, vo
 
 /* ------------------------------------------------------------------ BFS */
 
+/* Per-level statistics are kept for the first GP_BFS_MAX_LEVELS levels; a
+ * deeper search runs to the end all the same (levels, reached and the edge
+ * counts cover every level). */
 #define GP_BFS_MAX_LEVELS 512
 
 typedef struct gp_bfs_stats {
@@ -334,7 +337,8 @@ int gp_bfs(const gp_graph *g, int32_t src, int mode, int32_t *level_out, int32_t
 
 /* gp_bfs with the direction of every level chosen by the caller:
  * dirs[i] (GP_PUSH or GP_PULL) is used for level i, dirs[ndirs-1] for all
- * later levels.  Levels do not depend on the choice. */
+ * later levels; ndirs may exceed GP_BFS_MAX_LEVELS.  Levels do not depend on
+ * the choice. */
 int gp_bfs_directed(const gp_graph *g, int32_t src, const int8_t *dirs, int ndirs, int32_t *level_out,
                     int32_t *parent_out, gp_bfs_stats *stats, void *stream);
 

@@ -591,6 +591,7 @@ static int ensure_bfs_work(gp_graph *g, cudaStream_t s) {
     int8_t *d = nullptr;
     GP_TRY(w.mem.alloc(d, GP_BFS_MAX_LEVELS, s));
     w.dirs = d;
+    w.dirs_cap = GP_BFS_MAX_LEVELS;
     int per_sm = 0;
     GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs_persistent, BFS_THREADS, 0));
     if (per_sm < 1) return set_error(GP_ERR_UNSUPPORTED, "BFS kernel does not fit on an SM");
@@ -668,10 +669,16 @@ static int bfs_run(const gp_graph *gc, int32_t src, int mode, const int8_t *dirs
     R.summary = (BfsSummary *)w.summary;
     R.sync = (GridSync *)w.sync;
     if (dirs) {
-        const int nd = std::min(ndirs, GP_BFS_MAX_LEVELS);
-        GP_CUDA(cudaMemcpyAsync(w.dirs, dirs, nd, cudaMemcpyHostToDevice, s));
+        // every given direction is used (level i takes dirs[i]), however deep the search
+        if (ndirs > w.dirs_cap) {
+            int8_t *d = nullptr;
+            GP_TRY(w.mem.alloc(d, (size_t)ndirs, s));
+            w.dirs = d;
+            w.dirs_cap = ndirs;
+        }
+        GP_CUDA(cudaMemcpyAsync(w.dirs, dirs, (size_t)ndirs, cudaMemcpyHostToDevice, s));
         R.dirs = (const int8_t *)w.dirs;
-        R.ndirs = nd;
+        R.ndirs = ndirs;
     }
     GP_CUDA(cudaMemsetAsync(w.sync, 0, sizeof(GridSync), s));
     {

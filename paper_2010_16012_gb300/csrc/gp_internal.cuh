@@ -161,6 +161,7 @@ struct BfsWork {
     void *summary = nullptr;                 // search summary (device)
     void *sync = nullptr;                    // grid barrier word
     int8_t *dirs = nullptr;                  // forced directions (device copy)
+    int dirs_cap = 0;                        // entries `dirs` holds
     int grid = 0;                            // blocks of the cooperative launch
     cudaEvent_t done_ev = nullptr;           // end of the last asynchronous search
     bool pending = false;                    // its barrier status not yet checked

@@ -182,3 +182,63 @@ def test_level_times_reported(gp):
     assert len(st["level_us"]) == st["levels"] > 1
     assert all(t > 0 for t in st["level_us"]) and st["init_us"] > 0
     assert st["init_us"] + sum(st["level_us"]) <= st["ms"] * 1e3 * 1.05 + 5.0
+
+
+def _grid(r, c):
+    v = np.arange(r * c, dtype=np.int32).reshape(r, c)
+    u = np.concatenate([v[:, :-1].ravel(), v[:-1, :].ravel()])
+    w = np.concatenate([v[:, 1:].ravel(), v[1:, :].ravel()])
+    return gg.from_edges(r * c, u, w, symmetrize=True, name=f"grid{r}x{c}")
+
+
+DEEP = [lambda: gg.path(2000), lambda: gg.path(1500, directed=True), lambda: _grid(60, 60),
+        lambda: gg.cycle(1200)]
+
+
+@pytest.mark.parametrize("gi", range(len(DEEP)))
+def test_deeper_than_the_level_statistics(gp, gi):
+    """Searches of more than GP_BFS_MAX_LEVELS levels (paths of 1500-2000
+    vertices, a 60x60 grid of depth 118 from a corner and 60 from the centre, a
+    directed 1200-cycle): every mode and a forced direction sequence longer
+    than the statistics arrays, levels bit-exact, parents valid, and the level
+    count beyond the statistics reported."""
+    g = DEEP[gi]()
+    G = gp.Graph.from_graphgen(g, validate=True)
+    O = oracle.OracleGraph.from_graph(g)
+    srcs = [0, g.n // 2 + (30 if gi == 2 else 0)]
+    rng = np.random.default_rng(gi)
+    for src in srcs:
+        ref, _ = O.bfs(src)
+        depth = int(ref.max()) + 1
+        for mode in MODES:
+            lv, pa, st = gp.bfs(G, src, mode)
+            check(g, O, src, lv, pa)
+            assert st["levels"] == depth, (mode, st["levels"], depth)
+            assert st["reached"] == int((ref >= 0).sum())
+        dirs = rng.integers(0, 2, size=depth + 40).astype(np.int8)
+        lv, pa, st = gp.bfs(G, src, dirs=dirs)
+        check(g, O, src, lv, pa)
+        k = min(depth, gp.BFS_MAX_LEVELS)
+        assert list(st["direction"][:k]) == list(dirs[:k])
+        # the oracle's level-synchronous search with the same sequence
+        ref2, _, used = O.bfs_levelsync(src, dirs=dirs)
+        assert np.array_equal(to_np(lv), ref2)
+
+
+def test_forced_directions_beyond_512_levels_are_used(gp):
+    """On a 1500-vertex path from vertex 0, levels 600-1499 forced to bottom-up
+    scan in-edges, top-down ones out-edges: the edges examined tell which
+    direction each level beyond the statistics took."""
+    g = gg.path(1500)
+    G = gp.Graph.from_graphgen(g)
+    O = oracle.OracleGraph.from_graph(g)
+    depth = 1500
+    td = np.zeros(depth, dtype=np.int8)
+    mixed = td.copy()
+    mixed[600:] = 1
+    _, _, s_td = gp.bfs(G, 0, dirs=td)
+    lv, pa, s_mx = gp.bfs(G, 0, dirs=mixed)
+    check(g, O, 0, lv, pa)
+    # a top-down level of a path examines its frontier's 1-2 out-edges; a
+    # bottom-up level examines the in-edges of every unvisited vertex until a hit
+    assert s_mx["edges_examined"] > s_td["edges_examined"] + 100000, (s_mx["edges_examined"], s_td["edges_examined"])
