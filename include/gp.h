@@ -172,7 +172,10 @@ typedef struct gp_options {
     float bfs_alpha;          /* top-down -> bottom-up when m_f > m_u / alpha */
     float bfs_beta;           /* bottom-up -> top-down when n_f < n / beta (frontier shrinking) */
     int32_t push_fp64_accum;  /* push PageRank: 1 = accumulate the scattered updates with FP64
-                                 atomics (default; ranks stay FP32), 0 = FP32 atomics */
+                                 atomics (ranks stay FP32), 0 = FP32 atomics, -1 = by size
+                                 (default): FP64 unless its 8n-byte accumulator exceeds half
+                                 the L2 cache and no vertex takes more than 4096 updates per
+                                 sweep (then FP32, whose array stays in L2) */
     int32_t pull_hot_slots;   /* pull PageRank: contributions of this many highest out-degree
                                  vertices are served from shared memory (0 = off, <= 49152) */
     int32_t push_hot_slots;   /* push PageRank: updates to this many highest in-degree vertices are
@@ -229,6 +232,15 @@ typedef struct gp_pr_stats {
     double residual;    /* L1 norm (FP64) of the change made by the last sweep */
     float ms;           /* device time of the call by CUDA events (0 when stats is NULL) */
     int32_t converged;  /* 1 if residual < tol (or tol == 0 and all sweeps ran) */
+    /* Push sweeps' scattered updates, summed over the sweeps performed (all 0
+     * for pull, which issues no atomics; Table 1's atomics row).  Every edge
+     * update of a push sweep is exactly one of: an atomic sent to L2
+     * (push_updates_l2), an atomic into a block's shared-memory accumulator of a
+     * hot vertex (push_updates_shared), or folded into another lane's update for
+     * the same vertex inside a warp (push_updates_merged); the three sum to
+     * m * iters_done.  push_flush_l2 counts the L2 atomics that flush the
+     * shared accumulators (one per touched hot vertex per block and sweep). */
+    int64_t push_updates_l2, push_updates_shared, push_updates_merged, push_flush_l2;
 } gp_pr_stats;
 
 /*
@@ -239,8 +251,8 @@ typedef struct gp_pr_stats {
  * FP64; iteration stops at the first sweep where it is below tol, or after
  * `iters` sweeps (then GP_ERR_NOT_CONVERGED, with the last iterate written).
  * tol = 0 runs exactly `iters` sweeps and returns GP_OK.
- *   mode            GP_PUSH (scatter with atomics: FP64 reductions in L2 by default,
- *                   FP32 atomicAdd with push_fp64_accum = 0), GP_PULL (gather, no
+ *   mode            GP_PUSH (scatter with atomics: FP64 reductions in L2, or FP32
+ *                   atomicAdd, as push_fp64_accum says), GP_PULL (gather, no
  *                   atomics) or GP_AUTO.
  *   damping         in (0, 1).
  *   iters           >= 1.

@@ -58,7 +58,9 @@ class gp_graph_info(ctypes.Structure):
 
 class gp_pr_stats(ctypes.Structure):
     _fields_ = [("iters_done", ctypes.c_int32), ("mode_used", ctypes.c_int32), ("residual", ctypes.c_double),
-                ("ms", ctypes.c_float), ("converged", ctypes.c_int32)]
+                ("ms", ctypes.c_float), ("converged", ctypes.c_int32), ("push_updates_l2", ctypes.c_int64),
+                ("push_updates_shared", ctypes.c_int64), ("push_updates_merged", ctypes.c_int64),
+                ("push_flush_l2", ctypes.c_int64)]
 
 
 class gp_bfs_stats(ctypes.Structure):
@@ -330,7 +332,9 @@ def pagerank(g: Graph, mode=PULL, damping=0.85, iters=20, tol=0.0, personalizati
     _check(load().gp_pagerank(g.handle, int(mode), float(damping), int(iters), float(tol), _ptr(personalization),
                               _ptr(x0), _ptr(out), ctypes.byref(st), _stream_ptr(stream)), "gp_pagerank", allow)
     return out, {"iters_done": st.iters_done, "mode_used": st.mode_used, "residual": st.residual, "ms": st.ms,
-                 "converged": bool(st.converged)}
+                 "converged": bool(st.converged), "push_updates_l2": st.push_updates_l2,
+                 "push_updates_shared": st.push_updates_shared, "push_updates_merged": st.push_updates_merged,
+                 "push_flush_l2": st.push_flush_l2}
 
 
 def pagerank_backward(g: Graph, ranks, grad_ranks, mode=PULL, damping=0.85, iters=1000, tol=1e-7,

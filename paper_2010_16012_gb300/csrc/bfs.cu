@@ -41,7 +41,8 @@ struct BfsCtr {
     unsigned long long mf;        // sum of out-degrees of the frontier
     unsigned long long mu_dec;    // sum of in-degrees of the newly visited vertices
     unsigned long long examined;  // edges scanned by the level
-    unsigned long long pad[2];
+    unsigned long long deferred;  // bottom-up: hubs whose first in-edges held no frontier vertex
+    unsigned long long pad;
 };
 
 struct BfsArgs {
@@ -51,6 +52,9 @@ struct BfsArgs {
     const int32_t *push_rank;   // [n] rank among big out-degree vertices, -1 if light
     const int64_t *push_cstart;
     const Chunk *push_chunks;
+    const Chunk *pull_chunks;   // in-edge chunks of the vertices above the pull light limit
+    int64_t pull_nchunks;
+    int64_t bu_probe;           // bottom-up: in-edges a lane probes before deferring a hub
     int32_t *level, *parent;    // parent may be nullptr
     const int32_t *queue_cur;
     int32_t *queue_next;
@@ -109,18 +113,32 @@ __device__ __forceinline__ bool td_claim(const BfsArgs &a, int32_t w, int32_t u)
     return true;
 }
 
+// The five counters of a block summed in one pass (one shared-memory round
+// and two block barriers), then added to the next level's record.
 __device__ void flush_counters(const BfsArgs &a, unsigned long long nf, unsigned long long mf, unsigned long long mu,
-                               unsigned long long ex) {
-    __shared__ unsigned long long sm[32];
-    nf = block_sum(nf, sm);
-    mf = block_sum(mf, sm);
-    mu = block_sum(mu, sm);
-    ex = block_sum(ex, sm);
-    if (threadIdx.x == 0) {
-        if (nf) atomicAdd(&a.nxt->nf, nf);
-        if (mf) atomicAdd(&a.nxt->mf, mf);
-        if (mu) atomicAdd(&a.nxt->mu_dec, mu);
-        if (ex) atomicAdd(&a.nxt->examined, ex);
+                               unsigned long long ex, unsigned long long deferred = 0) {
+    constexpr int K = 5;
+    __shared__ unsigned long long sm[K][32];
+    unsigned long long v[K] = {nf, mf, mu, ex, deferred};
+#pragma unroll
+    for (int i = 0; i < K; ++i) v[i] = warp_sum(v[i]);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane_id() == 0) {
+#pragma unroll
+        for (int i = 0; i < K; ++i) sm[i][w] = v[i];
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int i = 0; i < K; ++i) v[i] = warp_sum(lane_id() < nw ? sm[i][lane_id()] : 0ull);
+        if (lane_id() == 0) {
+            if (v[0]) atomicAdd(&a.nxt->nf, v[0]);
+            if (v[1]) atomicAdd(&a.nxt->mf, v[1]);
+            if (v[2]) atomicAdd(&a.nxt->mu_dec, v[2]);
+            if (v[3]) atomicAdd(&a.nxt->examined, v[3]);
+            if (v[4]) atomicAdd(&a.nxt->deferred, v[4]);
+        }
     }
 }
 
@@ -211,6 +229,13 @@ constexpr int BFS_WARPS = GP_BFS_WARPS;  // warps per block of the persistent ke
 #define GP_BU_SCAN 4
 #endif
 constexpr int BU_SCAN = GP_BU_SCAN;  // in-edges a bottom-up lane checks per step
+// A candidate with more in-edges than this is a hub: its lane probes only that
+// many, and a hub with no frontier vertex among them is finished by the chunk
+// pass (one lane walking a hub's whole in-list would hold up its warp).
+#ifndef GP_BU_PROBE
+#define GP_BU_PROBE 64
+#endif
+constexpr int64_t BU_PROBE = GP_BU_PROBE;
 
 __device__ void bfs_bottomup_step(const BfsArgs &a) {
     __shared__ uint32_t s_found[BFS_WARPS][32];
@@ -218,7 +243,7 @@ __device__ void bfs_bottomup_step(const BfsArgs &a) {
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nwords = (a.n + 31) >> 5;
-    unsigned long long nf = 0, mf = 0, mu = 0, ex = 0;
+    unsigned long long nf = 0, mf = 0, mu = 0, ex = 0, deferred = 0;
     for (int64_t base = warp * 32; base < nwords; base += nwarps * 32) {
         const int64_t wd = base + lane;
         const uint32_t cand = wd < nwords ? a.unvis[wd] : 0u;
@@ -258,15 +283,20 @@ __device__ void bfs_bottomup_step(const BfsArgs &a) {
             locate(r + 32 + lane, kn, bitn, bn, en);
             if (r + lane < total) {
                 const int64_t v = (base + k) * 32 + bit;
+                // a hub's lane probes only its first bu_probe in-edges; if none is in
+                // the frontier the hub is deferred to the chunk pass (bfs_bottomup_hubs)
+                const bool hub = e - b > a.bu_probe;
+                const int64_t e1 = hub ? b + a.bu_probe : e;
+                bool found = false;
                 // BU_SCAN in-edges per step: their bitmap probes are independent
-                for (int64_t j = b; j < e; j += BU_SCAN) {
+                for (int64_t j = b; j < e1; j += BU_SCAN) {
                     int32_t u[BU_SCAN];
                     bool hit[BU_SCAN];
 #pragma unroll
-                    for (int q = 0; q < BU_SCAN; ++q) u[q] = j + q < e ? __ldg(a.csc_idx + j + q) : 0;
+                    for (int q = 0; q < BU_SCAN; ++q) u[q] = j + q < e1 ? __ldg(a.csc_idx + j + q) : 0;
 #pragma unroll
                     for (int q = 0; q < BU_SCAN; ++q)
-                        hit[q] = j + q < e && ((a.bits_cur[u[q] >> 5] >> (u[q] & 31)) & 1u);
+                        hit[q] = j + q < e1 && ((a.bits_cur[u[q] >> 5] >> (u[q] & 31)) & 1u);
                     int first = -1;
 #pragma unroll
                     for (int q = BU_SCAN - 1; q >= 0; --q)
@@ -283,10 +313,12 @@ __device__ void bfs_bottomup_step(const BfsArgs &a) {
                         nf += 1;
                         mf += (unsigned long long)(a.csr_off == a.csc_off ? e - b : a.csr_off[v + 1] - a.csr_off[v]);
                         mu += (unsigned long long)(e - b);
+                        found = true;
                         break;
                     }
-                    ex += (unsigned long long)(e - j < BU_SCAN ? e - j : BU_SCAN);
+                    ex += (unsigned long long)(e1 - j < BU_SCAN ? e1 - j : BU_SCAN);
                 }
+                if (hub && !found) ++deferred;
             }
             k = kn;
             bit = bitn;
@@ -300,6 +332,83 @@ __device__ void bfs_bottomup_step(const BfsArgs &a) {
             a.unvis[wd] = cand & ~fw;
         }
         __syncwarp();
+    }
+    flush_counters(a, nf, mf, mu, ex, deferred);
+}
+
+// Second pass of a bottom-up level, run only when some hub was deferred: the
+// in-edge chunks (chunk_edges each) of every hub still unvisited are scanned by
+// warps across the whole grid, so a hub's in-list is spread over many warps.
+// Each chunk stops at its first frontier vertex, or when another chunk has
+// claimed the hub; chunks of one hub settle the claim with one compare-and-swap
+// on its level (the owner-only rule applied to the hub's set of chunks).
+constexpr int BU_WARP_UNROLL = 8;
+
+__device__ void bfs_bottomup_hubs(const BfsArgs &a) {
+    const int lane = lane_id();
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    volatile int32_t *vlevel = a.level;
+    unsigned long long nf = 0, mf = 0, mu = 0, ex = 0;
+    for (int64_t base = warp * 32; base < a.pull_nchunks; base += nwarps * 32) {
+        const int64_t j = base + lane;
+        Chunk ch;
+        ch.beg = 0;
+        ch.len = 0;
+        ch.v = 0;
+        bool need = false;
+        if (j < a.pull_nchunks) {
+            ch = a.pull_chunks[j];
+            if (vlevel[ch.v] == -1) need = a.csc_off[ch.v + 1] - a.csc_off[ch.v] > a.bu_probe;
+        }
+        for (unsigned nm = __ballot_sync(FULL, need); nm; nm &= nm - 1) {
+            const int hl = __ffs(nm) - 1;
+            const int64_t cb = __shfl_sync(FULL, ch.beg, hl);
+            const int cl = __shfl_sync(FULL, ch.len, hl);
+            const int32_t v = __shfl_sync(FULL, ch.v, hl);
+            int64_t hit = -1;
+            int32_t par = 0;
+            int scanned = 0;
+            for (int i0 = 0; i0 < cl && hit < 0; i0 += 32 * BU_WARP_UNROLL) {
+                int claimed = 0;
+                if (lane == 0 && i0 > 0) claimed = vlevel[v] != -1;
+                if (__shfl_sync(FULL, claimed, 0)) break;  // uniform
+                int32_t u[BU_WARP_UNROLL];
+#pragma unroll
+                for (int q = 0; q < BU_WARP_UNROLL; ++q) {
+                    const int i = i0 + q * 32 + lane;
+                    u[q] = i < cl ? __ldg(a.csc_idx + cb + i) : 0;
+                }
+                unsigned bm[BU_WARP_UNROLL];
+#pragma unroll
+                for (int q = 0; q < BU_WARP_UNROLL; ++q) {
+                    const int i = i0 + q * 32 + lane;
+                    bm[q] = __ballot_sync(FULL, i < cl && ((a.bits_cur[u[q] >> 5] >> (u[q] & 31)) & 1u));
+                }
+#pragma unroll
+                for (int q = 0; q < BU_WARP_UNROLL; ++q) {
+                    if (hit < 0 && bm[q]) {  // uniform: the ballots are the warp's
+                        const int fl = __ffs(bm[q]) - 1;
+                        hit = cb + i0 + q * 32 + fl;
+                        par = __shfl_sync(FULL, u[q], fl);
+                    }
+                }
+                scanned = min(cl, i0 + 32 * BU_WARP_UNROLL);
+            }
+            if (lane == 0) {
+                ex += (unsigned long long)(hit >= 0 ? hit - cb + 1 : scanned);
+                if (hit >= 0 && atomicCAS(a.level + v, -1, a.L + 1) == -1) {
+                    if (a.parent) a.parent[v] = par;
+                    const uint32_t bit = 1u << (v & 31);
+                    atomicOr(a.bits_next + (v >> 5), bit);
+                    atomicAnd(a.unvis + (v >> 5), ~bit);
+                    const int64_t din = a.csc_off[v + 1] - a.csc_off[v];
+                    nf += 1;
+                    mf += (unsigned long long)(a.csr_off == a.csc_off ? din : a.csr_off[v + 1] - a.csr_off[v]);
+                    mu += (unsigned long long)din;
+                }
+            }
+        }
     }
     flush_counters(a, nf, mf, mu, ex);
 }
@@ -422,7 +531,7 @@ __global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(Bfs
     // shared memory: every thread loading the same line would queue tens of
     // thousands of requests on one L2 slice per level
     volatile BfsCtr *vc = (volatile BfsCtr *)R.ctr;
-    __shared__ unsigned long long s_ctr[6];
+    __shared__ unsigned long long s_ctr[7];
     auto read_ctr = [&](int slot) {
         if (threadIdx.x == 0) {
             s_ctr[0] = vc[slot].q_len;
@@ -431,6 +540,7 @@ __global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(Bfs
             s_ctr[3] = vc[slot].mf;
             s_ctr[4] = vc[slot].mu_dec;
             s_ctr[5] = vc[slot].examined;
+            s_ctr[6] = vc[slot].deferred;
         }
         __syncthreads();
     };
@@ -497,6 +607,11 @@ __global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(Bfs
         }
         if (!grid_sync(R.sync, gridDim.x)) return;
         read_ctr(nxt);
+        if (dir == GP_PULL && s_ctr[6] > 0) {  // hubs deferred by the lanes: the chunk pass
+            bfs_bottomup_hubs(a);
+            if (!grid_sync(R.sync, gridDim.x)) return;
+            read_ctr(nxt);
+        }
         const unsigned long long nf2 = s_ctr[2], mf2 = s_ctr[3], mud = s_ctr[4], ex = s_ctr[5];
         q_len = (int64_t)s_ctr[0];
         h_len = (int64_t)s_ctr[1];
@@ -650,6 +765,10 @@ static int bfs_run(const gp_graph *gc, int32_t src, int mode, const int8_t *dirs
     R.base.push_rank = g->push_bins.rank;
     R.base.push_cstart = g->push_bins.cstart;
     R.base.push_chunks = g->push_bins.chunks;
+    R.base.pull_chunks = g->pull_bins.chunks;
+    R.base.pull_nchunks = g->pull_bins.nchunks;
+    // every hub a lane defers has in-edge chunks: the probe is at least the pull light limit
+    R.base.bu_probe = std::max<int64_t>(BU_PROBE, g->pull_bins.light_max);
     R.base.level = level;
     R.base.parent = parent;
     for (int i = 0; i < 2; ++i) {

@@ -177,6 +177,7 @@ struct gp_bc_work;    // betweenness-centrality workspace (bc.cu)
 struct gp_graph {
     int device = 0;
     int num_sms = 0;
+    int64_t l2_bytes = 0;  // the device's L2 cache size
     int64_t n = 0, m = 0;
     bool symmetric = false, weighted = false, normalized = false;
     const int64_t *csr_off = nullptr, *csc_off = nullptr;

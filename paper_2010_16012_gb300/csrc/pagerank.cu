@@ -41,6 +41,10 @@ struct PrStatus {
     double residual;
     int32_t converged;
     int32_t pad;
+    // push scatter, summed over the sweeps of a call: updates sent to L2 as
+    // atomics, added into a block's shared-memory accumulators, and folded into
+    // another lane's update inside a warp; plus the flushes of the shared ones
+    unsigned long long upd_l2, upd_shared, upd_merged, flush_l2;
 };
 
 struct PrArgs {
@@ -133,6 +137,7 @@ __global__ void k_pr_init(int64_t n, const float *x0, const float *cmul, float *
         status->iters_done = 0;
         status->residual = 0.0;
         status->converged = 0;
+        status->upd_l2 = status->upd_shared = status->upd_merged = status->flush_l2 = 0;
     }
 }
 
@@ -333,12 +338,19 @@ __global__ void k_hot_gather(const int32_t *hot_id, int64_t nhot, const float *c
 // updates to the H most updated vertices (encoded in the index array) are
 // summed in the block's shared memory with shared-memory atomics and flushed
 // once per block; only the other updates use global atomics.
+struct PushCount {
+    unsigned l2 = 0, shared = 0, merged = 0, flush = 0;
+};
+
 template <class T, bool HOT>
-__device__ __forceinline__ void scatter_add(T *y, float *sh, int32_t dst, float val) {
-    if (HOT && dst < 0)
+__device__ __forceinline__ void scatter_add(T *y, float *sh, int32_t dst, float val, PushCount &cnt) {
+    if (HOT && dst < 0) {
         atomicAdd(sh + (dst & 0x7fffffff), val);
-    else
+        ++cnt.shared;
+    } else {
         atomicAdd(y + dst, (T)val);
+        ++cnt.l2;
+    }
 }
 
 template <bool W, class T, bool HOT>
@@ -355,6 +367,7 @@ __global__ void __launch_bounds__(1024) k_push_scatter(PrArgs a) {
     T *y = sizeof(T) == 8 ? (T *)a.acc64 : (T *)a.y;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    PushCount cnt;
     // big sources: one warp per chunk of out-edges
     for (int64_t j = warp; j < a.nchunks; j += nwarps) {
         const Chunk ch = a.chunks[j];
@@ -364,12 +377,12 @@ __global__ void __launch_bounds__(1024) k_push_scatter(PrArgs a) {
         int i = lane;
         for (; i + 96 < ch.len; i += 128) {
             const int v0 = __ldg(ip + i), v1 = __ldg(ip + i + 32), v2 = __ldg(ip + i + 64), v3 = __ldg(ip + i + 96);
-            scatter_add<T, HOT>(y, sh_acc, v0, W ? cu * __ldg(wp + i) : cu);
-            scatter_add<T, HOT>(y, sh_acc, v1, W ? cu * __ldg(wp + i + 32) : cu);
-            scatter_add<T, HOT>(y, sh_acc, v2, W ? cu * __ldg(wp + i + 64) : cu);
-            scatter_add<T, HOT>(y, sh_acc, v3, W ? cu * __ldg(wp + i + 96) : cu);
+            scatter_add<T, HOT>(y, sh_acc, v0, W ? cu * __ldg(wp + i) : cu, cnt);
+            scatter_add<T, HOT>(y, sh_acc, v1, W ? cu * __ldg(wp + i + 32) : cu, cnt);
+            scatter_add<T, HOT>(y, sh_acc, v2, W ? cu * __ldg(wp + i + 64) : cu, cnt);
+            scatter_add<T, HOT>(y, sh_acc, v3, W ? cu * __ldg(wp + i + 96) : cu, cnt);
         }
-        for (; i < ch.len; i += 32) scatter_add<T, HOT>(y, sh_acc, __ldg(ip + i), W ? cu * __ldg(wp + i) : cu);
+        for (; i < ch.len; i += 32) scatter_add<T, HOT>(y, sh_acc, __ldg(ip + i), W ? cu * __ldg(wp + i) : cu, cnt);
     }
     // light sources: 32 consecutive sources per warp, one merged edge stream
     __shared__ float agg[1024];
@@ -415,7 +428,7 @@ __global__ void __launch_bounds__(1024) k_push_scatter(PrArgs a) {
             // atomic per window instead of one per edge.
             const unsigned peers = __match_any_sync(FULL, dst);
             if (__all_sync(FULL, peers == (1u << lane))) {
-                if (eid < E) scatter_add<T, HOT>(y, sh_acc, dst, val);
+                if (eid < E) scatter_add<T, HOT>(y, sh_acc, dst, val, cnt);
             } else {
                 agg[threadIdx.x] = val;
                 __syncwarp();
@@ -423,7 +436,8 @@ __global__ void __launch_bounds__(1024) k_push_scatter(PrArgs a) {
                     float sum = val;
                     for (unsigned rest = peers & ~(1u << lane); rest; rest &= rest - 1)
                         sum += agg[(threadIdx.x & ~31u) + (__ffs(rest) - 1)];
-                    scatter_add<T, HOT>(y, sh_acc, dst, sum);
+                    scatter_add<T, HOT>(y, sh_acc, dst, sum, cnt);
+                    cnt.merged += __popc(peers) - 1;
                 }
                 __syncwarp();
             }
@@ -433,7 +447,31 @@ __global__ void __launch_bounds__(1024) k_push_scatter(PrArgs a) {
         __syncthreads();
         for (int64_t i = threadIdx.x; i < a.nhot; i += blockDim.x) {
             const float v = sh_acc[i];
-            if (v != 0.f) atomicAdd(y + a.hot_id[i], (T)v);
+            if (v != 0.f) {
+                atomicAdd(y + a.hot_id[i], (T)v);
+                ++cnt.flush;
+            }
+        }
+    }
+    // the block's update counts, one reduction and four atomics per block
+    __shared__ unsigned long long csum[4][32];
+    unsigned long long c4[4] = {cnt.l2, cnt.shared, cnt.merged, cnt.flush};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) c4[i] = warp_sum(c4[i]);
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) csum[i][threadIdx.x >> 5] = c4[i];
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) c4[i] = warp_sum(threadIdx.x < (blockDim.x >> 5) ? csum[i][threadIdx.x] : 0ull);
+        if (threadIdx.x == 0) {
+            if (c4[0]) atomicAdd(&a.status->upd_l2, c4[0]);
+            if (c4[1]) atomicAdd(&a.status->upd_shared, c4[1]);
+            if (c4[2]) atomicAdd(&a.status->upd_merged, c4[2]);
+            if (c4[3]) atomicAdd(&a.status->flush_l2, c4[3]);
         }
     }
 }
@@ -600,6 +638,20 @@ static const void *push_kernel(bool W, bool fp64, bool hot) {
     return hot ? (const void *)k_push_scatter<false, float, true> : (const void *)k_push_scatter<false, float, false>;
 }
 
+// Width of the push accumulator.  FP64 sums make the scattered result independent
+// of the atomic order up to one final rounding, and cost no throughput while the
+// 8n-byte accumulator stays in L2; above half the L2 its reductions reach DRAM
+// (Erdos-Renyi 2^24: 4.7 ms per scatter against 2.5 ms in FP32), so the default
+// (-1) switches to FP32 there unless some vertex takes more than
+// PUSH_FP32_MAX_UPDATES updates per sweep (FP32 order noise at such hubs sets a
+// residual floor near 1e-7).
+constexpr int64_t PUSH_FP32_MAX_UPDATES = 4096;
+static bool push_fp64(const gp_graph *g, int64_t max_updates) {
+    if (g->opt.push_fp64_accum >= 0) return g->opt.push_fp64_accum != 0;
+    const bool fits = 8 * g->n <= g->l2_bytes / 2;
+    return fits || max_updates > PUSH_FP32_MAX_UPDATES;
+}
+
 // One power iteration y = base + d * post_scale * (gather or scatter over the
 // given adjacency) of a PageRank-type linear system, with on-device
 // convergence; used for the forward pass and for the adjoint.
@@ -616,6 +668,7 @@ struct IterSpec {
     const float *post_scale, *cmul;
     int iters;
     double tol;
+    int64_t max_updates;  // push: most updates any vertex takes per sweep (its max in-degree)
 };
 
 static int pr_iterate(gp_graph *g, const IterSpec &sp, float *out, PrStatus &fin, cudaStream_t s) {
@@ -699,7 +752,7 @@ static int pr_iterate(gp_graph *g, const IterSpec &sp, float *out, PrStatus &fin
     } else {
         // one grid for big chunks and light tiles; as many resident blocks as fit,
         // capped by blocks_per_sm (256-thread units)
-        const void *ks = push_kernel(W, g->opt.push_fp64_accum != 0, hot);
+        const void *ks = push_kernel(W, push_fp64(g, sp.max_updates), hot);
         int os = 0;
         GP_TRY(occupancy(ks, 1024, smem, os));
         const int cap = std::max(1, g->opt.blocks_per_sm / 4) * g->num_sms;
@@ -713,7 +766,7 @@ static int pr_iterate(gp_graph *g, const IterSpec &sp, float *out, PrStatus &fin
     a.split_blocks = split;
 
     const int ib = (int)std::max<int64_t>(1, std::min<int64_t>(gb, (n + 255) / 256));
-    const bool fp64 = push && g->opt.push_fp64_accum;
+    const bool fp64 = push && push_fp64(g, sp.max_updates);
     if (fp64 && !w.acc64) GP_TRY(w.mem.alloc(w.acc64, (size_t)n, s));
     a.acc64 = fp64 ? w.acc64 : nullptr;
     GP_LAUNCH("pr_init", s, (k_pr_init<<<ib, 256, 0, s>>>(n, sp.x0, sp.cmul, R[0], C[0], (push && !fp64) ? R[1] : nullptr,
@@ -922,6 +975,7 @@ extern "C" int gp_pagerank(const gp_graph *gc, int mode, float damping, int iter
     sp.cmul = g->inv_deg;
     sp.iters = iters;
     sp.tol = tol;
+    sp.max_updates = g->max_in;
     PrStatus fin;
     GP_TRY(pr_iterate(g, sp, R0, fin, s));
     if (!out_dev) GP_CUDA(cudaMemcpyAsync(ranks_out, R0, n * sizeof(float), cudaMemcpyDeviceToHost, s));
@@ -937,6 +991,10 @@ extern "C" int gp_pagerank(const gp_graph *gc, int mode, float damping, int iter
         stats->residual = fin.residual;
         stats->ms = ms;
         stats->converged = (tol <= 0.0) ? 1 : fin.converged;
+        stats->push_updates_l2 = (int64_t)fin.upd_l2;
+        stats->push_updates_shared = (int64_t)fin.upd_shared;
+        stats->push_updates_merged = (int64_t)fin.upd_merged;
+        stats->push_flush_l2 = (int64_t)fin.flush_l2;
     } else if (!out_dev) {
         GP_CUDA(cudaStreamSynchronize(s));
     }
@@ -989,6 +1047,7 @@ extern "C" int gp_pagerank_backward(const gp_graph *gc, int mode, float damping,
     sp.cmul = nullptr;
     sp.iters = iters;
     sp.tol = tol;
+    sp.max_updates = g->max_out;  // the transposed scatter lands on sources
     PrStatus fin;
     GP_TRY(pr_iterate(g, sp, w.lam, fin, s));
     const int gb = grid_blocks(g, 256);

@@ -767,7 +767,7 @@ int gp_options_default(gp_options *opt) {
     opt->pr_auto_mode = -1;
     opt->bfs_alpha = 14.0f;
     opt->bfs_beta = 24.0f;
-    opt->push_fp64_accum = 1;
+    opt->push_fp64_accum = -1;
     opt->pull_hot_slots = 16384;
     opt->push_hot_slots = 16384;
     opt->sssp_alpha = 1.0f;
@@ -905,6 +905,11 @@ int gp_graph_upload(gp_graph **out, int64_t n, int64_t m, const int64_t *csr_off
     gp_graph *g = new gp_graph();
     GP_CUDA(cudaGetDevice(&g->device));
     GP_CUDA(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device));
+    {
+        int l2 = 0;
+        GP_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, g->device));
+        g->l2_bytes = l2;
+    }
     gp_options_default(&g->opt);
     g->n = n;
     g->m = m;
@@ -1075,7 +1080,7 @@ int gp_graph_set_options(gp_graph *g, const gp_options *opt, void *stream) {
         opt->push_light_max > (1 << 20) || opt->chunk_edges < 32 || opt->chunk_edges > (1 << 24) ||
         opt->blocks_per_sm < 1 || opt->blocks_per_sm > 32 || opt->poll_interval < 1 ||
         !(opt->bfs_alpha > 0.f) || !(opt->bfs_beta > 0.f) || !(opt->sssp_alpha > 0.f) || !(opt->fe_alpha > 0.f) || !(opt->bc_alpha > 0.f) || opt->pr_auto_mode < -1 || opt->pr_auto_mode > 1 ||
-        (opt->push_fp64_accum != 0 && opt->push_fp64_accum != 1) || opt->pull_hot_slots < 0 ||
+        opt->push_fp64_accum < -1 || opt->push_fp64_accum > 1 || opt->pull_hot_slots < 0 ||
         opt->pull_hot_slots > 49152 || opt->push_hot_slots < 0 || opt->push_hot_slots > 49152)
         return set_error(GP_ERR_INVALID, "gp_graph_set_options: option out of range");
     cudaStream_t s = (cudaStream_t)stream;

@@ -52,7 +52,7 @@ def test_struct_sizes_match_header():
 
     # layouts fixed by include/gp.h (x86-64 and AArch64 agree)
     assert ctypes.sizeof(gp.gp_options) == 64
-    assert ctypes.sizeof(gp.gp_pr_stats) == 24
+    assert ctypes.sizeof(gp.gp_pr_stats) == 56
     assert ctypes.sizeof(gp.gp_kernel_time) == 64
     assert ctypes.sizeof(gp.gp_graph_info) == 88
 

@@ -242,3 +242,43 @@ def test_forced_directions_beyond_512_levels_are_used(gp):
     # a top-down level of a path examines its frontier's 1-2 out-edges; a
     # bottom-up level examines the in-edges of every unvisited vertex until a hit
     assert s_mx["edges_examined"] > s_td["edges_examined"] + 100000, (s_mx["edges_examined"], s_td["edges_examined"])
+
+
+@pytest.mark.parametrize("src", [1, 32, 33, 64, 65, 200, 256, 257, 4095, 5000])
+@pytest.mark.parametrize("chunk", [256, 32])
+def test_bottom_up_hub(gp, src, chunk):
+    """Star with 5000 leaves from leaf `src`, bottom-up: the centre is a hub
+    candidate whose one frontier in-neighbour sits at position src - 1 of its
+    in-list.  Within the first 64 in-edges (the lane's probe) the centre's own
+    lane finds it and the level examines every other leaf's single in-edge plus
+    the centre's first src; further out the lane gives up after 64 and the
+    centre's in-edge chunks are scanned across the grid, which examines each
+    edge at most once more."""
+    g = gg.star(5000)
+    G = gp.Graph.from_graphgen(g)
+    G.set_options(chunk_edges=chunk)
+    O = oracle.OracleGraph.from_graph(g)
+    lv, pa, st = gp.bfs(G, src, dirs=[1])
+    check(g, O, src, lv, pa)
+    assert int(to_np(pa)[0]) == src
+    if src <= 64:
+        assert st["examined"][0] == (5000 - 1) + src
+    else:
+        assert (5000 - 1) + 64 + (src - 1) % chunk < st["examined"][0] <= (5000 - 1) + 64 + 5000
+
+
+def test_bottom_up_hubs_on_rmat(gp):
+    """Forced bottom-up from R-MAT sources (every hub scans its whole in-list at
+    the first levels, so the chunk pass runs) with several chunk sizes and pull
+    light limits: levels bit-exact and parents valid."""
+    g = gg.rmat(14, 16, seed=6)
+    G = gp.Graph.from_graphgen(g)
+    O = oracle.OracleGraph.from_graph(g)
+    srcs = gg.pick_vertices(g, 3, seed=7)
+    for opts in ({}, {"chunk_edges": 32}, {"pull_light_max": 200}, {"pull_light_max": 0, "chunk_edges": 64}):
+        if opts:
+            G.set_options(**opts)
+        for src in srcs:
+            for dirs in ([1], [1, 1, 0], [0, 1]):
+                lv, pa, _ = gp.bfs(G, int(src), dirs=dirs)
+                check(g, O, int(src), lv, pa)

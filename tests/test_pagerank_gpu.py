@@ -313,3 +313,36 @@ def test_graph_info(gp):
     assert info["isolated"] == int(((d == 0) & (g.in_degree() == 0)).sum())
     lm = G.options().pull_light_max
     assert info["pull_big_vertices"] == int((g.in_degree() > lm).sum())
+
+
+PUSH_COUNT_OPTS = [{}, {"push_hot_slots": 0}, {"push_hot_slots": 64, "push_light_max": 0, "chunk_edges": 32},
+                   {"push_fp64_accum": 0}, {"push_light_max": 1000}]
+
+
+@pytest.mark.parametrize("oi", range(len(PUSH_COUNT_OPTS)))
+def test_push_update_counts(gp, oi):
+    """Table 1's atomics row as an invariant: every push sweep issues exactly m
+    scattered updates -- each an L2 atomic, a shared-memory atomic into a hot
+    accumulator, or folded into a warp neighbour's update -- and pull issues
+    none.  A star's leaves update its centre from every lane of a tile, so the
+    warp folding is exercised; without hot slots nothing is shared or flushed."""
+    opts = PUSH_COUNT_OPTS[oi]
+    for g in (gg.rmat(12, 16, seed=9, symmetrize=False), gg.star(3000), gg.rmat(10, 8, seed=2)):
+        G = gp.Graph.from_graphgen(g)
+        if opts:
+            G.set_options(**opts)
+        k = 7
+        _, st = gp.pagerank(G, gp.PUSH, 0.85, k, 0.0)
+        total = st["push_updates_l2"] + st["push_updates_shared"] + st["push_updates_merged"]
+        assert st["iters_done"] == k and total == g.m * k, (g.name, opts, st)
+        if opts.get("push_hot_slots", 1) == 0:
+            assert st["push_updates_shared"] == 0 and st["push_flush_l2"] == 0
+        if g.name.startswith("star") and opts.get("push_light_max", 32) >= 1:
+            assert st["push_updates_merged"] > 0
+        _, sp = gp.pagerank(G, gp.PULL, 0.85, k, 0.0)
+        assert (sp["push_updates_l2"], sp["push_updates_shared"], sp["push_updates_merged"],
+                sp["push_flush_l2"]) == (0, 0, 0, 0)
+        # a run that stops at tol counts the sweeps it performed, not the ones enqueued after
+        _, st = gp.pagerank(G, gp.PUSH, 0.85, 300, 1e-5)
+        total = st["push_updates_l2"] + st["push_updates_shared"] + st["push_updates_merged"]
+        assert total == g.m * st["iters_done"]
