@@ -57,6 +57,8 @@ def parse_args(argv=None):
     p.add_argument("--only", choices=["pr_pull", "pr_push", "bfs", "batched", "sssp", "tc", "pr_fe", "bc"], default=None,
                    help="profiling case: run only this part (fixed --sweeps for PageRank), no contract line")
     p.add_argument("--sweeps", type=int, default=4)
+    p.add_argument("--batch-scale", type=int, default=None,
+                   help="--only batched: one R-MAT graph of this scale instead of the 32-graph workload")
     p.add_argument("--delta", type=float, default=64.0, help="--only sssp: bucket width")
     p.add_argument("--mode", choices=["push", "pull", "auto"], default="auto", help="--only sssp: direction mode")
     p.add_argument("--opt", action="append", default=[], metavar="KEY=VALUE",
@@ -799,11 +801,12 @@ def run_batched(args, graphs_scales=None):
     B.ppr(seeds, iters=1000, tol=1e-6)  # captures the CUDA graph
     B.msbfs(srcs)
     torch.cuda.synchronize()
-    tp, tb = [], []
+    tp, tb, tk = [], [], []
     for _ in range(REPS):
         t = time.perf_counter()
         outs, done, st = B.ppr(seeds, iters=1000, tol=1e-6)
         tp.append(time.perf_counter() - t)
+        tk.append(st["ms"])
         t = time.perf_counter()
         louts, bst = B.msbfs(srcs)
         tb.append(time.perf_counter() - t)
@@ -840,6 +843,25 @@ def run_batched(args, graphs_scales=None):
     max_err = max(float((xs[i][j] - outs[i][:, j]).abs().max()) for i in range(len(graphs)) for j in range(SAMPLE))
     nvec = len(graphs) * K
     edges = sum(g.m * int(done[i].sum()) for i, g in enumerate(graphs))
+    # roofline: compulsory bytes per sweep of a (graph, slice) job are the index
+    # stream and offsets (4m + 8n) plus the slice's iterate read once, written
+    # once and read for the residual (12 n KS); a graph runs until its slowest
+    # column stops.  Row gathers (m KS 4 bytes per job sweep) come from L2 by
+    # design and are reported as a rate beside it.
+    bo = B.options()
+    budget = bo["l2_budget_mb"] << 20
+
+    def width(n):
+        return next((w for w in (128, 64) if w <= K and 2 * n * w * 4 <= budget), 32)
+
+    comp_bytes = gath_bytes = 0.0
+    for i, g in enumerate(graphs):
+        sw = int(done[i].max())
+        jobs = K // width(g.n)
+        comp_bytes += sw * (jobs * (4 * g.m + 8 * (g.n + 1)) + 12 * K * g.n)
+        gath_bytes += sw * g.m * K * 4.0
+    peak, peak_kind = measured_peak_gbs()
+    kms = statistics.median(tk) if tk else None
     B.free()
     return {"graphs": len(graphs), "scales": scales, "n_total": int(sum(g.n for g in graphs)),
             "m_total": int(sum(g.m for g in graphs)), "ppr_vectors": nvec,
@@ -851,7 +873,11 @@ def run_batched(args, graphs_scales=None):
             "bfs_sources": len(graphs) * NSRC, "bfs_batched_ms": round(bfs_batched_s * 1e3, 2),
             "bfs_serial_ms_extrapolated": round(bfs_serial_s * 1e3, 1),
             "bfs_speedup": round(bfs_serial_s / bfs_batched_s, 2), "bfs_levels": bst["levels"],
-            "serial_sample_per_graph": SAMPLE, "repeats": REPS,
+            "serial_sample_per_graph": SAMPLE, "repeats": REPS, "options": bo, "ppr_jobs": st["jobs"],
+            "ppr_roofline": {"bound": "hbm", "kernel_ms": round(kms, 2), "compulsory_bytes": int(comp_bytes),
+                             "achieved": round(comp_bytes / (kms * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+                             "frac": round(comp_bytes / (kms * 1e-3) / 1e9 / peak, 4), "peak_kind": peak_kind,
+                             "l2_gather_gbs": round(gath_bytes / (kms * 1e-3) / 1e9, 1)},
             "ppr_batched_ms_all": [round(x * 1e3, 2) for x in tp],
             "ppr_serial_ms_all": [round(x * 1e3, 1) for x in ts]}
 
@@ -865,7 +891,12 @@ def run_only(args):
 
     gp.load()
     if args.only == "batched":
-        print(json.dumps({"profile_case": "batched", **run_batched(args)}), flush=True)
+        import graphgen as gg
+
+        gs = None
+        if args.batch_scale:
+            gs = ([gg.rmat(args.batch_scale, 16, seed=100)], [args.batch_scale])
+        print(json.dumps({"profile_case": "batched", **run_batched(args, gs)}), flush=True)
         return 0
     if args.only == "sssp":
         return run_only_sssp(args)

@@ -553,7 +553,26 @@ typedef struct gp_batch_stats {
     int32_t levels;  /* BFS: levels explored by the deepest search */
     float ms;        /* device time of the persistent launch (CUDA events) */
     int32_t blocks;  /* resident blocks of the cooperative launch */
+    int32_t jobs;    /* PageRank: (graph, column slice) jobs the vectors were split into */
 } gp_batch_stats;
+
+/* Tunables of a batch (gp_batch_autotune writes them; results never depend on them). */
+typedef struct gp_batch_options {
+    int32_t big_in_degree; /* in-degree above which a vertex's in-edges are split into chunks
+                              (PageRank) or scanned by a whole warp (bottom-up BFS) */
+    int32_t chunk_edges;   /* in-edges per chunk */
+    int32_t l2_budget_mb;  /* PageRank: the widest column slice (128, 64 or 32 columns, at most k_ppr) whose two iterates fit this many MiB is one job */
+    float msbfs_alpha;     /* BFS: a graph's level goes bottom-up when its frontier's out-edges
+                              times alpha exceed the in-edges of vertices some search misses */
+    float msbfs_beta;      /* BFS: back to top-down when the frontier is below n / beta */
+    int32_t reserved[3];
+} gp_batch_options;
+
+int gp_batch_options_default(gp_batch_options *opt);
+/* Replace the batch's options (rebuilds its work lists when the degree limit,
+ * chunk size or budget change; synchronises the stream then). */
+int gp_batch_set_options(gp_batch *b, const gp_batch_options *opt, void *stream);
+int gp_batch_get_options(const gp_batch *b, gp_batch_options *opt);
 
 /*
  * Prepare batched runs over `ngraphs` uploaded graphs (the handles stay owned

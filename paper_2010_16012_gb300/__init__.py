@@ -112,7 +112,12 @@ class gp_bc_stats(ctypes.Structure):
 
 class gp_batch_stats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int32), ("levels", ctypes.c_int32), ("ms", ctypes.c_float),
-                ("blocks", ctypes.c_int32)]
+                ("blocks", ctypes.c_int32), ("jobs", ctypes.c_int32)]
+
+
+class gp_batch_options(ctypes.Structure):
+    _fields_ = [("big_in_degree", ctypes.c_int32), ("chunk_edges", ctypes.c_int32), ("l2_budget_mb", ctypes.c_int32),
+                ("msbfs_alpha", ctypes.c_float), ("msbfs_beta", ctypes.c_float), ("reserved", ctypes.c_int32 * 3)]
 
 
 class gp_tune_result(ctypes.Structure):
@@ -159,6 +164,9 @@ SIGNATURES = [
                              ctypes.POINTER(gp_bc_stats), _VP]),
     ("gp_batch_create", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _VP]),
     ("gp_batch_free", ctypes.c_int, [_VP]),
+    ("gp_batch_options_default", ctypes.c_int, [ctypes.POINTER(gp_batch_options)]),
+    ("gp_batch_set_options", ctypes.c_int, [_VP, ctypes.POINTER(gp_batch_options), _VP]),
+    ("gp_batch_get_options", ctypes.c_int, [_VP, ctypes.POINTER(gp_batch_options)]),
     ("gp_ppr_batched", ctypes.c_int, [_VP, _VP, _F, ctypes.c_int, _D, ctypes.POINTER(_VP), _VP,
                                       ctypes.POINTER(gp_batch_stats), _VP]),
     ("gp_msbfs_batched", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(gp_batch_stats),
@@ -564,6 +572,22 @@ class Batch:
         except Exception:
             pass
 
+    BATCH_OPTION_FIELDS = ("big_in_degree", "chunk_edges", "l2_budget_mb", "msbfs_alpha", "msbfs_beta")
+
+    def options(self) -> dict:
+        o = gp_batch_options()
+        _check(load().gp_batch_get_options(self._h, ctypes.byref(o)), "gp_batch_get_options")
+        return {f: getattr(o, f) for f in self.BATCH_OPTION_FIELDS}
+
+    def set_options(self, stream=None, **kw):
+        o = gp_batch_options()
+        _check(load().gp_batch_get_options(self._h, ctypes.byref(o)), "gp_batch_get_options")
+        for k, v in kw.items():
+            if k not in self.BATCH_OPTION_FIELDS:
+                raise KeyError(k)
+            setattr(o, k, v)
+        _check(load().gp_batch_set_options(self._h, ctypes.byref(o), _stream_ptr(stream)), "gp_batch_set_options")
+
     def ppr(self, seeds, damping=0.85, iters=1000, tol=1e-6, outs=None, stream=None):
         """seeds: int array [ngraphs][k].  Returns (list of [n_i, k] tensors, iters_done [ngraphs, k], stats)."""
         torch = _torch()
@@ -575,7 +599,7 @@ class Batch:
         st = gp_batch_stats()
         _check(load().gp_ppr_batched(self._h, _ptr(seeds), float(damping), int(iters), float(tol), optr, _ptr(done),
                                      ctypes.byref(st), _stream_ptr(stream)), "gp_ppr_batched")
-        return outs, done, {"sweeps": st.sweeps, "ms": st.ms, "blocks": st.blocks}
+        return outs, done, {"sweeps": st.sweeps, "ms": st.ms, "blocks": st.blocks, "jobs": st.jobs}
 
     def msbfs(self, sources, outs=None, stream=None):
         """sources: int array [ngraphs][nsrc] (nsrc <= 64).  Returns (list of [n_i, 64] int32 tensors, stats)."""

@@ -127,3 +127,59 @@ def test_batched_rejects_bad_input(gp):
         B.ppr(np.full((1, 32), 10, dtype=np.int32))
     with pytest.raises(gp.GpError):
         B.msbfs(np.full((1, 3), -1, dtype=np.int32))
+
+
+BATCH_OPTS = [{"big_in_degree": 8, "chunk_edges": 32, "l2_budget_mb": 1},  # many chunks, 32-column jobs
+              {"big_in_degree": 0, "chunk_edges": 64},                   # every vertex chunked
+              {"big_in_degree": 100000, "l2_budget_mb": 4096},           # nothing chunked, widest slices
+              {"msbfs_alpha": 1e-6},                                     # BFS stays top-down
+              {"msbfs_alpha": 1e6, "msbfs_beta": 1e-6}]                  # BFS bottom-up from level 1 on
+
+
+@pytest.mark.parametrize("oi", range(len(BATCH_OPTS)))
+def test_batch_options_do_not_change_results(gp, oi):
+    """Every batch option value gives the oracle's results: PPR vectors within
+    the tolerance at their sweep counts (whatever the column slices and chunk
+    layout), BFS levels bit-exact (whatever mix of top-down and bottom-up)."""
+    graphs = uneven_graphs() + [gg.rmat(13, 16, seed=45)]
+    G = [gp.Graph.from_graphgen(g) for g in graphs]
+    k = 128
+    B = gp.Batch(G, k_ppr=k)
+    B.set_options(**BATCH_OPTS[oi])
+    assert {kk: B.options()[kk] for kk in BATCH_OPTS[oi]} == pytest.approx(BATCH_OPTS[oi])
+    seeds = np.stack([seeds_for(g, k, 150 + i) for i, g in enumerate(graphs)])
+    outs, done, st = B.ppr(seeds, iters=500, tol=1e-6)
+    # a graph's slice is the widest of 128, 64, 32 columns whose two iterates fit the budget
+    budget = B.options()["l2_budget_mb"] << 20
+
+    def width(n):
+        return next((w for w in (128, 64) if w <= k and 2 * n * w * 4 <= budget), 32)
+
+    assert st["jobs"] == sum(k // width(g.n) for g in graphs)
+    rng = np.random.default_rng(oi)
+    for i, g in enumerate(graphs):
+        O = oracle.OracleGraph.from_graph(g)
+        X = outs[i].cpu().numpy()
+        for j in sorted({0, 31, 32, 63, 64, k - 1, int(rng.integers(k))}):
+            e = np.zeros(g.n)
+            e[seeds[i, j]] = 1.0
+            ref, _, _, _ = O.pagerank(oracle.PULL, 0.85, iters=int(done[i, j]), personalization=e)
+            err = np.abs(X[:, j].astype(np.float64) - ref)
+            assert err.max() <= MAX_ABS and err.sum() <= L1, (oi, i, j, err.max(), err.sum())
+    srcs = np.stack([np.resize(gg.pick_vertices(g, 64, seed=170 + i, min_out_degree=0), 64)
+                     for i, g in enumerate(graphs)]).astype(np.int32)
+    louts, _ = B.msbfs(srcs)
+    for i, g in enumerate(graphs):
+        O = oracle.OracleGraph.from_graph(g)
+        L = louts[i].cpu().numpy()
+        for j in (0, 17, 63):
+            ref, _ = O.bfs(int(srcs[i, j]))
+            assert np.array_equal(L[:, j], ref), (oi, i, j)
+    B.free()
+
+
+def test_batch_option_validation(gp):
+    B = gp.Batch([gp.Graph.from_graphgen(gg.path(10))], k_ppr=32)
+    for bad in ({"chunk_edges": 8}, {"l2_budget_mb": 0}, {"msbfs_alpha": 0.0}, {"big_in_degree": -1}):
+        with pytest.raises(gp.GpError):
+            B.set_options(**bad)
