@@ -783,7 +783,8 @@ def batched_workload(nscale_lo=12, nscale_hi=18, ngraphs=32):
 def run_batched(args, graphs_scales=None):
     """Batched personalised PageRank (256 one-hot vectors per graph, tol 1e-6) and
     64-source BFS over 32 graphs in one persistent launch each, against
-    one-at-a-time gp_pagerank / gp_bfs calls on the same stream (timed on a
+    one-at-a-time gp_pagerank / gp_bfs calls on the same stream, each vector
+    started at its seed's one-hot vector on both sides (timed on a
     sample of vectors and sources per graph, scaled to all of them; CUDA-graph
     capture is excluded from the batched side, launch overheads are included on
     both sides)."""
@@ -830,7 +831,7 @@ def run_batched(args, graphs_scales=None):
         t = time.perf_counter()
         for i in range(len(graphs)):
             for j in range(SAMPLE):
-                gp.pagerank(G[i], gp.PULL, 0.85, 1000, 1e-6, personalization=ev[i][j], out=xs[i][j])
+                gp.pagerank(G[i], gp.PULL, 0.85, 1000, 1e-6, personalization=ev[i][j], x0=ev[i][j], out=xs[i][j])
         torch.cuda.synchronize()
         ts.append((time.perf_counter() - t) * K / SAMPLE)
         t = time.perf_counter()

@@ -117,7 +117,8 @@ class gp_batch_stats(ctypes.Structure):
 
 class gp_batch_options(ctypes.Structure):
     _fields_ = [("big_in_degree", ctypes.c_int32), ("chunk_edges", ctypes.c_int32), ("l2_budget_mb", ctypes.c_int32),
-                ("msbfs_alpha", ctypes.c_float), ("msbfs_beta", ctypes.c_float), ("reserved", ctypes.c_int32 * 3)]
+                ("msbfs_alpha", ctypes.c_float), ("msbfs_beta", ctypes.c_float), ("ppr_start", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class gp_tune_result(ctypes.Structure):
@@ -572,7 +573,7 @@ class Batch:
         except Exception:
             pass
 
-    BATCH_OPTION_FIELDS = ("big_in_degree", "chunk_edges", "l2_budget_mb", "msbfs_alpha", "msbfs_beta")
+    BATCH_OPTION_FIELDS = ("big_in_degree", "chunk_edges", "l2_budget_mb", "msbfs_alpha", "msbfs_beta", "ppr_start")
 
     def options(self) -> dict:
         o = gp_batch_options()

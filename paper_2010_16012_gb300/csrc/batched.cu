@@ -11,8 +11,9 @@
 // iterates fits the L2 budget, so every gathered row segment (KS * 4 bytes, a whole number of
 // 128-byte lines) comes from L2 for the job's whole run.  Jobs run one after
 // another over the whole grid; each sweeps its slice to convergence.  Every
-// vector (column) has its own L1 residual, reduced in FP64, and stops at its
-// first sweep below tol; its column is then carried forward unchanged.
+// vector (column) starts at its seed's one-hot vector (or at 1/n), has its own
+// L1 residual, reduced in FP64, and stops at its first sweep below tol; its
+// column is then carried forward unchanged.
 //
 // Multi-source BFS (Section 3.3 / Algorithm 3 with ready = 1, up to 64 sources
 // at once): F[v], V[v] and N[v] are 64-bit masks (bit j = search j).  Each
@@ -74,6 +75,7 @@ struct BatchDev {
     double tol;
     int iters;
     int64_t big_min;        // in-degree above which a vertex's in-edges are split into chunks
+    int32_t one_hot_start;  // PPR iterates start at e_seed (else 1/n)
     float alpha, beta;      // MS-BFS direction rule
     const BGraph *graphs;
     const BJob *jobs;
@@ -234,8 +236,14 @@ __device__ bool ppr_job(const BatchDev &B, const BJob &J, float (*s_res)[32][4],
     const int64_t gthread = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int64_t gwarp = gthread >> 5, nwarps = nthreads >> 5;
+    // start: every column at 1/n, or at its seed's one-hot vector
     const float x0 = 1.0f / (float)n;
-    for (int64_t i = gthread; i < n * KS; i += nthreads) G.X0[(i / KS) * K + J.c0 + (i % KS)] = x0;
+    for (int64_t i = gthread; i < n * KS; i += nthreads) {
+        const int64_t v = i / KS;
+        const int c = (int)(i % KS);
+        G.X0[v * K + J.c0 + c] =
+            B.one_hot_start ? (B.seeds[J.graph * K + J.c0 + c] == (int32_t)v ? 1.0f : 0.0f) : x0;
+    }
     for (int c = threadIdx.x; c < KS; c += blockDim.x) s_active[c] = 1;
     if (gthread < 3 * KS) B.res_acc[(gthread / KS) * K + (gthread % KS)] = 0.0;
     if (!grid_sync(B.sync, gridDim.x)) return false;
@@ -644,6 +652,7 @@ static int batch_layout(gp_batch *b, cudaStream_t s) {
     D.njobs = (int)b->jobs.size();
     D.alpha = b->opt.msbfs_alpha;
     D.beta = b->opt.msbfs_beta;
+    D.one_hot_start = b->opt.ppr_start;
     b->ppr_stale = b->bfs_stale = true;  // captured launches hold the old arguments
     return GP_OK;
 }
@@ -661,6 +670,7 @@ extern "C" int gp_batch_options_default(gp_batch_options *opt) {
     opt->l2_budget_mb = 128;
     opt->msbfs_alpha = 16.0f;
     opt->msbfs_beta = 24.0f;
+    opt->ppr_start = 1;
     return GP_OK;
 }
 
@@ -751,7 +761,8 @@ extern "C" int gp_batch_set_options(gp_batch *b, const gp_batch_options *opt, vo
     clear_error();
     if (!b || !opt) return set_error(GP_ERR_INVALID, "gp_batch_set_options: NULL argument");
     if (opt->big_in_degree < 0 || opt->chunk_edges < 32 || opt->chunk_edges > (1 << 20) || opt->l2_budget_mb < 1 ||
-        opt->l2_budget_mb > (1 << 20) || !(opt->msbfs_alpha > 0.f) || !(opt->msbfs_beta > 0.f))
+        opt->l2_budget_mb > (1 << 20) || !(opt->msbfs_alpha > 0.f) || !(opt->msbfs_beta > 0.f) ||
+        (opt->ppr_start != 0 && opt->ppr_start != 1))
         return set_error(GP_ERR_INVALID, "gp_batch_set_options: option out of range");
     const gp_batch_options old = b->opt;
     b->opt = *opt;
@@ -760,7 +771,8 @@ extern "C" int gp_batch_set_options(gp_batch *b, const gp_batch_options *opt, vo
         return batch_layout(b, (cudaStream_t)stream);
     b->dev.alpha = opt->msbfs_alpha;
     b->dev.beta = opt->msbfs_beta;
-    b->bfs_stale = true;
+    b->dev.one_hot_start = opt->ppr_start;
+    b->bfs_stale = b->ppr_stale = true;
     return GP_OK;
 }
 

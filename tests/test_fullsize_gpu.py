@@ -198,7 +198,7 @@ def test_batch_32_graphs(gp):
         for j in (int(rng.integers(K)), K - 1):
             e = np.zeros(graphs[i].n)
             e[seeds[i, j]] = 1.0
-            ref, _, _, _ = O.pagerank(oracle.PULL, 0.85, iters=int(done[i, j]), personalization=e, nthreads=NT)
+            ref, _, _, _ = O.pagerank(oracle.PULL, 0.85, iters=int(done[i, j]), personalization=e, x0=e, nthreads=NT)
             err = np.abs(X[:, j].astype(np.float64) - ref)
             assert err.max() <= MAX_ABS and err.sum() <= L1, (i, j, err.max(), err.sum())
         L = louts[i].cpu().numpy()
