@@ -556,7 +556,7 @@ typedef struct gp_batch_stats {
     int32_t jobs;    /* PageRank: (graph, column slice) jobs the vectors were split into */
 } gp_batch_stats;
 
-/* Tunables of a batch (gp_batch_autotune writes them; results never depend on them). */
+/* Tunables of a batch (gp_batch_autotune chooses them; results never depend on them). */
 typedef struct gp_batch_options {
     int32_t big_in_degree; /* in-degree above which a vertex's in-edges are split into chunks
                               (PageRank) or scanned by a whole warp (bottom-up BFS) */
@@ -575,6 +575,26 @@ int gp_batch_options_default(gp_batch_options *opt);
  * chunk size or budget change; synchronises the stream then). */
 int gp_batch_set_options(gp_batch *b, const gp_batch_options *opt, void *stream);
 int gp_batch_get_options(const gp_batch *b, gp_batch_options *opt);
+
+typedef struct gp_batch_tune_result {
+    gp_batch_options options; /* the chosen options (also installed in the batch) */
+    float ppr_ms;             /* device time of ppr_sweeps fixed sweeps with them */
+    float msbfs_ms;           /* device time of the multi-source search with them */
+    int32_t trials;           /* timed candidates */
+} gp_batch_tune_result;
+
+/*
+ * Autotuner of a batch (not in the paper): coordinate descent over the chunk
+ * threshold {8..128}, chunk size {64, 128, 256} and L2 budget {48..192 MiB},
+ * each candidate timed by CUDA events on `ppr_sweeps` fixed sweeps of
+ * gp_ppr_batched with these seeds (host int32[ngraphs][k_ppr]; NULL skips the
+ * PageRank axes), then over the BFS alpha {2..64} and beta {8, 24, 64} timed on
+ * gp_msbfs_batched with these sources (host int32[ngraphs][nsrc]; NULL skips).
+ * The best options stay installed.  Results never depend on the options.
+ * Synchronises; the batch's previous outputs are overwritten.
+ */
+int gp_batch_autotune(gp_batch *b, const int32_t *seeds, const int32_t *sources, int nsrc, int ppr_sweeps,
+                      gp_batch_tune_result *res, void *stream);
 
 /*
  * Prepare batched runs over `ngraphs` uploaded graphs (the handles stay owned

@@ -121,6 +121,11 @@ class gp_batch_options(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 2)]
 
 
+class gp_batch_tune_result(ctypes.Structure):
+    _fields_ = [("options", gp_batch_options), ("ppr_ms", ctypes.c_float), ("msbfs_ms", ctypes.c_float),
+                ("trials", ctypes.c_int32)]
+
+
 class gp_tune_result(ctypes.Structure):
     _fields_ = [("best", gp_options), ("pull_ms_per_sweep", ctypes.c_float), ("push_ms_per_sweep", ctypes.c_float),
                 ("bfs_ms", ctypes.c_float), ("evaluated", ctypes.c_int32)]
@@ -168,6 +173,8 @@ SIGNATURES = [
     ("gp_batch_options_default", ctypes.c_int, [ctypes.POINTER(gp_batch_options)]),
     ("gp_batch_set_options", ctypes.c_int, [_VP, ctypes.POINTER(gp_batch_options), _VP]),
     ("gp_batch_get_options", ctypes.c_int, [_VP, ctypes.POINTER(gp_batch_options)]),
+    ("gp_batch_autotune", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(gp_batch_tune_result), _VP]),
     ("gp_ppr_batched", ctypes.c_int, [_VP, _VP, _F, ctypes.c_int, _D, ctypes.POINTER(_VP), _VP,
                                       ctypes.POINTER(gp_batch_stats), _VP]),
     ("gp_msbfs_batched", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(gp_batch_stats),
@@ -588,6 +595,20 @@ class Batch:
                 raise KeyError(k)
             setattr(o, k, v)
         _check(load().gp_batch_set_options(self._h, ctypes.byref(o), _stream_ptr(stream)), "gp_batch_set_options")
+
+    def autotune(self, seeds=None, sources=None, ppr_sweeps=16, stream=None) -> dict:
+        """gp_batch_autotune: choose and install the fastest options for these
+        seeds ([ngraphs][k]) and BFS sources ([ngraphs][nsrc]).  Returns
+        {"options", "ppr_ms", "msbfs_ms", "trials"}."""
+        sd = None if seeds is None else np.ascontiguousarray(
+            np.asarray(seeds, dtype=np.int32).reshape(len(self.graphs), self.k))
+        so = None if sources is None else np.ascontiguousarray(np.asarray(sources, dtype=np.int32))
+        nsrc = 0 if so is None else int(so.shape[1])
+        r = gp_batch_tune_result()
+        _check(load().gp_batch_autotune(self._h, _ptr(sd), _ptr(so), nsrc, int(ppr_sweeps), ctypes.byref(r),
+                                        _stream_ptr(stream)), "gp_batch_autotune")
+        return {"options": {f: getattr(r.options, f) for f in self.BATCH_OPTION_FIELDS}, "ppr_ms": r.ppr_ms,
+                "msbfs_ms": r.msbfs_ms, "trials": r.trials}
 
     def ppr(self, seeds, damping=0.85, iters=1000, tol=1e-6, outs=None, stream=None):
         """seeds: int array [ngraphs][k].  Returns (list of [n_i, k] tensors, iters_done [ngraphs, k], stats)."""

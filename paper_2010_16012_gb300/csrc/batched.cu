@@ -31,6 +31,7 @@
 // block returns and the host reports GP_ERR_TIMEOUT).
 #include <algorithm>
 #include <cstring>
+#include <initializer_list>
 #include <vector>
 
 #include "gp_internal.cuh"
@@ -911,5 +912,91 @@ extern "C" int gp_msbfs_batched(gp_batch *b, const int32_t *sources, int nsrc, i
         stats->jobs = (int32_t)b->jobs.size();
     }
     if (hs.err) return set_error(GP_ERR_TIMEOUT, "batched BFS: a grid barrier wait ran out");
+    return GP_OK;
+}
+
+// ------------------------------------------------------------------ tuning
+
+namespace gp {
+
+// Device time of one batched call (a warm-up call first: a changed option
+// re-captures the launch).
+static int time_ppr(gp_batch *b, const int32_t *seeds, int sweeps, cudaStream_t s, float &ms) {
+    gp_batch_stats st;
+    GP_TRY(gp_ppr_batched(b, seeds, 0.85f, sweeps, 0.0, nullptr, nullptr, &st, s));
+    GP_TRY(gp_ppr_batched(b, seeds, 0.85f, sweeps, 0.0, nullptr, nullptr, &st, s));
+    ms = st.ms;
+    return GP_OK;
+}
+
+static int time_msbfs(gp_batch *b, const int32_t *sources, int nsrc, cudaStream_t s, float &ms) {
+    gp_batch_stats st;
+    GP_TRY(gp_msbfs_batched(b, sources, nsrc, nullptr, &st, s));
+    GP_TRY(gp_msbfs_batched(b, sources, nsrc, nullptr, &st, s));
+    ms = st.ms;
+    return GP_OK;
+}
+
+}  // namespace gp
+
+extern "C" int gp_batch_autotune(gp_batch *b, const int32_t *seeds, const int32_t *sources, int nsrc, int ppr_sweeps,
+                                 gp_batch_tune_result *res, void *stream) {
+    clear_error();
+    if (!b || !res) return set_error(GP_ERR_INVALID, "gp_batch_autotune: NULL argument");
+    if (ppr_sweeps < 1) return set_error(GP_ERR_INVALID, "gp_batch_autotune: ppr_sweeps must be >= 1");
+    if (sources && (nsrc < 1 || nsrc > 64)) return set_error(GP_ERR_INVALID, "gp_batch_autotune: nsrc outside [1, 64]");
+    cudaStream_t s = (cudaStream_t)stream;
+    memset(res, 0, sizeof(*res));
+    gp_batch_options best = b->opt;
+    int trials = 0;
+    // coordinate descent, each axis over its candidates with the others fixed
+    auto axis_i32 = [&](int32_t gp_batch_options::*field, std::initializer_list<int32_t> cands, bool ppr,
+                        float &best_ms) -> int {
+        for (int32_t c : cands) {
+            gp_batch_options o = best;
+            o.*field = c;
+            GP_TRY(gp_batch_set_options(b, &o, stream));
+            float ms = 0.f;
+            if (ppr)
+                GP_TRY(time_ppr(b, seeds, ppr_sweeps, s, ms));
+            else
+                GP_TRY(time_msbfs(b, sources, nsrc, s, ms));
+            ++trials;
+            if (best_ms <= 0.f || ms < best_ms) {
+                best_ms = ms;
+                best = o;
+            }
+        }
+        return gp_batch_set_options(b, &best, stream);
+    };
+    auto axis_f32 = [&](float gp_batch_options::*field, std::initializer_list<float> cands, float &best_ms) -> int {
+        for (float c : cands) {
+            gp_batch_options o = best;
+            o.*field = c;
+            GP_TRY(gp_batch_set_options(b, &o, stream));
+            float ms = 0.f;
+            GP_TRY(time_msbfs(b, sources, nsrc, s, ms));
+            ++trials;
+            if (best_ms <= 0.f || ms < best_ms) {
+                best_ms = ms;
+                best = o;
+            }
+        }
+        return gp_batch_set_options(b, &best, stream);
+    };
+    float ppr_ms = 0.f, bfs_ms = 0.f;
+    if (seeds) {
+        GP_TRY(axis_i32(&gp_batch_options::big_in_degree, {8, 16, 32, 64, 128}, true, ppr_ms));
+        GP_TRY(axis_i32(&gp_batch_options::chunk_edges, {64, 128, 256}, true, ppr_ms));
+        GP_TRY(axis_i32(&gp_batch_options::l2_budget_mb, {48, 64, 96, 128, 192}, true, ppr_ms));
+    }
+    if (sources) {
+        GP_TRY(axis_f32(&gp_batch_options::msbfs_alpha, {2.f, 4.f, 8.f, 16.f, 32.f, 64.f}, bfs_ms));
+        GP_TRY(axis_f32(&gp_batch_options::msbfs_beta, {8.f, 24.f, 64.f}, bfs_ms));
+    }
+    res->options = best;
+    res->ppr_ms = ppr_ms;
+    res->msbfs_ms = bfs_ms;
+    res->trials = trials;
     return GP_OK;
 }

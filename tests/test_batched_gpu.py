@@ -196,3 +196,32 @@ def test_batch_option_validation(gp):
     for bad in ({"chunk_edges": 8}, {"l2_budget_mb": 0}, {"msbfs_alpha": 0.0}, {"big_in_degree": -1}, {"ppr_start": 2}):
         with pytest.raises(gp.GpError):
             B.set_options(**bad)
+
+
+def test_batch_autotune(gp):
+    """The tuner installs one of its candidates per axis and the results stay
+    the oracle's."""
+    graphs = uneven_graphs()
+    G = [gp.Graph.from_graphgen(g) for g in graphs]
+    k = 64
+    B = gp.Batch(G, k_ppr=k)
+    seeds = np.stack([seeds_for(g, k, 200 + i) for i, g in enumerate(graphs)])
+    srcs = np.stack([np.resize(gg.pick_vertices(g, 64, seed=210 + i, min_out_degree=0), 64)
+                     for i, g in enumerate(graphs)]).astype(np.int32)
+    r = B.autotune(seeds, srcs, ppr_sweeps=4)
+    o = r["options"]
+    assert r["trials"] == 5 + 3 + 5 + 6 + 3 and r["ppr_ms"] > 0 and r["msbfs_ms"] > 0
+    assert o["big_in_degree"] in (8, 16, 32, 64, 128) and o["chunk_edges"] in (64, 128, 256)
+    assert o["l2_budget_mb"] in (48, 64, 96, 128, 192) and o["msbfs_alpha"] in (2, 4, 8, 16, 32, 64)
+    assert o["msbfs_beta"] in (8, 24, 64) and B.options() == o
+    outs, done, _ = B.ppr(seeds, iters=500, tol=1e-6)
+    louts, _ = B.msbfs(srcs)
+    for i, g in enumerate(graphs):
+        O = oracle.OracleGraph.from_graph(g)
+        for j in (0, k - 1):
+            e = np.zeros(g.n)
+            e[seeds[i, j]] = 1.0
+            ref, _, _, _ = O.pagerank(oracle.PULL, 0.85, iters=int(done[i, j]), personalization=e, x0=e)
+            assert np.abs(outs[i][:, j].cpu().numpy() - ref).max() <= MAX_ABS
+            lref, _ = O.bfs(int(srcs[i, j]))
+            assert np.array_equal(louts[i].cpu().numpy()[:, j], lref)
