@@ -881,6 +881,9 @@ def run_batched(args, graphs_scales=None):
                              "achieved": round(comp_bytes / (kms * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
                              "frac": round(comp_bytes / (kms * 1e-3) / 1e9 / peak, 4), "peak_kind": peak_kind,
                              "l2_gather_gbs": round(gath_bytes / (kms * 1e-3) / 1e9, 1)},
+            "ppr_sweeps_per_vector": {"median": float(np.median(done)), "p90": float(np.percentile(done, 90)),
+                                      "max": int(done.max()),
+                                      "graph_max_median": float(np.median(done.max(axis=1)))},
             "ppr_batched_ms_all": [round(x * 1e3, 2) for x in tp],
             "ppr_serial_ms_all": [round(x * 1e3, 1) for x in ts]}
 
