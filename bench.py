@@ -54,13 +54,16 @@ def parse_args(argv=None):
     p.add_argument("--quiet", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-legs", action="store_true", help="skip the per-configuration push/pull legs")
-    p.add_argument("--only", choices=["pr_pull", "pr_push", "bfs", "batched", "sssp", "tc", "pr_fe", "bc"], default=None,
+    p.add_argument("--only", choices=["pr_pull", "pr_push", "bfs", "batched", "sssp", "tc", "pr_fe", "bc", "pr_shapes"],
+                   default=None,
                    help="profiling case: run only this part (fixed --sweeps for PageRank), no contract line")
     p.add_argument("--sweeps", type=int, default=4)
     p.add_argument("--batch-scale", type=int, default=None,
                    help="--only batched: one R-MAT graph of this scale instead of the 32-graph workload")
     p.add_argument("--delta", type=float, default=64.0, help="--only sssp: bucket width")
-    p.add_argument("--mode", choices=["push", "pull", "auto"], default="auto", help="--only sssp: direction mode")
+    p.add_argument("--mode", choices=["push", "pull", "auto"], default="auto",
+                   help="--only sssp / --only bfs: direction mode")
+    p.add_argument("--no-batch-tune", action="store_true", help="--only batched: keep the default batch options")
     p.add_argument("--opt", action="append", default=[], metavar="KEY=VALUE",
                    help="gp_options override for the profiling case (repeatable)")
     return p.parse_args(argv)
@@ -799,7 +802,7 @@ def run_batched(args, graphs_scales=None):
     B = gp.Batch(G, k_ppr=K)
     seeds = np.stack([np.resize(gg.pick_vertices(g, K, seed=6 + 1000 * i), K) for i, g in enumerate(graphs)])
     srcs = np.stack([np.resize(gg.pick_vertices(g, NSRC, seed=7 + 1000 * i), NSRC) for i, g in enumerate(graphs)])
-    tuned = B.autotune(seeds, srcs)  # outside the timed region
+    tuned = {"trials": 0} if getattr(args, "no_batch_tune", False) else B.autotune(seeds, srcs)  # outside the timed region
     B.ppr(seeds, iters=1000, tol=1e-6)  # captures the CUDA graph
     B.msbfs(srcs)
     torch.cuda.synchronize()
@@ -896,6 +899,8 @@ def run_only(args):
     import paper_2010_16012_gb300 as gp
 
     gp.load()
+    if args.only == "pr_shapes":
+        return run_only_pr_shapes(args)
     if args.only == "batched":
         import graphgen as gg
 
@@ -931,8 +936,9 @@ def run_only(args):
             gp.profile_read(reset=True)
             gp.profile_enable(True)
         if args.only == "bfs":
+            bmode = {"push": gp.PUSH, "pull": gp.PULL, "auto": gp.AUTO}[args.mode]
             for s in srcs:
-                _, _, st = gp.bfs(G, int(s), gp.AUTO)
+                _, _, st = gp.bfs(G, int(s), bmode)
             # the last search's levels: direction, frontier, edges examined, device time
             res = {"levels": st["levels"], "reached": st["reached"], "init_us": round(st["init_us"], 1),
                    "level_table": [[d, f, e, round(t, 1)] for d, f, e, t in
@@ -940,7 +946,9 @@ def run_only(args):
         else:
             mode = gp.PULL if args.only == "pr_pull" else gp.PUSH
             _, st = gp.pagerank(G, mode, 0.85, args.sweeps, 0.0, out=out)
-            res = {"sweeps": st["iters_done"]}
+            res = {"sweeps": st["iters_done"], "push_updates_l2": st["push_updates_l2"],
+                   "push_updates_shared": st["push_updates_shared"], "push_updates_merged": st["push_updates_merged"],
+                   "push_flush_l2": st["push_flush_l2"], "m": g.m}
     torch.cuda.synchronize()
     gp.profile_enable(False)
     kt = gp.profile_read(reset=True)
@@ -1106,6 +1114,62 @@ def run_only_tc(args):
                              "ms": round(dt * 1e3, 1), "gteps": round(g.m / dt / 1e9, 4)}
         out["equals_oracle"] = bool(np.array_equal(counts["pull"], ref))
     print(json.dumps({"profile_case": "tc", "scale": args.scale, "n": g.n, "m": g.m, "opts": opts, **out}), flush=True)
+    return 0
+
+
+def run_only_pr_shapes(args):
+    """PageRank push against pull on graphs of several shapes, with the default
+    options and after gp_autotune (the calibration of GP_AUTO): CUDA-event time
+    of --sweeps fixed sweeps, median of 3, per sweep."""
+    import torch
+
+    import graphgen as gg
+    import paper_2010_16012_gb300 as gp
+
+    def per_sweep(G, n, mode, sweeps):
+        out = torch.empty(n, device="cuda")
+        gp.pagerank(G, mode, 0.85, sweeps, 0.0, out=out)
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            gp.pagerank(G, mode, 0.85, sweeps, 0.0, out=out)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return round(statistics.median(ts) / sweeps, 4)
+
+    shapes = [
+        ("rmat20_sym", lambda: gg.rmat(20, 16, seed=1)),
+        ("rmat20_dir", lambda: gg.rmat(20, 16, seed=1, symmetrize=False)),
+        ("rmat20_ef64_sym", lambda: gg.rmat(20, 64, seed=1)),
+        ("rmat16_sym", lambda: gg.rmat(16, 16, seed=1)),
+        ("dst_skew20_dir", lambda: gg.rmat(20, 16, a=0.45, b=0.05, c=0.45, seed=1, symmetrize=False)),
+        ("dst_skew22_dir", lambda: gg.rmat(22, 16, a=0.45, b=0.05, c=0.45, seed=1, symmetrize=False)),
+        ("src_skew20_dir", lambda: gg.rmat(20, 16, a=0.45, b=0.45, c=0.05, seed=1, symmetrize=False)),
+        ("er22", lambda: gg.erdos_renyi(1 << 22, 16 << 22, seed=3)),
+    ]
+    sweeps = max(args.sweeps, 20)
+    out = {}
+    for name, make in shapes:
+        g = make()
+        G = gp.Graph.from_graphgen(g)
+        r = {"n": g.n, "m": g.m, "pull_default_ms": per_sweep(G, g.n, gp.PULL, sweeps),
+             "push_default_ms": per_sweep(G, g.n, gp.PUSH, sweeps)}
+        t = gp.autotune(G, gp.TUNE_PULL | gp.TUNE_PUSH | gp.TUNE_AUTO, use_cache=False)
+        r["pull_tuned_ms"] = per_sweep(G, g.n, gp.PULL, sweeps)
+        r["push_tuned_ms"] = per_sweep(G, g.n, gp.PUSH, sweeps)
+        r["auto_tuned"] = "push" if t["options"]["pr_auto_mode"] == gp.PUSH else "pull"
+        _, st = gp.pagerank(G, gp.AUTO, 0.85, 1, 0.0)
+        G.free()
+        G = gp.Graph.from_graphgen(g)
+        _, st = gp.pagerank(G, gp.AUTO, 0.85, 1, 0.0)
+        r["auto_untuned"] = "push" if st["mode_used"] == gp.PUSH else "pull"
+        G.free()
+        out[name] = r
+        log(f"[bench] {name}: {r}")
+    print(json.dumps({"profile_case": "pr_shapes", "sweeps": sweeps, **out}), flush=True)
     return 0
 
 

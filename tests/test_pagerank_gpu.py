@@ -346,3 +346,26 @@ def test_push_update_counts(gp, oi):
         _, st = gp.pagerank(G, gp.PUSH, 0.85, 300, 1e-5)
         total = st["push_updates_l2"] + st["push_updates_shared"] + st["push_updates_merged"]
         assert total == g.m * st["iters_done"]
+
+
+def test_auto_without_tuning_picks_the_faster_direction(gp):
+    """GP_AUTO with no tuning result resolves to pull, the direction measured
+    faster on every graph shape (R-MAT, destination-skewed R-MAT,
+    Erdos-Renyi); checked here by timing both on three of them."""
+    import torch
+
+    for g in (gg.rmat(18, 16, seed=1), gg.rmat(18, 16, a=0.45, b=0.05, c=0.45, seed=1, symmetrize=False),
+              gg.erdos_renyi(1 << 18, 16 << 18, seed=3)):
+        G = gp.Graph.from_graphgen(g)
+        _, st = gp.pagerank(G, gp.AUTO, 0.85, 2, 0.0)
+        assert st["mode_used"] == gp.PULL
+        t = {}
+        for mode in (gp.PULL, gp.PUSH):
+            gp.pagerank(G, mode, 0.85, 5, 0.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            gp.pagerank(G, mode, 0.85, 20, 0.0)
+            e1.record()
+            e1.synchronize()
+            t[mode] = e0.elapsed_time(e1)
+        assert t[gp.PULL] < t[gp.PUSH], (g.name, t)
