@@ -107,7 +107,11 @@ int gp_set_allocator(gp_alloc_fn alloc, gp_free_fn free_fn, void *ctx);
  * bytes handed out and not yet freed (used); both are 0 before first use.
  * gp_pool_trim synchronises the current device, then returns held memory to
  * the driver until at most keep_bytes stay reserved (memory in use is never
- * released).  Neither touches memory of a registered allocator (gp_set_allocator). */
+ * released).  Neither touches memory of a registered allocator (gp_set_allocator).
+ * The small page-locked host blocks a graph uses for the kernels' status words
+ * are kept in the same way when the graph is freed (page-locking is a driver
+ * call that can take milliseconds) and reused by later graphs; gp_pool_trim
+ * also frees the kept ones. */
 int gp_pool_usage(int64_t *reserved_bytes, int64_t *used_bytes);
 int gp_pool_trim(int64_t keep_bytes);
 

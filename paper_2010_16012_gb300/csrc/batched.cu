@@ -695,7 +695,7 @@ extern "C" int gp_batch_create(gp_batch **out, gp_graph *const *graphs, int ngra
     auto fail = [&](int st) {
         b->layout.release(s);
         b->mem.release(s);
-        if (b->hcounters) cudaFreeHost(b->hcounters);
+        pinned_free(b->hcounters, 8 * sizeof(int32_t));
         delete b;
         return st;
     };
@@ -744,8 +744,10 @@ extern "C" int gp_batch_create(gp_batch **out, gp_graph *const *graphs, int ngra
     if (st == GP_OK) st = b->mem.alloc(sync, 1, s);
     if (st != GP_OK) return fail(st);
     {
-        cudaError_t e = cudaMallocHost(&b->hcounters, 8 * sizeof(int32_t));
-        if (e != cudaSuccess) return fail(set_error(GP_ERR_CUDA, "gp_batch_create: %s", cudaGetErrorString(e)));
+        void *h = nullptr;
+        st = pinned_alloc(&h, 8 * sizeof(int32_t));
+        if (st != GP_OK) return fail(st);
+        b->hcounters = (int32_t *)h;
     }
     D.graphs = b->dgraphs;
     D.seeds = b->seeds;
@@ -792,7 +794,7 @@ extern "C" int gp_batch_free(gp_batch *b) {
     if (b->bfs_exec) cudaGraphExecDestroy(b->bfs_exec);
     b->layout.release(b->home);
     b->mem.release(b->home);
-    if (b->hcounters) cudaFreeHost(b->hcounters);
+    pinned_free(b->hcounters, 8 * sizeof(int32_t));
     cudaError_t e = cudaStreamSynchronize(b->home);
     delete b;
     if (e != cudaSuccess) return set_error(GP_ERR_CUDA, "gp_batch_free: %s", cudaGetErrorString(e));

@@ -865,13 +865,16 @@ struct gp_bc_work {
 
 namespace gp {
 
+// host mirror: summary, per-step statistics, barrier status
+constexpr size_t BC_HOST_BYTES = sizeof(BcSummary) + GP_BC_MAX_STEPS * sizeof(BcStepStat) + sizeof(GridSync);
+
 void release_bc_work(gp_graph *g, cudaStream_t s) {
     if (!g->bc) return;
     if (g->bc->done_ev) {
         cudaEventSynchronize(g->bc->done_ev);
         cudaEventDestroy(g->bc->done_ev);
     }
-    if (g->bc->host) cudaFreeHost(g->bc->host);
+    pinned_free(g->bc->host, BC_HOST_BYTES);
     g->bc->mem.release(s);
     g->bc->src_mem.release(s);
     g->bc->hub_out.mem.release(s);
@@ -918,7 +921,7 @@ static int ensure_bc_work(gp_graph *g, cudaStream_t s) {
     GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bc_persistent, BC_THREADS, 0));
     if (per_sm < 1) return set_error(GP_ERR_UNSUPPORTED, "BC kernel does not fit on an SM");
     w.grid = per_sm * g->num_sms;
-    GP_CUDA(cudaMallocHost(&w.host, sizeof(BcSummary) + GP_BC_MAX_STEPS * sizeof(BcStepStat) + sizeof(GridSync)));
+    GP_TRY(pinned_alloc(&w.host, BC_HOST_BYTES));
     GP_CUDA(cudaEventCreateWithFlags(&w.done_ev, cudaEventDisableTiming));
     w.ready = true;
     return GP_OK;

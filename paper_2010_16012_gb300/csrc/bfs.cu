@@ -663,12 +663,15 @@ __global__ void k_nzin_bits(int64_t n, const int64_t *csc_off, uint32_t *bits) {
     }
 }
 
+// host mirror: summary, per-level statistics, barrier status
+constexpr size_t BFS_HOST_BYTES = sizeof(BfsSummary) + GP_BFS_MAX_LEVELS * sizeof(BfsLevelStat) + sizeof(GridSync);
+
 void release_bfs_work(gp_graph *g, cudaStream_t s) {
     if (g->bfs.done_ev) {
         cudaEventSynchronize(g->bfs.done_ev);
         cudaEventDestroy(g->bfs.done_ev);
     }
-    if (g->bfs.ctr_host) cudaFreeHost(g->bfs.ctr_host);
+    pinned_free(g->bfs.ctr_host, BFS_HOST_BYTES);
     g->bfs.ctr_host = nullptr;
     g->bfs.mem.release(s);
     g->bfs = BfsWork();
@@ -711,7 +714,7 @@ static int ensure_bfs_work(gp_graph *g, cudaStream_t s) {
     GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs_persistent, BFS_THREADS, 0));
     if (per_sm < 1) return set_error(GP_ERR_UNSUPPORTED, "BFS kernel does not fit on an SM");
     w.grid = per_sm * g->num_sms;
-    GP_CUDA(cudaMallocHost(&w.ctr_host, sizeof(BfsSummary) + GP_BFS_MAX_LEVELS * sizeof(BfsLevelStat) + sizeof(GridSync)));
+    GP_TRY(pinned_alloc(&w.ctr_host, BFS_HOST_BYTES));
     GP_CUDA(cudaEventCreateWithFlags(&w.done_ev, cudaEventDisableTiming));
     w.ready = true;
     return GP_OK;

@@ -48,6 +48,9 @@ struct DevBuf {
 // Allocate `bytes` of device memory through the registered allocator.
 int dev_alloc(DevBuf &b, size_t bytes, cudaStream_t s);
 void dev_free(DevBuf &b, cudaStream_t s);
+// Page-locked host blocks (status mirrors), reused across graphs.
+int pinned_alloc(void **p, size_t bytes);
+void pinned_free(void *p, size_t bytes);
 
 // Owned allocations of a handle (freed together).
 struct Arena {

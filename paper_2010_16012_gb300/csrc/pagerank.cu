@@ -165,6 +165,15 @@ __device__ __forceinline__ float gather_c(const float *__restrict__ c, const flo
     return __ldg(c + u);
 }
 
+// The same gather with the hot contributions read from their compact global
+// copy (pull_light: its few hot gathers do not pay for a shared-memory copy,
+// whose size would also cut the light kernel's resident blocks).
+template <bool HOT>
+__device__ __forceinline__ float gather_c_glob(const float *__restrict__ c, const float *__restrict__ c_hot, int32_t u) {
+    if (HOT && u < 0) return __ldg(c_hot + (u & 0x7fffffff));
+    return __ldg(c + u);
+}
+
 constexpr int BIG_UNROLL = 8;
 
 // Index arrays are streamed once per sweep: loaded with the evict-first hint so
@@ -241,14 +250,12 @@ constexpr int LIGHT_UNROLL = 8;  // in-edges of a light vertex in flight per lan
 
 template <bool W, bool HOT>
 __global__ void __launch_bounds__(512, GP_LIGHT_MIN_BLOCKS) k_pull_light(PrArgs a) {
-    extern __shared__ float sh_hot[];
     __shared__ double sm[32];
     if (((volatile PrStatus *)a.status)->done) return;
     const int lane = lane_id();
     ResSum res;
     const int64_t n = a.n;
     if ((int)blockIdx.x < a.split_blocks) {
-        load_hot<HOT>(a, sh_hot);
         const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
         const int64_t nwarps = ((int64_t)a.split_blocks * blockDim.x) >> 5;
         const int64_t ntiles = (n + 31) >> 5;
@@ -293,7 +300,7 @@ __global__ void __launch_bounds__(512, GP_LIGHT_MIN_BLOCKS) k_pull_light(PrArgs 
                 for (int q = 0; q < LIGHT_UNROLL; ++q) {
                     f[q] = 0.f;
                     if (p0 + q < e1) {
-                        f[q] = gather_c<HOT>(c, sh_hot, u[q]);
+                        f[q] = gather_c_glob<HOT>(c, a.c_hot, u[q]);
                         if (W) f[q] *= __ldg(wv + p0 + q);
                     }
                 }
@@ -588,7 +595,7 @@ __global__ void __launch_bounds__(256) k_grad_w(GradArgs a) {
 // ------------------------------------------------------------------ driver
 
 void release_pr_work(gp_graph *g, cudaStream_t s) {
-    if (g->pr.status_host) cudaFreeHost(g->pr.status_host);
+    pinned_free(g->pr.status_host, 4 * sizeof(PrStatus));
     g->pr.status_host = nullptr;
     g->pr.mem.release(s);
     g->pr = PrWork();
@@ -619,7 +626,7 @@ static int ensure_pr_work(gp_graph *g, cudaStream_t s) {
     PrStatus *st = nullptr;
     GP_TRY(w.mem.alloc(st, 1, s));
     w.status = st;
-    GP_CUDA(cudaMallocHost(&w.status_host, 4 * sizeof(PrStatus)));
+    GP_TRY(pinned_alloc(&w.status_host, 4 * sizeof(PrStatus)));
     w.ready = true;
     return GP_OK;
 }
@@ -744,7 +751,7 @@ static int pr_iterate(gp_graph *g, const IterSpec &sp, float *out, PrStatus &fin
         const void *kl_ = W ? (hot ? (const void *)k_pull_light<true, true> : (const void *)k_pull_light<true, false>)
                             : (hot ? (const void *)k_pull_light<false, true> : (const void *)k_pull_light<false, false>);
         GP_TRY(occupancy(kb_, tbp, smem, ob));
-        GP_TRY(occupancy(kl_, tbl, smem, ol));
+        GP_TRY(occupancy(kl_, tbl, 0, ol));
         const int wpb = tbp / 32, wpl = tbl / 32;
         g1 = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ob * g->num_sms, (bins.nchunks + wpb - 1) / wpb));
         split = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ol * g->num_sms, (ntiles + wpl - 1) / wpl));
@@ -790,13 +797,13 @@ static int pr_iterate(gp_graph *g, const IterSpec &sp, float *out, PrStatus &fin
             b.c_next = C[k & 1];
             if (W && hot) {
                 GP_LAUNCH("pull_big", s, (k_pull_big<true, true><<<g1, tbp, smem, s>>>(b)));
-                GP_LAUNCH("pull_light", s, (k_pull_light<true, true><<<g2, tbl, smem, s>>>(b)));
+                GP_LAUNCH("pull_light", s, (k_pull_light<true, true><<<g2, tbl, 0, s>>>(b)));
             } else if (W) {
                 GP_LAUNCH("pull_big", s, (k_pull_big<true, false><<<g1, tbp, 0, s>>>(b)));
                 GP_LAUNCH("pull_light", s, (k_pull_light<true, false><<<g2, tbl, 0, s>>>(b)));
             } else if (hot) {
                 GP_LAUNCH("pull_big", s, (k_pull_big<false, true><<<g1, tbp, smem, s>>>(b)));
-                GP_LAUNCH("pull_light", s, (k_pull_light<false, true><<<g2, tbl, smem, s>>>(b)));
+                GP_LAUNCH("pull_light", s, (k_pull_light<false, true><<<g2, tbl, 0, s>>>(b)));
             } else {
                 GP_LAUNCH("pull_big", s, (k_pull_big<false, false><<<g1, tbp, 0, s>>>(b)));
                 GP_LAUNCH("pull_light", s, (k_pull_light<false, false><<<g2, tbl, 0, s>>>(b)));

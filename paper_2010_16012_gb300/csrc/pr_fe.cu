@@ -409,9 +409,12 @@ struct gp_fe_work {
 
 namespace gp {
 
+// host mirror: summary, per-iteration statistics, barrier status
+constexpr size_t FE_HOST_BYTES = sizeof(FeSummary) + GP_FE_MAX_ITERS * sizeof(FeIterStat) + sizeof(GridSync);
+
 void release_fe_work(gp_graph *g, cudaStream_t s) {
     if (!g->fe) return;
-    if (g->fe->host) cudaFreeHost(g->fe->host);
+    pinned_free(g->fe->host, FE_HOST_BYTES);
     g->fe->mem.release(s);
     delete g->fe;
     g->fe = nullptr;
@@ -441,7 +444,7 @@ static int ensure_fe_work(gp_graph *g, cudaStream_t s) {
     GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pr_fe, FE_THREADS, 0));
     if (per_sm < 1) return set_error(GP_ERR_UNSUPPORTED, "Frontier-Exploit PageRank kernel does not fit on an SM");
     w.grid = per_sm * g->num_sms;
-    GP_CUDA(cudaMallocHost(&w.host, sizeof(FeSummary) + GP_FE_MAX_ITERS * sizeof(FeIterStat) + sizeof(GridSync)));
+    GP_TRY(pinned_alloc(&w.host, FE_HOST_BYTES));
     w.ready = true;
     return GP_OK;
 }

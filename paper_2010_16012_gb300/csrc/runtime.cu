@@ -8,6 +8,8 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "gp_internal.cuh"
 
@@ -80,6 +82,53 @@ static cudaMemPool_t lib_pool() {
         g_pool[dev] = pool;
     }
     return g_pool[dev];
+}
+
+// Page-locked host blocks.  Every graph takes a few small ones (the host
+// mirrors of the kernels' status words); page-locking is a driver call that
+// pins pages and now and then takes milliseconds, so a freed block is kept and
+// handed out again for the same size (gp_pool_trim releases the kept ones).
+// Portable: one block may serve graphs on any device.
+static std::mutex g_pin_mu;
+static std::vector<std::pair<size_t, void *>> g_pin_free;
+constexpr size_t PIN_KEEP_MAX = 256;
+
+int pinned_alloc(void **p, size_t bytes) {
+    *p = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        for (size_t i = 0; i < g_pin_free.size(); ++i) {
+            if (g_pin_free[i].first == bytes) {
+                *p = g_pin_free[i].second;
+                g_pin_free[i] = g_pin_free.back();
+                g_pin_free.pop_back();
+                return GP_OK;
+            }
+        }
+    }
+    GP_CUDA(cudaHostAlloc(p, bytes, cudaHostAllocPortable));
+    return GP_OK;
+}
+
+void pinned_free(void *p, size_t bytes) {
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        if (g_pin_free.size() < PIN_KEEP_MAX) {
+            g_pin_free.emplace_back(bytes, p);
+            return;
+        }
+    }
+    cudaFreeHost(p);
+}
+
+static void pinned_release_all() {
+    std::vector<std::pair<size_t, void *>> blocks;
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        blocks.swap(g_pin_free);
+    }
+    for (auto &b : blocks) cudaFreeHost(b.second);
 }
 
 int dev_alloc(DevBuf &b, size_t bytes, cudaStream_t s) {
@@ -742,6 +791,7 @@ int gp_pool_usage(int64_t *reserved_bytes, int64_t *used_bytes) {
 int gp_pool_trim(int64_t keep_bytes) {
     clear_error();
     if (keep_bytes < 0) return set_error(GP_ERR_INVALID, "gp_pool_trim: keep_bytes %lld < 0", (long long)keep_bytes);
+    pinned_release_all();
     int dev = 0;
     GP_CUDA(cudaGetDevice(&dev));
     cudaMemPool_t pool = nullptr;
@@ -768,7 +818,7 @@ int gp_options_default(gp_options *opt) {
     opt->bfs_alpha = 14.0f;
     opt->bfs_beta = 24.0f;
     opt->push_fp64_accum = -1;
-    opt->pull_hot_slots = 16384;
+    opt->pull_hot_slots = 20480;
     opt->push_hot_slots = 16384;
     opt->sssp_alpha = 1.0f;
     opt->fe_alpha = 8.0f;

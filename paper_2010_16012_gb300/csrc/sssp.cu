@@ -579,13 +579,16 @@ struct gp_sssp_work {
 
 namespace gp {
 
+// host mirror: summary, per-iteration statistics, barrier status
+constexpr size_t SS_HOST_BYTES = sizeof(SsSummary) + GP_SSSP_MAX_ITERS * sizeof(SsIterStat) + sizeof(GridSync);
+
 void release_sssp_work(gp_graph *g, cudaStream_t s) {
     if (!g->sssp) return;
     if (g->sssp->done_ev) {
         cudaEventSynchronize(g->sssp->done_ev);
         cudaEventDestroy(g->sssp->done_ev);
     }
-    if (g->sssp->host) cudaFreeHost(g->sssp->host);
+    pinned_free(g->sssp->host, SS_HOST_BYTES);
     g->sssp->mem.release(s);
     delete g->sssp;
     g->sssp = nullptr;
@@ -619,7 +622,7 @@ static int ensure_sssp_work(gp_graph *g, cudaStream_t s) {
     GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sssp_persistent, SS_THREADS, 0));
     if (per_sm < 1) return set_error(GP_ERR_UNSUPPORTED, "SSSP kernel does not fit on an SM");
     w.grid = per_sm * g->num_sms;
-    GP_CUDA(cudaMallocHost(&w.host, sizeof(SsSummary) + GP_SSSP_MAX_ITERS * sizeof(SsIterStat) + sizeof(GridSync)));
+    GP_TRY(pinned_alloc(&w.host, SS_HOST_BYTES));
     GP_CUDA(cudaEventCreateWithFlags(&w.done_ev, cudaEventDisableTiming));
     w.ready = true;
     return GP_OK;
