@@ -4,7 +4,8 @@
 One step runs the whole hot path once on the graph already resident in HBM:
   gp_graph_upload (validation + degree preparation + degree bins),
   gp_pagerank PULL, PUSH and AUTO, each to L1 tolerance 1e-7 (cap 300 sweeps),
-  gp_bfs AUTO (direction-switching) from 64 random non-isolated sources.
+  gp_bfs_multi AUTO (direction-switching) from 64 random non-isolated sources,
+  all searches in one launch (groups of blocks searching concurrently).
 Metric: traversed edges per second (GTEPS): m per PageRank sweep, and for BFS
 the undirected edges of the reached component (Graph500 convention, the graph
 being symmetric).  One JSON line on rank 0.
@@ -58,6 +59,8 @@ def parse_args(argv=None):
                    default=None,
                    help="profiling case: run only this part (fixed --sweeps for PageRank), no contract line")
     p.add_argument("--sweeps", type=int, default=4)
+    p.add_argument("--bfs-groups", type=int, default=0,
+                   help="groups of blocks of gp_bfs_multi in the step (0: the library's choice)")
     p.add_argument("--batch-scale", type=int, default=None,
                    help="--only batched: one R-MAT graph of this scale instead of the 32-graph workload")
     p.add_argument("--delta", type=float, default=64.0, help="--only sssp: bucket width")
@@ -202,7 +205,7 @@ def pick_sources(g, count: int):
 
 
 KERNEL_SOURCE = {"pull_big": "pagerank.cu", "pull_light": "pagerank.cu", "push_scatter": "pagerank.cu",
-                 "push_epilogue": "pagerank.cu", "bfs_persistent": "bfs.cu"}
+                 "push_epilogue": "pagerank.cu", "bfs_persistent": "bfs.cu", "bfs_multi": "bfs.cu"}
 
 
 def source_key(cu_name: str) -> str:
@@ -301,8 +304,9 @@ def run_ours(args, dist: Dist):
     idx = torch.from_numpy(g.csr_idx).to(dev)
     n, m = g.n, g.m
     ranks = [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(3)]
-    level = torch.empty(n, dtype=torch.int32, device=dev)
-    parent = torch.empty(n, dtype=torch.int32, device=dev)
+    # one level and one parent vector per search (gp_bfs_multi writes all of them)
+    lv_all = [torch.empty(n, dtype=torch.int32, device=dev) for _ in srcs]
+    pa_all = [torch.empty(n, dtype=torch.int32, device=dev) for _ in srcs]
     modes = [(gp.PULL, "pull"), (gp.PUSH, "push"), (gp.AUTO, "auto")]
 
     # autotune once (outside the timed region; cached by graph statistics), then
@@ -338,15 +342,19 @@ def run_ours(args, dist: Dist):
                     w = work.setdefault(kn, [0.0, 0])
                     w[0] += kb[kn] * k
                     w[1] += k
-        # The first pass (a warm-up step) waits for each search and keeps its
-        # statistics; the component sizes and level counts are properties of the
-        # source, so later steps enqueue all searches back to back without them.
+        # The first pass (a warm-up step) runs each search on its own and keeps
+        # its per-level statistics; the component sizes and level counts are
+        # properties of the source (the direction decisions depend only on the
+        # frontier counters), so later steps run all searches in one
+        # gp_bfs_multi launch (groups of blocks searching concurrently).
         first = not bfs_stats
         ta = time.perf_counter()
-        for s in srcs:
-            _, _, st = gp.bfs(G, int(s), gp.AUTO, level=level, parent=parent, want_stats=first)
-            if first:
+        if first:
+            for s in srcs:
+                _, _, st = gp.bfs(G, int(s), gp.AUTO, level=lv_all[0], parent=pa_all[0])
                 bfs_stats[int(s)] = st
+        else:
+            gp.bfs_multi(G, srcs, gp.AUTO, levels=lv_all, parents=pa_all, groups=args.bfs_groups, want_summary=False)
         torch.cuda.synchronize()
         bfs_ms = (time.perf_counter() - ta) * 1e3
         bfs_edges, switches = 0.0, 0
@@ -356,17 +364,18 @@ def run_ours(args, dist: Dist):
             edges += e
             bfs_edges += e
             switches += st["switches"]
-            if work is not None:  # one launch per search: the sum of its levels' bytes
+            if work is not None:  # one launch for all searches: the sum of their levels' bytes
                 seen, by = 0, 0
                 fr = st["frontier"] + [0]
                 for L, d in enumerate(st["direction"]):
                     seen += fr[L]
                     by += bfs_level_bytes(n, d, fr[L], st["examined"][L], n_in - seen, fr[L + 1])[1]
-                w = work.setdefault("bfs_persistent", [0.0, 0])
-                w[0] += by
-                w[1] += 1
+                work.setdefault("bfs_multi", [0.0, 0])[0] += by
+        if work is not None and not first:
+            work["bfs_multi"][1] += 1
         parts["bfs_auto"] = {"sources": len(srcs), "ms": bfs_ms, "gteps_total": bfs_edges / bfs_ms / 1e6,
-                             "switches_per_source": switches / max(len(srcs), 1)}
+                             "switches_per_source": switches / max(len(srcs), 1),
+                             "launch": "one gp_bfs_multi launch" if not first else "one gp_bfs launch per source"}
         G.free()
         return edges, parts
 
@@ -495,17 +504,22 @@ def pr_leg(gp, g, G, mode: int, sweeps: int, peak: float, repeats: int = 3, tol:
             "bytes_per_sweep": pr_sweep_bytes(g, mode, weighted), "converged": bool(res["converged"])}
 
 
-def bfs_leg(gp, g, G, srcs, mode: int, peak: float, undirected: bool, repeats: int = 3):
-    """Searches from every source in one direction mode, enqueued back to back
-    (statistics from a first, untimed pass).  GTEPS: undirected edges of the
-    reached component (Graph500) or, for a directed graph, out-edges of the
-    reached vertices, over the time; also the adjacency entries examined per
-    second and the fraction of the HBM peak on the per-level compulsory bytes."""
+def bfs_leg(gp, g, G, srcs, mode: int, peak: float, undirected: bool, repeats: int = 3, groups=None):
+    """Searches from every source in one direction mode: one gp_bfs launch per
+    source enqueued back to back, or (groups not None) all of them in one
+    gp_bfs_multi launch with that many groups (statistics from a first, untimed
+    pass of single searches).  GTEPS: undirected edges of the reached component
+    (Graph500) or, for a directed graph, out-edges of the reached vertices, over
+    the time; also the adjacency entries examined per second and the fraction
+    of the HBM peak on the per-level compulsory bytes."""
     import torch
 
     n = g.n
     level = torch.empty(n, dtype=torch.int32, device="cuda")
     parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    if groups is not None:
+        lv_all = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in srcs]
+        pa_all = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in srcs]
     n_in = int(np.count_nonzero(np.diff(g.csc_off)))
     edges = examined = by = 0.0
     levels = switches = 0
@@ -522,11 +536,15 @@ def bfs_leg(gp, g, G, srcs, mode: int, peak: float, undirected: bool, repeats: i
             by += bfs_level_bytes(n, d, fr[L], st["examined"][L], n_in - seen, fr[L + 1])[1]
 
     def run():
+        if groups is not None:
+            gp.bfs_multi(G, srcs, mode, levels=lv_all, parents=pa_all, groups=groups, want_summary=False)
+            return
         for s in srcs:
             gp.bfs(G, int(s), mode, level=level, parent=parent, want_stats=False)
 
     t = statistics.median(_events_ms(run, repeats))
-    return {"sources": len(srcs), "ms_per_search": round(t / len(srcs), 4), "gteps": round(edges / t / 1e6, 2),
+    out = {"launch": "gp_bfs_multi" if groups is not None else "gp_bfs per source"}
+    return {**out, "sources": len(srcs), "ms_per_search": round(t / len(srcs), 4), "gteps": round(edges / t / 1e6, 2),
             "examined_per_s_g": round(examined / t / 1e6, 2), "levels_per_search": round(levels / len(srcs), 2),
             "switches_per_search": round(switches / len(srcs), 2),
             "hbm_frac": round(by / (t * 1e-3) / 1e9 / peak, 4)}
@@ -538,10 +556,11 @@ def run_legs(args, g2, srcs2, tuned_opts):
       C1  R-MAT scale 14 (seed 1): PageRank push and pull, exactly 20 sweeps
           from 1/n; BFS from vertex 0 top-down, bottom-up and switching;
       C2  R-MAT scale 22: BFS from the 64 step sources forced top-down,
-          forced bottom-up and switching;
+          forced bottom-up and switching, one launch per search and all
+          searches in one gp_bfs_multi launch;
       C3  directed Erdos-Renyi G(2^24, 16*2^24 draws) (seed 3): PageRank pull
-          and push, 20 sweeps; BFS top-down and bottom-up from 16 sources with
-          out-degree > 0 (seed 4);
+          and push, 20 sweeps; BFS top-down, bottom-up and switching from 16
+          sources with out-degree > 0 (seed 4), per source and in one launch;
       C5  weighted R-MAT scale 20 (seed 8, weights U(0,1] seed 9, normalised
           per source): forward PageRank to L1 tol 1e-10 (cap 300) and the
           adjoint for L = g.x, g ~ N(0,1) (seed 10), to the same tolerance."""
@@ -557,6 +576,9 @@ def run_legs(args, g2, srcs2, tuned_opts):
     G.set_options(**tuned_opts)
     legs["c2_bfs"] = {name: bfs_leg(gp, g2, G, srcs2, mode, peak, True, repeats=2)
                       for name, mode in (("top_down", gp.PUSH), ("bottom_up", gp.PULL), ("auto", gp.AUTO))}
+    legs["c2_bfs"].update({name + "_multi": bfs_leg(gp, g2, G, srcs2, mode, peak, True, repeats=2,
+                                                     groups=args.bfs_groups)
+                           for name, mode in (("top_down", gp.PUSH), ("bottom_up", gp.PULL), ("auto", gp.AUTO))})
     G.free()
     # C1
     t = time.time()
@@ -583,6 +605,7 @@ def run_legs(args, g2, srcs2, tuned_opts):
         c3[name] = pr_leg(gp, g3, G, mode, 20, peak)
     c3["bfs"] = {name: bfs_leg(gp, g3, G, s3, mode, peak, False, repeats=2)
                  for name, mode in (("top_down", gp.PUSH), ("bottom_up", gp.PULL), ("auto", gp.AUTO))}
+    c3["bfs"]["auto_multi"] = bfs_leg(gp, g3, G, s3, gp.AUTO, peak, False, repeats=2, groups=args.bfs_groups)
     G.free()
     del g3
     legs["c3_er24"] = c3
@@ -612,14 +635,15 @@ def run_legs(args, g2, srcs2, tuned_opts):
 
 
 def run_e2e(args, g, srcs, dist: Dist, tuned_opts=None):
-    """Same step through the C ABI with host buffers: the CSR arrays are copied
+    """Same step through the C ABI from host memory: the CSR arrays are copied
     from pinned host memory by gp_graph_upload (GP_UPLOAD_COPY) and every result
     (three rank vectors, 64 level + parent vectors) is read back into its own
-    pinned host buffer, all inside the timed region.  The searches are enqueued
-    without waiting (device outputs in a ring of four buffers); each search's
-    results are copied out on a second stream while the next ones run, and a
-    buffer is reused only after its copy has finished.  The edge count of a
-    search is a property of its source: taken from one untimed step."""
+    pinned host buffer, all inside the timed region.  The searches run first, in
+    one gp_bfs_multi launch; their results (2.15 GB) are copied out on a second
+    stream while the three PageRank runs compute (PageRank polls its status
+    through mapped memory, so it never waits behind those copies), and the rank
+    vectors follow on the same stream.  The edge count of a search is a property
+    of its source: taken from one untimed step."""
     import torch
 
     import paper_2010_16012_gb300 as gp
@@ -627,15 +651,14 @@ def run_e2e(args, g, srcs, dist: Dist, tuned_opts=None):
     n, m = g.n, g.m
     pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
     off_h, idx_h = pin(g.csr_off), pin(g.csr_idx)
-    ranks_h = [torch.empty(n, dtype=torch.float32).pin_memory().numpy() for _ in range(3)]
+    ranks_h = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in range(3)]
+    ranks_d = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
     lv_h = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in srcs]
     pa_h = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in srcs]
-    R = 4
-    lv_d = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(R)]
-    pa_d = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(R)]
+    lv_d = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in srcs]
+    pa_d = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in srcs]
     main = torch.cuda.current_stream()
     copy = torch.cuda.Stream()
-    freed = [torch.cuda.Event() for _ in range(R)]
     h2d = off_h.nbytes + idx_h.nbytes
     d2h = 3 * 4 * n + len(srcs) * 8 * n
     bfs_edges = {}
@@ -645,26 +668,29 @@ def run_e2e(args, g, srcs, dist: Dist, tuned_opts=None):
         if tuned_opts:
             G.set_options(**tuned_opts)
         edges = 0.0
-        for i, mode in enumerate((gp.PULL, gp.PUSH, gp.AUTO)):
-            _, st = gp.pagerank(G, mode, 0.85, args.cap, args.tol, out=ranks_h[i])
-            edges += m * st["iters_done"]
-        for i, s in enumerate(srcs):
-            k = i % R
-            if i >= R:
-                main.wait_event(freed[k])  # the copy out of this buffer has finished
-            if int(s) not in bfs_edges:  # untimed first step: the source's component size
-                _, _, st = gp.bfs(G, int(s), gp.AUTO, level=lv_d[k], parent=pa_d[k])
+        first = not bfs_edges  # untimed first step: the sources' component sizes
+        _, _, summ = gp.bfs_multi(G, srcs, gp.AUTO, levels=lv_d, parents=pa_d, groups=args.bfs_groups,
+                                  want_summary=first)
+        if first:
+            for s, st in zip(srcs, summ):
                 bfs_edges[int(s)] = st["edges_reached"] / 2
-            else:
-                gp.bfs(G, int(s), gp.AUTO, level=lv_d[k], parent=pa_d[k], want_stats=False)
-            done = torch.cuda.Event()
-            done.record(main)
-            copy.wait_event(done)
-            with torch.cuda.stream(copy):
-                lv_h[i].copy_(lv_d[k], non_blocking=True)
-                pa_h[i].copy_(pa_d[k], non_blocking=True)
-                freed[k].record(copy)
-            edges += bfs_edges[int(s)]
+        done = torch.cuda.Event()
+        done.record(main)
+        copy.wait_event(done)
+        with torch.cuda.stream(copy):
+            for i in range(len(srcs)):
+                lv_h[i].copy_(lv_d[i], non_blocking=True)
+                pa_h[i].copy_(pa_d[i], non_blocking=True)
+        edges += sum(bfs_edges[int(s)] for s in srcs)
+        for i, mode in enumerate((gp.PULL, gp.PUSH, gp.AUTO)):
+            _, st = gp.pagerank(G, mode, 0.85, args.cap, args.tol, out=ranks_d[i])
+            edges += m * st["iters_done"]
+        done = torch.cuda.Event()
+        done.record(main)
+        copy.wait_event(done)
+        with torch.cuda.stream(copy):
+            for i in range(3):
+                ranks_h[i].copy_(ranks_d[i], non_blocking=True)
         copy.synchronize()
         G.free()
         return edges
@@ -688,10 +714,11 @@ def run_e2e(args, g, srcs, dist: Dist, tuned_opts=None):
     for i in (0, len(srcs) - 1):
         lv = lv_h[i].numpy()
         assert lv[int(srcs[i])] == 0 and (lv >= -1).all()
+    assert all(bool((r >= 0).all()) and float(r.max()) > 0 for r in ranks_h)
     return {"value": round(v / 1e9, 4), "unit": "GTEPS", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "steps": steps, "ms_per_step": round(ms, 3),
             "median_step_ms": round(statistics.median(step_ms), 3), "max_step_ms": round(max(step_ms), 3),
-            "overlap": "searches enqueued without waiting; results copied out on a second stream"}
+            "overlap": "searches in one launch first; their results copied out on a second stream during PageRank"}
 
 
 # ------------------------------------------------------------------ CPU oracle (baseline and reference arm)
@@ -939,7 +966,13 @@ def run_only(args):
             torch.cuda.synchronize()
             gp.profile_read(reset=True)
             gp.profile_enable(True)
-        if args.only == "bfs":
+        if args.only == "bfs" and args.bfs_groups > 0:
+            # all sources in one gp_bfs_multi launch with --bfs-groups groups
+            bmode = {"push": gp.PUSH, "pull": gp.PULL, "auto": gp.AUTO}[args.mode]
+            _, _, summ = gp.bfs_multi(G, srcs, bmode, groups=args.bfs_groups)
+            res = {"searches": len(summ), "levels": [x["levels"] for x in summ],
+                   "reached": [x["reached"] for x in summ]}
+        elif args.only == "bfs":
             bmode = {"push": gp.PUSH, "pull": gp.PULL, "auto": gp.AUTO}[args.mode]
             for s in srcs:
                 _, _, st = gp.bfs(G, int(s), bmode)

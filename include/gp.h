@@ -351,6 +351,43 @@ typedef struct gp_bfs_stats {
 int gp_bfs(const gp_graph *g, int32_t src, int mode, int32_t *level_out, int32_t *parent_out, gp_bfs_stats *stats,
            void *stream);
 
+/* Per-search figures of gp_bfs_multi (the totals of gp_bfs_stats). */
+typedef struct gp_bfs_summary {
+    int32_t levels;         /* levels explored (depth + 1) */
+    int32_t switches;       /* direction changes */
+    int64_t reached;        /* vertices with level >= 0 */
+    int64_t edges_examined; /* out-edges scanned top-down + in-edges scanned bottom-up */
+    int64_t edges_reached;  /* sum of out-degrees of the reached vertices */
+} gp_bfs_summary;
+
+/*
+ * Several independent searches (the same per-source search as gp_bfs: Section
+ * 3.3, Algorithm 3, with gp_bfs's modes and direction rule) in one cooperative
+ * launch.  The GPU's resident blocks are cut into `groups` equal groups, each
+ * with its own frontier workspace and grid barrier; a group that finishes a
+ * search takes the next one not yet started (the order in which searches run
+ * is not fixed, their results are).  A search's levels cost a
+ * fixed barrier and counter round trip each whatever the frontier's size, so
+ * groups that never wait on one another overlap those costs.
+ *   sources     host int32[nsources], each in [0, n) (repeats allowed).
+ *   level_out   host array of nsources DEVICE pointers, each int32[n]: the
+ *               levels of search i (as gp_bfs's level_out).
+ *   parent_out  NULL, or a host array of nsources device pointers (int32[n]
+ *               each): a BFS parent per vertex (as gp_bfs's parent_out).
+ *   groups      0: the library's choice (8); otherwise clamped to
+ *               [1, min(nsources, resident blocks, 32)].
+ *   summary     NULL, or host gp_bfs_summary[nsources] filled on return (the
+ *               call then waits for the searches).
+ * Returns GP_ERR_INVALID (nothing launched) for a source outside [0, n) or an
+ * output pointer that is not device memory.  With summary == NULL the call only
+ * enqueues the launch on `stream`; a grid-barrier timeout (GP_ERR_TIMEOUT,
+ * outputs incomplete) is then returned by the next gp_bfs_multi on this graph.
+ * Workspace: per group two n-entry queues and four n-bit bitmaps, kept with
+ * the graph; calls on one graph share it, so issue them on one stream.
+ */
+int gp_bfs_multi(const gp_graph *g, const int32_t *sources, int nsources, int mode, int32_t *const *level_out,
+                 int32_t *const *parent_out, int groups, gp_bfs_summary *summary, void *stream);
+
 /* gp_bfs with the direction of every level chosen by the caller:
  * dirs[i] (GP_PUSH or GP_PULL) is used for level i, dirs[ndirs-1] for all
  * later levels; ndirs may exceed GP_BFS_MAX_LEVELS.  Levels do not depend on

@@ -71,6 +71,11 @@ class gp_bfs_stats(ctypes.Structure):
                 ("level_ns", ctypes.c_int32 * BFS_MAX_LEVELS)]
 
 
+class gp_bfs_summary(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("switches", ctypes.c_int32), ("reached", ctypes.c_int64),
+                ("edges_examined", ctypes.c_int64), ("edges_reached", ctypes.c_int64)]
+
+
 SSSP_MAX_ITERS = 1024
 
 
@@ -159,6 +164,8 @@ SIGNATURES = [
                                             ctypes.POINTER(gp_pr_stats), _VP]),
     ("gp_graph_set_weights", ctypes.c_int, [_VP, _VP, _VP, _VP]),
     ("gp_bfs", ctypes.c_int, [_VP, _I32, ctypes.c_int, _VP, _VP, ctypes.POINTER(gp_bfs_stats), _VP]),
+    ("gp_bfs_multi", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_int,
+                                    ctypes.POINTER(gp_bfs_summary), _VP]),
     ("gp_bfs_directed", ctypes.c_int, [_VP, _I32, _VP, ctypes.c_int, _VP, _VP, ctypes.POINTER(gp_bfs_stats),
                                        _VP]),
     ("gp_sssp", ctypes.c_int, [_VP, _I32, _F, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP,
@@ -456,6 +463,35 @@ def bfs(g: Graph, src: int, mode=AUTO, level=None, parent=None, want_parent=True
              "examined": list(st.examined[:L]), "init_us": st.init_ns / 1e3,
              "level_us": [x / 1e3 for x in st.level_ns[:L]]}
     return level, parent, stats
+
+
+def bfs_multi(g: Graph, sources, mode=AUTO, levels=None, parents=None, want_parent=True, groups=0, stream=None,
+              want_summary=True):
+    """gp_bfs_multi: independent searches from every source in one launch.
+    levels / parents: lists of CUDA int32 tensors of n entries (allocated when
+    None).  Returns (levels, parents or None, list of summary dicts or None).
+    With want_summary=False the call returns without waiting (a barrier
+    timeout is then reported by the next gp_bfs_multi on the graph)."""
+    torch = _torch()
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32).reshape(-1))
+    k = int(src.shape[0])
+    if levels is None:
+        levels = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in range(k)]
+    if parents is None and want_parent:
+        parents = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in range(k)]
+    if len(levels) != k or (parents is not None and len(parents) != k):
+        raise ValueError("bfs_multi: one level (and parent) tensor per source")
+    lp = (ctypes.c_void_p * max(k, 1))(*[t.data_ptr() for t in levels])
+    pp = None if parents is None else (ctypes.c_void_p * max(k, 1))(*[t.data_ptr() for t in parents])
+    sm = (gp_bfs_summary * max(k, 1))() if want_summary else None
+    _check(load().gp_bfs_multi(g.handle, _ptr(src), k, int(mode), ctypes.cast(lp, _VP),
+                               None if pp is None else ctypes.cast(pp, _VP), int(groups), sm, _stream_ptr(stream)),
+           "gp_bfs_multi")
+    if not want_summary:
+        return levels, parents, None
+    out = [{"levels": x.levels, "switches": x.switches, "reached": x.reached, "edges_examined": x.edges_examined,
+            "edges_reached": x.edges_reached} for x in sm[:k]]
+    return levels, parents, out
 
 
 def sssp(g: Graph, src: int, delta: float, mode=AUTO, dist=None, pred=None, want_pred=True, dirs=None,

@@ -67,7 +67,15 @@ struct BfsArgs {
     int32_t L;           // level being expanded: new vertices get L + 1
     int32_t make_queue;  // top-down: also build the next frontier's queue
     int64_t q_len, h_len;  // top-down: lengths of the current frontier's queue and heavy list
+    int32_t gblk, ngblk;   // this block's index among the blocks running the search, and their number
 };
+
+// Warp index and warp count within the blocks that run one search (the whole
+// grid for gp_bfs, one group of blocks for gp_bfs_multi).
+__device__ __forceinline__ int64_t search_warp(const BfsArgs &a) {
+    return ((int64_t)a.gblk * blockDim.x + threadIdx.x) >> 5;
+}
+__device__ __forceinline__ int64_t search_nwarps(const BfsArgs &a) { return ((int64_t)a.ngblk * blockDim.x) >> 5; }
 
 // Count w (newly visited) into the next frontier's statistics and, when the
 // level builds a queue, append it: light vertices to the queue (warp-
@@ -151,8 +159,8 @@ constexpr unsigned long long TD_QUEUE_EDGES = 1ull << 14;
 // ones 32 queue entries per warp with a merged edge stream.
 __device__ void bfs_topdown_step(const BfsArgs &a) {
     const int lane = lane_id();
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t warp = search_warp(a);
+    const int64_t nwarps = search_nwarps(a);
     const int64_t h_len = a.h_len, q_len = a.q_len;
     unsigned long long nf = 0, mf = 0, mu = 0, ex = 0;
     // each heavy chunk is split TD_SPLIT ways so a frontier of a few hubs still spreads over many warps
@@ -240,8 +248,8 @@ constexpr int64_t BU_PROBE = GP_BU_PROBE;
 __device__ void bfs_bottomup_step(const BfsArgs &a) {
     __shared__ uint32_t s_found[BFS_WARPS][32];
     const int lane = lane_id(), wib = threadIdx.x >> 5;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t warp = search_warp(a);
+    const int64_t nwarps = search_nwarps(a);
     const int64_t nwords = (a.n + 31) >> 5;
     unsigned long long nf = 0, mf = 0, mu = 0, ex = 0, deferred = 0;
     for (int64_t base = warp * 32; base < nwords; base += nwarps * 32) {
@@ -346,8 +354,8 @@ constexpr int BU_WARP_UNROLL = 8;
 
 __device__ void bfs_bottomup_hubs(const BfsArgs &a) {
     const int lane = lane_id();
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t warp = search_warp(a);
+    const int64_t nwarps = search_nwarps(a);
     volatile int32_t *vlevel = a.level;
     unsigned long long nf = 0, mf = 0, mu = 0, ex = 0;
     for (int64_t base = warp * 32; base < a.pull_nchunks; base += nwarps * 32) {
@@ -417,8 +425,8 @@ __device__ void bfs_bottomup_hubs(const BfsArgs &a) {
 // a warp ranks the set bits of 32 words and appends them 32 at a time.
 __device__ void bits_to_queue_step(const BfsArgs &a) {
     const int lane = lane_id();
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t warp = search_warp(a);
+    const int64_t nwarps = search_nwarps(a);
     const int64_t nwords = (a.n + 31) >> 5;
     unsigned long long nf = 0, mf = 0, mu = 0;  // already counted by the level that made the bitmap
     for (int64_t base = warp * 32; base < nwords; base += nwarps * 32) {
@@ -486,23 +494,32 @@ struct BfsRun {
 // counter), which is what a level's fixed cost is made of.
 constexpr int BFS_THREADS = BFS_WARPS * 32;
 
-// Every block keeps identical copies of the frontier statistics (read from the
-// counters after each barrier), so all blocks take the same direction decision
-// without a host round trip.
-__global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(BfsRun R) {
+// The outputs and source of one search.
+struct SearchIO {
+    int32_t src;
+    int32_t *level, *parent;  // parent may be nullptr
+    BfsSummary *summary;
+};
+
+// One whole search, run by `ngblk` blocks (gblk = this block's index among
+// them) that share R's workspace and barrier.  Every block keeps identical
+// copies of the frontier statistics (read from the counters after each
+// barrier), so all blocks take the same direction decision without a host
+// round trip.  Returns false when a barrier wait ran out.
+__device__ bool bfs_search(const BfsRun &R, const SearchIO &io, int gblk, int ngblk) {
     const unsigned long long t_start = global_ns();
     const int64_t n = R.base.n;
-    const int64_t gthread = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gthread = (int64_t)gblk * blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)ngblk * blockDim.x;
     const int64_t nwords = (n + 31) >> 5;
     // level/parent, counters, bitmaps and candidates set for frontier 0 = {src}
-    const int32_t src = R.src;
+    const int32_t src = io.src;
     const int32_t s_rank = R.base.push_rank[src];
     const int64_t s_c0 = s_rank >= 0 ? R.base.push_cstart[s_rank] : 0;
     const int64_t s_c1 = s_rank >= 0 ? R.base.push_cstart[s_rank + 1] : 0;
     for (int64_t v = gthread; v < n; v += nthreads) {
-        R.base.level[v] = v == src ? 0 : -1;
-        if (R.base.parent) R.base.parent[v] = v == src ? src : -1;
+        io.level[v] = v == src ? 0 : -1;
+        if (io.parent) io.parent[v] = v == src ? src : -1;
     }
     constexpr int CW = (int)(sizeof(BfsCtr) / sizeof(unsigned long long));
     if (gthread < 3 * CW) {
@@ -523,10 +540,14 @@ __global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(Bfs
         R.bits[1][i] = 0u;
         R.base.unvis[i] = R.nzin[i] & (i == sw ? ~sbit : ~0u);
     }
-    if (!grid_sync(R.sync, gridDim.x)) return;
+    if (!grid_sync(R.sync, ngblk)) return false;
     unsigned long long t_level = global_ns();
     const unsigned long long t_init = t_level - t_start;
     BfsArgs a = R.base;
+    a.level = io.level;
+    a.parent = io.parent;
+    a.gblk = gblk;
+    a.ngblk = ngblk;
     // counter records are read by one thread per block and shared through
     // shared memory: every thread loading the same line would queue tens of
     // thousands of requests on one L2 slice per level
@@ -585,7 +606,7 @@ __global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(Bfs
             c.queue_next = R.queue[L & 1];
             c.h_next = R.hchunk[L & 1];
             bits_to_queue_step(c);
-            if (!grid_sync(R.sync, gridDim.x)) return;
+            if (!grid_sync(R.sync, ngblk)) return false;
             read_ctr(cur);
             q_len = (int64_t)s_ctr[0];
             h_len = (int64_t)s_ctr[1];
@@ -605,17 +626,17 @@ __global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(Bfs
             bfs_bottomup_step(a);
             in_queue = false;
         }
-        if (!grid_sync(R.sync, gridDim.x)) return;
+        if (!grid_sync(R.sync, ngblk)) return false;
         read_ctr(nxt);
         if (dir == GP_PULL && s_ctr[6] > 0) {  // hubs deferred by the lanes: the chunk pass
             bfs_bottomup_hubs(a);
-            if (!grid_sync(R.sync, gridDim.x)) return;
+            if (!grid_sync(R.sync, ngblk)) return false;
             read_ctr(nxt);
         }
         const unsigned long long nf2 = s_ctr[2], mf2 = s_ctr[3], mud = s_ctr[4], ex = s_ctr[5];
         q_len = (int64_t)s_ctr[0];
         h_len = (int64_t)s_ctr[1];
-        if (gthread == 0 && L < GP_BFS_MAX_LEVELS) {
+        if (gthread == 0 && R.stats && L < GP_BFS_MAX_LEVELS) {
             const unsigned long long t = global_ns();
             R.stats[L].ns = (int32_t)min(t - t_level, 0x7fffffffull);
             t_level = t;
@@ -635,12 +656,60 @@ __global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(Bfs
         ++L;
     }
     if (gthread == 0) {
-        R.summary->levels = L;
-        R.summary->reached = reached;
-        R.summary->examined = examined;
-        R.summary->edges_reached = edges_reached;
-        R.summary->switches = switches;
-        R.summary->init_ns = (int64_t)t_init;
+        io.summary->levels = L;
+        io.summary->reached = reached;
+        io.summary->examined = examined;
+        io.summary->edges_reached = edges_reached;
+        io.summary->switches = switches;
+        io.summary->init_ns = (int64_t)t_init;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_persistent(BfsRun R) {
+    const SearchIO io = {R.src, R.base.level, R.base.parent, R.summary};
+    bfs_search(R, io, blockIdx.x, gridDim.x);
+}
+
+// Several searches in one launch: the grid is cut into `groups` groups of
+// `bpg` consecutive blocks, each with its own workspace and barrier (runs[g]).
+// A group takes the next search from a shared counter whenever it finishes
+// one, so groups that drew short searches take more of them.  The groups
+// never wait on one another, so each search's fixed per-level cost (barrier
+// and counter round trip) overlaps the other groups' work.
+constexpr int BFS_MULTI_MAX_GROUPS = 32;
+// Passed by value: the runs sit in the kernel's parameter space, which every
+// thread reads at the cost of a constant load.
+struct BfsMulti {
+    BfsRun runs[BFS_MULTI_MAX_GROUPS];  // the groups' workspaces and barriers (kernel parameters)
+    const int32_t *src;      // [nsrc]
+    int32_t *const *level;   // [nsrc] device pointers
+    int32_t *const *parent;  // [nsrc] device pointers, or nullptr
+    BfsSummary *summary;     // [nsrc]
+    int32_t *next;           // the next search to hand out (zero at launch)
+    int32_t *slot;           // [2 * groups]: the search a group's leader drew, by draw parity
+    int32_t nsrc, groups, bpg;
+};
+
+static_assert(sizeof(BfsMulti) <= 32764, "kernel parameters are limited to 32764 bytes");
+
+__global__ void __launch_bounds__(BFS_THREADS, GP_BFS_MINB) k_bfs_multi(BfsMulti M) {
+    const int grp = blockIdx.x / M.bpg;
+    const int gblk = blockIdx.x - grp * M.bpg;
+    if (grp >= M.groups) return;
+    const BfsRun &R = M.runs[grp];
+    for (int draw = 0;; ++draw) {
+        // the leader draws a search and the group's barrier publishes it; the
+        // same barrier also ends the previous search in every block before the
+        // workspace is reset.  Draws alternate between two slots, so a slot is
+        // rewritten only after every block has read it (two barriers later).
+        int32_t *sl = M.slot + 2 * grp + (draw & 1);
+        if (gblk == 0 && threadIdx.x == 0) *sl = atomicAdd(M.next, 1);
+        if (!grid_sync(R.sync, M.bpg)) return;
+        const int i = *(volatile int32_t *)sl;
+        if (i >= M.nsrc) return;
+        const SearchIO io = {M.src[i], M.level[i], M.parent ? M.parent[i] : nullptr, M.summary + i};
+        if (!bfs_search(R, io, gblk, M.bpg)) return;
     }
 }
 
@@ -671,9 +740,15 @@ void release_bfs_work(gp_graph *g, cudaStream_t s) {
         cudaEventSynchronize(g->bfs.done_ev);
         cudaEventDestroy(g->bfs.done_ev);
     }
+    if (g->bfs.mdone_ev) {
+        cudaEventSynchronize(g->bfs.mdone_ev);
+        cudaEventDestroy(g->bfs.mdone_ev);
+    }
     pinned_free(g->bfs.ctr_host, BFS_HOST_BYTES);
+    pinned_free(g->bfs.mhost, g->bfs.mhost_bytes);
     g->bfs.ctr_host = nullptr;
     g->bfs.mem.release(s);
+    g->bfs.mmem.release(s);
     g->bfs = BfsWork();
 }
 
@@ -720,6 +795,28 @@ static int ensure_bfs_work(gp_graph *g, cudaStream_t s) {
     return GP_OK;
 }
 
+// The fields of a search that depend only on the graph, its options and the mode.
+static void run_common(const gp_graph *g, int mode, BfsRun &R) {
+    memset(&R, 0, sizeof(R));
+    R.base.n = g->n;
+    R.base.csr_off = g->csr_off;
+    R.base.csc_off = g->csc_off;
+    R.base.csr_idx = g->csr_idx;
+    R.base.csc_idx = g->csc_idx;
+    R.base.push_rank = g->push_bins.rank;
+    R.base.push_cstart = g->push_bins.cstart;
+    R.base.push_chunks = g->push_bins.chunks;
+    R.base.pull_chunks = g->pull_bins.chunks;
+    R.base.pull_nchunks = g->pull_bins.nchunks;
+    // every hub a lane defers has in-edge chunks: the probe is at least the pull light limit
+    R.base.bu_probe = std::max<int64_t>(BU_PROBE, g->pull_bins.light_max);
+    R.nzin = g->bfs.nzin;
+    R.mode = mode;
+    R.alpha = g->opt.bfs_alpha;
+    R.beta = g->opt.bfs_beta;
+    R.m = g->m;
+}
+
 static int bfs_run(const gp_graph *gc, int32_t src, int mode, const int8_t *dirs, int ndirs, int32_t *level_out,
                    int32_t *parent_out, gp_bfs_stats *stats, cudaStream_t s) {
     gp_graph *g = const_cast<gp_graph *>(gc);
@@ -759,19 +856,7 @@ static int bfs_run(const gp_graph *gc, int32_t src, int mode, const int8_t *dirs
         parent = w.parent_dev;
     }
     BfsRun R;
-    memset(&R, 0, sizeof(R));
-    R.base.n = n;
-    R.base.csr_off = g->csr_off;
-    R.base.csc_off = g->csc_off;
-    R.base.csr_idx = g->csr_idx;
-    R.base.csc_idx = g->csc_idx;
-    R.base.push_rank = g->push_bins.rank;
-    R.base.push_cstart = g->push_bins.cstart;
-    R.base.push_chunks = g->push_bins.chunks;
-    R.base.pull_chunks = g->pull_bins.chunks;
-    R.base.pull_nchunks = g->pull_bins.nchunks;
-    // every hub a lane defers has in-edge chunks: the probe is at least the pull light limit
-    R.base.bu_probe = std::max<int64_t>(BU_PROBE, g->pull_bins.light_max);
+    run_common(g, mode, R);
     R.base.level = level;
     R.base.parent = parent;
     for (int i = 0; i < 2; ++i) {
@@ -779,13 +864,8 @@ static int bfs_run(const gp_graph *gc, int32_t src, int mode, const int8_t *dirs
         R.hchunk[i] = w.hchunk[i];
     }
     for (int i = 0; i < 3; ++i) R.bits[i] = w.bits[i];
-    R.nzin = w.nzin;
     R.base.unvis = w.unvis;
     R.ctr = (BfsCtr *)w.ctr;
-    R.mode = mode;
-    R.alpha = g->opt.bfs_alpha;
-    R.beta = g->opt.bfs_beta;
-    R.m = g->m;
     R.src = src;
     R.stats = (BfsLevelStat *)w.stats;
     R.summary = (BfsSummary *)w.summary;
@@ -848,6 +928,171 @@ static int bfs_run(const gp_graph *gc, int32_t src, int mode, const int8_t *dirs
     return GP_OK;
 }
 
+// ------------------------------------------------------------------ several searches per launch
+
+// Byte layout of the staged tables: src[cap], level[cap], parent[cap].
+struct MultiLayout {
+    size_t src, level, parent, tab_bytes, summary, sync, host_bytes;
+    MultiLayout(int groups, int cap) {
+        auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+        src = 0;
+        level = up(src + cap * sizeof(int32_t));
+        parent = up(level + cap * sizeof(int32_t *));
+        tab_bytes = up(parent + cap * sizeof(int32_t *));
+        summary = tab_bytes;  // in the pinned block, the summaries and barrier words follow the tables
+        sync = up(summary + cap * sizeof(BfsSummary));
+        host_bytes = sync + groups * sizeof(GridSync);
+    }
+};
+
+static int ensure_bfs_multi(gp_graph *g, int groups, int nsrc, cudaStream_t s) {
+    BfsWork &w = g->bfs;
+    if ((int)w.mgrp.size() >= groups && w.msrc_cap >= nsrc) return GP_OK;
+    groups = std::max<int>(groups, (int)w.mgrp.size());
+    nsrc = std::max(nsrc, w.msrc_cap);
+    w.mmem.release(s);
+    pinned_free(w.mhost, w.mhost_bytes);
+    w.mhost = nullptr;
+    w.mhost_bytes = 0;
+    w.mgrp.clear();
+    w.msrc_cap = 0;
+    const size_t n = (size_t)std::max<int64_t>(g->n, 1);
+    const size_t words = (n + 31) / 32;
+    const size_t hcap = (size_t)std::max<int64_t>(g->push_bins.nchunks, 1);
+    std::vector<BfsWork::Group> grp((size_t)groups);
+    for (auto &q : grp) {
+        for (int i = 0; i < 2; ++i) {
+            GP_TRY(w.mmem.alloc(q.queue[i], n, s));
+            GP_TRY(w.mmem.alloc(q.hchunk[i], hcap, s));
+        }
+        for (int i = 0; i < 3; ++i) GP_TRY(w.mmem.alloc(q.bits[i], words, s));
+        GP_TRY(w.mmem.alloc(q.unvis, words, s));
+        BfsCtr *c = nullptr;
+        GP_TRY(w.mmem.alloc(c, 3, s));
+        q.ctr = c;
+    }
+    const MultiLayout lay(groups, nsrc);
+    char *tab = nullptr;
+    GP_TRY(w.mmem.alloc(tab, lay.tab_bytes, s));
+    w.mtab = tab;
+    BfsSummary *sum = nullptr;
+    GP_TRY(w.mmem.alloc(sum, (size_t)nsrc, s));
+    w.msummary = sum;
+    GridSync *sync = nullptr;
+    GP_TRY(w.mmem.alloc(sync, (size_t)groups, s));
+    w.msync = sync;
+    int32_t *draw = nullptr;
+    GP_TRY(w.mmem.alloc(draw, 1 + 2 * (size_t)groups, s));
+    w.mdraw = draw;
+    GP_TRY(pinned_alloc(&w.mhost, lay.host_bytes));
+    w.mhost_bytes = lay.host_bytes;
+    if (!w.mdone_ev) GP_CUDA(cudaEventCreateWithFlags(&w.mdone_ev, cudaEventDisableTiming));
+    w.mgrp = std::move(grp);
+    w.msrc_cap = nsrc;
+    return GP_OK;
+}
+
+// Groups when the caller leaves the choice to the library.
+constexpr int BFS_MULTI_GROUPS = 8;
+
+static int bfs_multi(const gp_graph *gc, const int32_t *sources, int nsrc, int mode, int32_t *const *level_out,
+                     int32_t *const *parent_out, int groups, gp_bfs_summary *summary, cudaStream_t s) {
+    gp_graph *g = const_cast<gp_graph *>(gc);
+    const int64_t n = g->n;
+    for (int i = 0; i < nsrc; ++i) {
+        if (sources[i] < 0 || (int64_t)sources[i] >= n)
+            return set_error(GP_ERR_INVALID, "gp_bfs_multi: sources[%d] = %d outside [0, %lld)", i, sources[i], (long long)n);
+        if (!level_out[i] || !is_device_ptr(level_out[i]))
+            return set_error(GP_ERR_INVALID, "gp_bfs_multi: level_out[%d] is not device memory", i);
+        if (parent_out && (!parent_out[i] || !is_device_ptr(parent_out[i])))
+            return set_error(GP_ERR_INVALID, "gp_bfs_multi: parent_out[%d] is not device memory", i);
+    }
+    if (summary) memset(summary, 0, (size_t)nsrc * sizeof(gp_bfs_summary));
+    if (nsrc == 0) return GP_OK;
+    GP_TRY(ensure_bfs_work(g, s));
+    BfsWork &w = g->bfs;
+    if (w.mpending) {  // the previous asynchronous call: its barrier status, and its staged tables are free again
+        GP_CUDA(cudaEventSynchronize(w.mdone_ev));
+        w.mpending = false;
+        const MultiLayout old((int)w.mgrp.size(), w.msrc_cap);
+        const GridSync *hs = (const GridSync *)((char *)w.mhost + old.sync);
+        int err = 0;
+        for (size_t i = 0; i < w.mgrp.size(); ++i) err |= hs[i].err;
+        if (err) return set_error(GP_ERR_TIMEOUT, "BFS: a grid barrier wait ran out in the previous asynchronous gp_bfs_multi");
+    }
+    int per_sm = 0;
+    GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs_multi, BFS_THREADS, 0));
+    if (per_sm < 1) return set_error(GP_ERR_UNSUPPORTED, "BFS kernel does not fit on an SM");
+    const int blocks = per_sm * g->num_sms;
+    int G = groups > 0 ? groups : BFS_MULTI_GROUPS;
+    G = std::max(1, std::min(std::min(std::min(G, nsrc), blocks), BFS_MULTI_MAX_GROUPS));
+    const int bpg = blocks / G;
+    GP_TRY(ensure_bfs_multi(g, G, nsrc, s));
+    const int gcap = (int)w.mgrp.size();
+    const MultiLayout lay(gcap, w.msrc_cap);
+    char *h = (char *)w.mhost;
+    char *d = (char *)w.mtab;
+    BfsMulti M;
+    memset(&M, 0, sizeof(M));
+    for (int q = 0; q < G; ++q) {
+        BfsRun &R = M.runs[q];
+        run_common(g, mode, R);
+        const BfsWork::Group &b = w.mgrp[(size_t)q];
+        for (int i = 0; i < 2; ++i) {
+            R.queue[i] = b.queue[i];
+            R.hchunk[i] = b.hchunk[i];
+        }
+        for (int i = 0; i < 3; ++i) R.bits[i] = b.bits[i];
+        R.base.unvis = b.unvis;
+        R.ctr = (BfsCtr *)b.ctr;
+        R.sync = (GridSync *)w.msync + q;
+        R.stats = nullptr;  // per-level statistics are gp_bfs's
+    }
+    memcpy(h + lay.src, sources, (size_t)nsrc * sizeof(int32_t));
+    memcpy(h + lay.level, level_out, (size_t)nsrc * sizeof(int32_t *));
+    if (parent_out) memcpy(h + lay.parent, parent_out, (size_t)nsrc * sizeof(int32_t *));
+    GP_CUDA(cudaMemcpyAsync(d, h, lay.tab_bytes, cudaMemcpyHostToDevice, s));
+    GP_CUDA(cudaMemsetAsync(w.msync, 0, (size_t)G * sizeof(GridSync), s));
+    GP_CUDA(cudaMemsetAsync(w.mdraw, 0, sizeof(int32_t), s));
+    M.src = (const int32_t *)(d + lay.src);
+    M.level = (int32_t *const *)(d + lay.level);
+    M.parent = parent_out ? (int32_t *const *)(d + lay.parent) : nullptr;
+    M.summary = (BfsSummary *)w.msummary;
+    M.next = w.mdraw;
+    M.slot = w.mdraw + 1;
+    M.nsrc = nsrc;
+    M.groups = G;
+    M.bpg = bpg;
+    {
+        ProfScope ps("bfs_multi", s);
+        void *args[] = {&M};
+        GP_CUDA(cudaLaunchCooperativeKernel((const void *)k_bfs_multi, dim3((unsigned)(G * bpg)), dim3(BFS_THREADS), args, 0,
+                                            s));
+    }
+    GridSync *hsync = (GridSync *)(h + lay.sync);
+    GP_CUDA(cudaMemcpyAsync(hsync, w.msync, (size_t)G * sizeof(GridSync), cudaMemcpyDeviceToHost, s));
+    for (int q = G; q < gcap; ++q) hsync[q].err = 0;  // groups this call left unused
+    if (!summary) {
+        GP_CUDA(cudaEventRecord(w.mdone_ev, s));
+        w.mpending = true;
+        return GP_OK;
+    }
+    BfsSummary *hs = (BfsSummary *)(h + lay.summary);
+    GP_CUDA(cudaMemcpyAsync(hs, w.msummary, (size_t)nsrc * sizeof(BfsSummary), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    int err = 0;
+    for (int q = 0; q < G; ++q) err |= hsync[q].err;
+    if (err) return set_error(GP_ERR_TIMEOUT, "BFS: a grid barrier wait ran out in gp_bfs_multi");
+    for (int i = 0; i < nsrc; ++i) {
+        summary[i].levels = (int32_t)hs[i].levels;
+        summary[i].switches = (int32_t)hs[i].switches;
+        summary[i].reached = hs[i].reached;
+        summary[i].edges_examined = hs[i].examined;
+        summary[i].edges_reached = hs[i].edges_reached;
+    }
+    return GP_OK;
+}
+
 }  // namespace gp
 
 using namespace gp;
@@ -858,6 +1103,17 @@ extern "C" int gp_bfs(const gp_graph *g, int32_t src, int mode, int32_t *level_o
     if (!g) return set_error(GP_ERR_INVALID, "gp_bfs: graph is NULL");
     if (mode != GP_PUSH && mode != GP_PULL && mode != GP_AUTO) return set_error(GP_ERR_INVALID, "bad mode %d", mode);
     return bfs_run(g, src, mode, nullptr, 0, level_out, parent_out, stats, (cudaStream_t)stream);
+}
+
+extern "C" int gp_bfs_multi(const gp_graph *g, const int32_t *sources, int nsources, int mode, int32_t *const *level_out,
+                            int32_t *const *parent_out, int groups, gp_bfs_summary *summary, void *stream) {
+    clear_error();
+    if (!g) return set_error(GP_ERR_INVALID, "gp_bfs_multi: graph is NULL");
+    if (mode != GP_PUSH && mode != GP_PULL && mode != GP_AUTO) return set_error(GP_ERR_INVALID, "bad mode %d", mode);
+    if (nsources < 0) return set_error(GP_ERR_INVALID, "gp_bfs_multi: nsources %d < 0", nsources);
+    if (groups < 0) return set_error(GP_ERR_INVALID, "gp_bfs_multi: groups %d < 0", groups);
+    if (nsources > 0 && (!sources || !level_out)) return set_error(GP_ERR_INVALID, "gp_bfs_multi: sources or level_out is NULL");
+    return bfs_multi(g, sources, nsources, mode, level_out, parent_out, groups, summary, (cudaStream_t)stream);
 }
 
 extern "C" int gp_bfs_directed(const gp_graph *g, int32_t src, const int8_t *dirs, int ndirs, int32_t *level_out,

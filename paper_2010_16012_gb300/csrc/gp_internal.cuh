@@ -51,6 +51,13 @@ void dev_free(DevBuf &b, cudaStream_t s);
 // Page-locked host blocks (status mirrors), reused across graphs.
 int pinned_alloc(void **p, size_t bytes);
 void pinned_free(void *p, size_t bytes);
+// The address under which kernels on the current device write a pinned block.
+int pinned_device_ptr(void *host, void **dev);
+// Device-to-host read of a result the host waits for (sizes, counts, flags):
+// a kernel on `s` writes it into a mapped page-locked block, then `s` is
+// synchronised.  No copy-engine transfer is involved, so the read never waits
+// behind large copies the caller has in flight on other streams.
+cudaError_t read_mapped(void *dst, const void *src, size_t bytes, cudaStream_t s);
 
 // Owned allocations of a handle (freed together).
 struct Arena {
@@ -144,7 +151,8 @@ struct PrWork {
     float *lam = nullptr;          // adjoint solution
     float *gw_dev = nullptr;       // weight gradient when the output is host memory
     void *status = nullptr;        // device PrStatus
-    void *status_host = nullptr;   // pinned mirror
+    void *status_host = nullptr;   // pinned mirror (written by the kernels)
+    void *status_mirror = nullptr; // its device-side address
     int max_blocks = 0;
     Arena mem;
 };
@@ -169,6 +177,24 @@ struct BfsWork {
     cudaEvent_t done_ev = nullptr;           // end of the last asynchronous search
     bool pending = false;                    // its barrier status not yet checked
     Arena mem;
+    // gp_bfs_multi: one frontier workspace per group of blocks, and the tables
+    // of one call (group runs, sources, output pointers) staged through pinned memory
+    struct Group {
+        int32_t *queue[2], *hchunk[2];
+        uint32_t *bits[3], *unvis;
+        void *ctr;
+    };
+    std::vector<Group> mgrp;
+    int msrc_cap = 0;                        // searches the tables hold
+    void *mtab = nullptr;                    // device copy of the staged tables
+    void *msummary = nullptr;                // per-search summaries (device)
+    void *msync = nullptr;                   // a barrier word per group (device)
+    int32_t *mdraw = nullptr;                // the next search to hand out, then two slots per group (device)
+    void *mhost = nullptr;                   // pinned: staged tables, then summaries and barrier words
+    size_t mhost_bytes = 0;
+    cudaEvent_t mdone_ev = nullptr;          // end of the last asynchronous gp_bfs_multi
+    bool mpending = false;                   // its barrier status not yet checked
+    Arena mmem;
 };
 
 }  // namespace gp

@@ -141,8 +141,23 @@ __global__ void k_pr_init(int64_t n, const float *x0, const float *cmul, float *
     }
 }
 
-// Records the decision for the last sweep enqueued (sweep k-1) without doing a sweep.
-__global__ void k_pr_finish(PrArgs a) { pr_gate(a, a.k); }
+// Records the decision for the last sweep enqueued (sweep k-1) without doing a
+// sweep, and writes the status into the host's mapped mirror slot: the host
+// polls it with no copy, so polling never waits behind other transfers.
+__global__ void k_pr_finish(PrArgs a, PrStatus *mirror) {
+    pr_gate(a, a.k);
+    if (threadIdx.x == 0) {
+        *mirror = *a.status;  // the gate ended with a block barrier
+        __threadfence_system();
+    }
+}
+
+// dst = src over n floats (the result's move into the caller's buffer, kept
+// off the copy engines for the same reason).
+__global__ void k_copy_f32(int64_t n, const float *__restrict__ src, float *__restrict__ dst) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
+}
 
 // ------------------------------------------------------------------ pull
 
@@ -627,6 +642,7 @@ static int ensure_pr_work(gp_graph *g, cudaStream_t s) {
     GP_TRY(w.mem.alloc(st, 1, s));
     w.status = st;
     GP_TRY(pinned_alloc(&w.status_host, 4 * sizeof(PrStatus)));
+    GP_TRY(pinned_device_ptr(w.status_host, &w.status_mirror));
     w.ready = true;
     return GP_OK;
 }
@@ -828,10 +844,8 @@ static int pr_iterate(gp_graph *g, const IterSpec &sp, float *out, PrStatus &fin
     auto enqueue_finish = [&](int k_next, int slot) -> int {
         PrArgs b = a;
         b.k = k_next;
-        GP_LAUNCH("pr_finish", s, (k_pr_finish<<<1, 256, 0, s>>>(b)));
-        GP_TRY(check_launch("pr_finish"));
-        GP_CUDA(cudaMemcpyAsync((PrStatus *)w.status_host + slot, status, sizeof(PrStatus), cudaMemcpyDeviceToHost, s));
-        return GP_OK;
+        GP_LAUNCH("pr_finish", s, (k_pr_finish<<<1, 256, 0, s>>>(b, (PrStatus *)w.status_mirror + slot)));
+        return check_launch("pr_finish");
     };
 
     const int poll = std::max(1, g->opt.poll_interval);
@@ -881,10 +895,21 @@ static int pr_iterate(gp_graph *g, const IterSpec &sp, float *out, PrStatus &fin
     cudaEventDestroy(evs[1]);
     if (st != GP_OK) return st;
     if (e != cudaSuccess) return set_error(GP_ERR_CUDA, "pagerank iteration: %s", cudaGetErrorString(e));
-    GP_CUDA(cudaMemcpyAsync(&fin, status, sizeof(PrStatus), cudaMemcpyDeviceToHost, s));
+    // the final status: one more gate-only launch (the iteration has stopped,
+    // so it changes nothing) writes it into mirror slot 2
+    {
+        PrArgs b = a;
+        b.k = issued + 1;
+        GP_LAUNCH("pr_finish", s, (k_pr_finish<<<1, 256, 0, s>>>(b, (PrStatus *)w.status_mirror + 2)));
+        GP_TRY(check_launch("pr_finish"));
+    }
     GP_CUDA(cudaStreamSynchronize(s));
-    if ((fin.iters_done & 1) && fin.iters_done > 0)
-        GP_CUDA(cudaMemcpyAsync(out, R[1], n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    memcpy(&fin, (const PrStatus *)w.status_host + 2, sizeof(fin));  // written by the kernel, complete after the sync
+    if ((fin.iters_done & 1) && fin.iters_done > 0) {
+        const int cb = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4 * (int64_t)g->num_sms));
+        GP_LAUNCH("copy_result", s, (k_copy_f32<<<cb, 256, 0, s>>>(n, R[1], out)));
+        GP_TRY(check_launch("copy_result"));
+    }
     return GP_OK;
 }
 

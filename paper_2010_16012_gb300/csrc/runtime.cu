@@ -88,7 +88,10 @@ static cudaMemPool_t lib_pool() {
 // mirrors of the kernels' status words); page-locking is a driver call that
 // pins pages and now and then takes milliseconds, so a freed block is kept and
 // handed out again for the same size (gp_pool_trim releases the kept ones).
-// Portable: one block may serve graphs on any device.
+// Portable: one block may serve graphs on any device.  Mapped: kernels may
+// write a block directly (pinned_device_ptr), so a status the host polls
+// needs no copy, which would queue behind any large transfer the caller has
+// in flight on the copy engines.
 static std::mutex g_pin_mu;
 static std::vector<std::pair<size_t, void *>> g_pin_free;
 constexpr size_t PIN_KEEP_MAX = 256;
@@ -106,7 +109,12 @@ int pinned_alloc(void **p, size_t bytes) {
             }
         }
     }
-    GP_CUDA(cudaHostAlloc(p, bytes, cudaHostAllocPortable));
+    GP_CUDA(cudaHostAlloc(p, bytes, cudaHostAllocPortable | cudaHostAllocMapped));
+    return GP_OK;
+}
+
+int pinned_device_ptr(void *host, void **dev) {
+    GP_CUDA(cudaHostGetDevicePointer(dev, host, 0));
     return GP_OK;
 }
 
@@ -120,6 +128,30 @@ void pinned_free(void *p, size_t bytes) {
         }
     }
     cudaFreeHost(p);
+}
+
+static __global__ void k_copy_bytes(const unsigned char *__restrict__ src, unsigned char *__restrict__ dst,
+                                    size_t bytes) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < bytes; i += stride) dst[i] = src[i];
+    __threadfence_system();
+}
+
+cudaError_t read_mapped(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return cudaStreamSynchronize(s);
+    const size_t cap = (bytes + 4095) & ~size_t(4095);  // pooled by size: a few distinct sizes
+    void *h = nullptr, *d = nullptr;
+    if (pinned_alloc(&h, cap) != GP_OK) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaHostGetDevicePointer(&d, h, 0);
+    if (e == cudaSuccess) {
+        const unsigned blocks = (unsigned)std::min<size_t>((bytes + 4095) / 4096, 64);
+        k_copy_bytes<<<blocks, 256, 0, s>>>((const unsigned char *)src, (unsigned char *)d, bytes);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) memcpy(dst, h, bytes);
+    pinned_free(h, cap);
+    return e;
 }
 
 static void pinned_release_all() {
@@ -492,8 +524,7 @@ int select_by_degree(const int64_t *off, int64_t n, int64_t lo, int64_t hi, Aren
     if (st == GP_OK) st = exclusive_scan(segc, segc, nseg, tmp, s);
     int64_t total = 0;
     if (st == GP_OK) {
-        cudaError_t e = cudaMemcpyAsync(&total, segc + nseg, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaError_t e = read_mapped(&total, segc + nseg, sizeof(int64_t), s);
         if (e != cudaSuccess) st = set_error(GP_ERR_CUDA, "selection count read-back: %s", cudaGetErrorString(e));
     }
     const int64_t keep = std::min(total, cap);
@@ -590,9 +621,8 @@ int build_hot(gp_graph *g, HotSet &h, int32_t slots, const int64_t *sel_off, con
         int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)g->num_sms * 8));
         if (e == cudaSuccess) {
             GP_LAUNCH("deg_hist", s, (k_deg_hist<<<blocks, 256, 0, s>>>(sel_off, n, hist)));
-            e = cudaMemcpyAsync(hh.data(), hist, HOT_HIST * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+            e = read_mapped(hh.data(), hist, HOT_HIST * sizeof(unsigned long long), s);
         }
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = set_error(GP_ERR_CUDA, "hot-set histogram: %s", cudaGetErrorString(e));
     }
     // bucket B: every vertex above B is taken, then the lowest ids of bucket B until `slots`
@@ -694,8 +724,7 @@ int build_bins(gp_graph *g, BigBins &b, const int64_t *off, int32_t light_max, i
         st = check_launch("chunk_counts");
         if (st == GP_OK) st = exclusive_scan(b.cstart, b.cstart, nbig, tmp, s);
         if (st == GP_OK) {
-            cudaError_t e = cudaMemcpyAsync(&nchunks, b.cstart + nbig, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            cudaError_t e = read_mapped(&nchunks, b.cstart + nbig, sizeof(int64_t), s);
             if (e != cudaSuccess) st = set_error(GP_ERR_CUDA, "chunk count read-back: %s", cudaGetErrorString(e));
         }
         if (st == GP_OK) st = b.mem.alloc(b.chunks, (size_t)std::max<int64_t>(nchunks, 1), s);
@@ -1005,9 +1034,8 @@ int gp_graph_upload(gp_graph **out, int64_t n, int64_t m, const int64_t *csr_off
             GP_LAUNCH("check_offsets", s, (k_check_offsets<<<blocks, 256, 0, s>>>(g->csr_off, n, m, err)));
             if (g->csc_off != g->csr_off)
                 GP_LAUNCH("check_offsets", s, (k_check_offsets<<<blocks, 256, 0, s>>>(g->csc_off, n, m, err + 1)));
-            e = cudaMemcpyAsync(herr, err, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+            e = read_mapped(herr, err, 4 * sizeof(unsigned), s);
         }
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return upload_fail(g, s, set_error(GP_ERR_CUDA, "offset check: %s", cudaGetErrorString(e)));
         if (herr[0] | herr[1])
             return upload_fail(g, s, set_error(GP_ERR_INVALID, "malformed %s offsets (code %u): need off[0]=0, off[n]=m, non-decreasing",
@@ -1018,8 +1046,7 @@ int gp_graph_upload(gp_graph **out, int64_t n, int64_t m, const int64_t *csr_off
             if (g->csc_idx != g->csr_idx)
                 GP_LAUNCH("check_indices", s, (k_check_indices<<<eb, 256, 0, s>>>(g->csc_idx, m, n, err + 3)));
         }
-        e = cudaMemcpyAsync(herr, err, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        e = read_mapped(herr, err, 4 * sizeof(unsigned), s);
         if (e != cudaSuccess) return upload_fail(g, s, set_error(GP_ERR_CUDA, "index check: %s", cudaGetErrorString(e)));
         if (herr[2] | herr[3])
             return upload_fail(g, s, set_error(GP_ERR_INVALID, "%s index outside [0, n)", herr[2] ? "CSR" : "CSC"));
@@ -1037,9 +1064,8 @@ int gp_graph_upload(gp_graph **out, int64_t n, int64_t m, const int64_t *csr_off
                 GP_LAUNCH("edge_fingerprint", s, (k_edge_fingerprint<<<blocks, 256, 0, s>>>(g->csc_off, g->csc_idx, g->csc_w, n, 1, 0, fp + 1)));
             else  // symmetric: the reversed edge multiset must equal the edge multiset
                 GP_LAUNCH("edge_fingerprint", s, (k_edge_fingerprint<<<blocks, 256, 0, s>>>(g->csr_off, g->csr_idx, g->csr_w, n, 0, 1, fp + 1)));
-            e = cudaMemcpyAsync(hfp, fp, sizeof(hfp), cudaMemcpyDeviceToHost, s);
+            e = read_mapped(hfp, fp, sizeof(hfp), s);
         }
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return upload_fail(g, s, set_error(GP_ERR_CUDA, "fingerprint: %s", cudaGetErrorString(e)));
         if (hfp[0] != hfp[1])
             return upload_fail(g, s, set_error(GP_ERR_INVALID, g->csc_off != g->csr_off
@@ -1055,9 +1081,8 @@ int gp_graph_upload(gp_graph **out, int64_t n, int64_t m, const int64_t *csr_off
         if (e == cudaSuccess) {
             GP_LAUNCH("degree_prep", s, (k_degree_prep<<<blocks, 256, 0, s>>>(g->csr_off, g->csc_off, g->csr_w, n,
                                                                              g->weighted, g->normalized, g->inv_deg, dst)));
-            e = cudaMemcpyAsync(&hs, dst, sizeof(hs), cudaMemcpyDeviceToHost, s);
+            e = read_mapped(&hs, dst, sizeof(hs), s);
         }
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return upload_fail(g, s, set_error(GP_ERR_CUDA, "degree prep: %s", cudaGetErrorString(e)));
         g->max_out = (int64_t)hs.max_out;
         g->max_in = (int64_t)hs.max_in;

@@ -55,6 +55,7 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(gp.gp_pr_stats) == 56
     assert ctypes.sizeof(gp.gp_kernel_time) == 64
     assert ctypes.sizeof(gp.gp_graph_info) == 88
+    assert ctypes.sizeof(gp.gp_bfs_summary) == 32
 
 
 def test_struct_layouts_match_c_compiler(tmp_path):
@@ -68,7 +69,7 @@ def test_struct_layouts_match_c_compiler(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if not cc:
         pytest.skip("no C compiler")
-    structs = {"gp_options": gp.gp_options, "gp_pr_stats": gp.gp_pr_stats, "gp_bfs_stats": gp.gp_bfs_stats,
+    structs = {"gp_options": gp.gp_options, "gp_pr_stats": gp.gp_pr_stats, "gp_bfs_stats": gp.gp_bfs_stats, "gp_bfs_summary": gp.gp_bfs_summary,
                "gp_batch_stats": gp.gp_batch_stats, "gp_tune_result": gp.gp_tune_result, "gp_sssp_stats": gp.gp_sssp_stats, "gp_tc_stats": gp.gp_tc_stats, "gp_fe_stats": gp.gp_fe_stats, "gp_bc_stats": gp.gp_bc_stats,
                "gp_kernel_time": gp.gp_kernel_time, "gp_graph_info": gp.gp_graph_info}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gp.h"', "int main(void) {"]
@@ -107,6 +108,8 @@ def test_host_argument_checks(lib):
     st = lib.gp_pagerank(None, 0, 0.85, 10, 0.0, None, None, None, None, None)
     assert st == gp.ERR_INVALID
     st = lib.gp_bfs(None, 0, 0, None, None, None, None)
+    assert st == gp.ERR_INVALID
+    st = lib.gp_bfs_multi(None, None, 1, 0, None, None, 0, None, None)
     assert st == gp.ERR_INVALID
     assert lib.gp_graph_free(None) == gp.OK
     assert lib.gp_options_default(None) == gp.ERR_INVALID

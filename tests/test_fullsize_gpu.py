@@ -109,6 +109,31 @@ def test_rmat22_bfs_auto(gp, rmat22):
         assert np.array_equal(lv, ref), s
 
 
+def test_rmat22_bfs_multi(gp, rmat22):
+    """All 64 benchmark searches in one gp_bfs_multi launch, as the benchmark
+    step runs them (default groups): every search's levels equal those of its
+    single-search launch (levels are unique), 8 of them checked by the edge
+    rule with valid parents, 3 bit for bit against the oracle, and their
+    summaries equal to the single-search statistics."""
+    import torch
+
+    g, G, O, srcs, _ = rmat22
+    esrc = edge_sources(g.csr_off)
+    levels, parents, summ = gp.bfs_multi(G, srcs, gp.AUTO)
+    for i, s in enumerate(srcs):
+        lv1, _, st = gp.bfs(G, int(s), gp.AUTO, want_parent=False)
+        assert torch.equal(levels[i], lv1), s
+        if i % 8 == 0:
+            lv, pa = levels[i].cpu().numpy(), parents[i].cpu().numpy()
+            assert check_levels_by_edges(esrc, g.csr_idx, int(s), lv) == 0, s
+            assert check_parents_np(g.csr_off, g.csr_idx, int(s), lv, pa) == 0, s
+            for k in ("levels", "switches", "reached", "edges_examined", "edges_reached"):
+                assert summ[i][k] == st[k], (s, k)
+        if i in (0, 31, 63):
+            ref, _ = O.bfs(int(s))
+            assert np.array_equal(levels[i].cpu().numpy(), ref), s
+
+
 def test_rmat22_bc(gp, rmat22):
     """Betweenness centrality on the benchmark graph: two sources against the
     oracle's Brandes vertex by vertex; the 16 sources of the measured case
