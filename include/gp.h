@@ -191,7 +191,12 @@ typedef struct gp_options {
                                  frontier's out-edges times fe_alpha exceed m */
     float bc_alpha;           /* betweenness centrality GP_AUTO: a step pulls when the push side's
                                  edges times bc_alpha exceed the pull side's */
-    int32_t reserved[2];
+    int32_t bfs_light_max;    /* BFS top-down levels (gp_bfs, gp_bfs_multi): frontier vertices with
+                                 more out-edges than this are expanded as chunk_edges-sized chunks
+                                 by whole warps, the others in 32-vertex tiles (default 32; its own
+                                 setting, since the push sweep's best push_light_max can be far
+                                 from the traversal's) */
+    int32_t reserved[1];
 } gp_options;
 
 /* Fill *opt with the built-in defaults. */
@@ -208,7 +213,7 @@ int gp_graph_get_options(const gp_graph *g, gp_options *opt);
 #define GP_TUNE_PULL 0x1u /* pull_light_max, chunk_edges, pull_hot_slots */
 #define GP_TUNE_PUSH 0x2u /* push_light_max, blocks_per_sm, push_hot_slots */
 #define GP_TUNE_AUTO 0x4u /* pr_auto_mode: the faster of pull and push for this graph */
-#define GP_TUNE_BFS 0x8u  /* bfs_alpha, bfs_beta */
+#define GP_TUNE_BFS 0x8u  /* bfs_light_max, bfs_alpha, bfs_beta */
 #define GP_TUNE_ALL 0xFu
 
 typedef struct gp_tune_result {

@@ -11,7 +11,8 @@
 //   push PageRank: push_light_max, then blocks_per_sm, then push_hot_slots;
 //   AUTO:          pr_auto_mode = whichever of pull and push sweeps faster
 //                  (the per-graph push/pull choice of the Generic-Switch idea, Section 5);
-//   BFS switch:    bfs_alpha, then bfs_beta (gp_bfs(GP_AUTO) from the given sources).
+//   BFS:           bfs_light_max, then bfs_alpha, then bfs_beta (gp_bfs(GP_AUTO)
+//                  from the given sources).
 // The best options are left set on the graph and returned.
 #include <algorithm>
 #include <cstring>
@@ -139,7 +140,8 @@ extern "C" int gp_autotune(gp_graph *g, unsigned what, const int32_t *sources, i
             st = try_values<int32_t>(g, best, push_ms, &gp_options::push_light_max, {8, 16, 32, 64}, s, push, evaluated);
             if (st == GP_OK) st = try_values<int32_t>(g, best, push_ms, &gp_options::blocks_per_sm, {4, 8, 12}, s, push, evaluated);
             if (st == GP_OK)
-                st = try_values<int32_t>(g, best, push_ms, &gp_options::push_hot_slots, {0, 8192, 16384, 24576}, s, push, evaluated);
+                st = try_values<int32_t>(g, best, push_ms, &gp_options::push_hot_slots,
+                                         {0, 8192, 16384, 24576, 32768, 40960, 49152}, s, push, evaluated);
             if (!memcmp(&before, &best, sizeof(best))) break;
         }
     }
@@ -154,6 +156,8 @@ extern "C" int gp_autotune(gp_graph *g, unsigned what, const int32_t *sources, i
     if (st == GP_OK && (what & GP_TUNE_BFS)) {
         st = bfs(bfs_ms);
         ++evaluated;
+        if (st == GP_OK)
+            st = try_values<int32_t>(g, best, bfs_ms, &gp_options::bfs_light_max, {8, 16, 32, 64, 128}, s, bfs, evaluated);
         if (st == GP_OK) st = try_values<float>(g, best, bfs_ms, &gp_options::bfs_alpha, {4.f, 8.f, 14.f, 24.f, 48.f}, s, bfs, evaluated);
         if (st == GP_OK) st = try_values<float>(g, best, bfs_ms, &gp_options::bfs_beta, {8.f, 24.f, 64.f}, s, bfs, evaluated);
     }

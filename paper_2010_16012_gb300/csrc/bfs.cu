@@ -752,12 +752,33 @@ void release_bfs_work(gp_graph *g, cudaStream_t s) {
     g->bfs = BfsWork();
 }
 
-static int ensure_bfs_work(gp_graph *g, cudaStream_t s) {
+// The out-degree bins top-down levels expand the frontier with: vertices above
+// bfs_light_max go by chunks.  The push sweep's bins when the two limits agree,
+// else the graph's BFS bins, built on first use for the current options.
+static int bfs_bins(gp_graph *g, const BigBins *&b, cudaStream_t s) {
+    if (g->opt.bfs_light_max == g->opt.push_light_max) {
+        b = &g->push_bins;
+        return GP_OK;
+    }
+    BigBins &own = g->bfs_bins;
+    if (own.light_max != g->opt.bfs_light_max || own.chunk_edges != g->opt.chunk_edges || !own.rank) {
+        const int st = build_bins(g, own, g->csr_off, g->opt.bfs_light_max, g->opt.chunk_edges, s);
+        if (st != GP_OK) {
+            own.mem.release(s);
+            own.rank = nullptr;  // rebuilt by the next call
+            return st;
+        }
+    }
+    b = &own;
+    return GP_OK;
+}
+
+static int ensure_bfs_work(gp_graph *g, const BigBins &bins, cudaStream_t s) {
     BfsWork &w = g->bfs;
     if (w.ready) return GP_OK;
     const size_t n = (size_t)std::max<int64_t>(g->n, 1);
     const size_t words = (n + 31) / 32;
-    const size_t hcap = (size_t)std::max<int64_t>(g->push_bins.nchunks, 1);
+    const size_t hcap = (size_t)std::max<int64_t>(bins.nchunks, 1);
     for (int i = 0; i < 2; ++i) {
         GP_TRY(w.mem.alloc(w.queue[i], n, s));
         GP_TRY(w.mem.alloc(w.hchunk[i], hcap, s));
@@ -795,17 +816,18 @@ static int ensure_bfs_work(gp_graph *g, cudaStream_t s) {
     return GP_OK;
 }
 
-// The fields of a search that depend only on the graph, its options and the mode.
-static void run_common(const gp_graph *g, int mode, BfsRun &R) {
+// The fields of a search that depend only on the graph, its options, the
+// top-down bins and the mode.
+static void run_common(const gp_graph *g, const BigBins &bins, int mode, BfsRun &R) {
     memset(&R, 0, sizeof(R));
     R.base.n = g->n;
     R.base.csr_off = g->csr_off;
     R.base.csc_off = g->csc_off;
     R.base.csr_idx = g->csr_idx;
     R.base.csc_idx = g->csc_idx;
-    R.base.push_rank = g->push_bins.rank;
-    R.base.push_cstart = g->push_bins.cstart;
-    R.base.push_chunks = g->push_bins.chunks;
+    R.base.push_rank = bins.rank;
+    R.base.push_cstart = bins.cstart;
+    R.base.push_chunks = bins.chunks;
     R.base.pull_chunks = g->pull_bins.chunks;
     R.base.pull_nchunks = g->pull_bins.nchunks;
     // every hub a lane defers has in-edge chunks: the probe is at least the pull light limit
@@ -823,7 +845,9 @@ static int bfs_run(const gp_graph *gc, int32_t src, int mode, const int8_t *dirs
     const int64_t n = g->n;
     if (src < 0 || (int64_t)src >= n) return set_error(GP_ERR_INVALID, "source %d outside [0, %lld)", src, (long long)n);
     if (!level_out) return set_error(GP_ERR_INVALID, "gp_bfs: level_out is NULL");
-    GP_TRY(ensure_bfs_work(g, s));
+    const BigBins *bins = nullptr;
+    GP_TRY(bfs_bins(g, bins, s));
+    GP_TRY(ensure_bfs_work(g, *bins, s));
     BfsWork &w = g->bfs;
     char *h = (char *)w.ctr_host;
     BfsSummary *hs = (BfsSummary *)h;
@@ -856,7 +880,7 @@ static int bfs_run(const gp_graph *gc, int32_t src, int mode, const int8_t *dirs
         parent = w.parent_dev;
     }
     BfsRun R;
-    run_common(g, mode, R);
+    run_common(g, *bins, mode, R);
     R.base.level = level;
     R.base.parent = parent;
     for (int i = 0; i < 2; ++i) {
@@ -945,7 +969,7 @@ struct MultiLayout {
     }
 };
 
-static int ensure_bfs_multi(gp_graph *g, int groups, int nsrc, cudaStream_t s) {
+static int ensure_bfs_multi(gp_graph *g, const BigBins &bins, int groups, int nsrc, cudaStream_t s) {
     BfsWork &w = g->bfs;
     if ((int)w.mgrp.size() >= groups && w.msrc_cap >= nsrc) return GP_OK;
     groups = std::max<int>(groups, (int)w.mgrp.size());
@@ -958,7 +982,7 @@ static int ensure_bfs_multi(gp_graph *g, int groups, int nsrc, cudaStream_t s) {
     w.msrc_cap = 0;
     const size_t n = (size_t)std::max<int64_t>(g->n, 1);
     const size_t words = (n + 31) / 32;
-    const size_t hcap = (size_t)std::max<int64_t>(g->push_bins.nchunks, 1);
+    const size_t hcap = (size_t)std::max<int64_t>(bins.nchunks, 1);
     std::vector<BfsWork::Group> grp((size_t)groups);
     for (auto &q : grp) {
         for (int i = 0; i < 2; ++i) {
@@ -1009,7 +1033,9 @@ static int bfs_multi(const gp_graph *gc, const int32_t *sources, int nsrc, int m
     }
     if (summary) memset(summary, 0, (size_t)nsrc * sizeof(gp_bfs_summary));
     if (nsrc == 0) return GP_OK;
-    GP_TRY(ensure_bfs_work(g, s));
+    const BigBins *bins = nullptr;
+    GP_TRY(bfs_bins(g, bins, s));
+    GP_TRY(ensure_bfs_work(g, *bins, s));
     BfsWork &w = g->bfs;
     if (w.mpending) {  // the previous asynchronous call: its barrier status, and its staged tables are free again
         GP_CUDA(cudaEventSynchronize(w.mdone_ev));
@@ -1027,7 +1053,7 @@ static int bfs_multi(const gp_graph *gc, const int32_t *sources, int nsrc, int m
     int G = groups > 0 ? groups : BFS_MULTI_GROUPS;
     G = std::max(1, std::min(std::min(std::min(G, nsrc), blocks), BFS_MULTI_MAX_GROUPS));
     const int bpg = blocks / G;
-    GP_TRY(ensure_bfs_multi(g, G, nsrc, s));
+    GP_TRY(ensure_bfs_multi(g, *bins, G, nsrc, s));
     const int gcap = (int)w.mgrp.size();
     const MultiLayout lay(gcap, w.msrc_cap);
     char *h = (char *)w.mhost;
@@ -1036,7 +1062,7 @@ static int bfs_multi(const gp_graph *gc, const int32_t *sources, int nsrc, int m
     memset(&M, 0, sizeof(M));
     for (int q = 0; q < G; ++q) {
         BfsRun &R = M.runs[q];
-        run_common(g, mode, R);
+        run_common(g, *bins, mode, R);
         const BfsWork::Group &b = w.mgrp[(size_t)q];
         for (int i = 0; i < 2; ++i) {
             R.queue[i] = b.queue[i];

@@ -217,6 +217,7 @@ struct gp_graph {
     gp_options opt;
     gp::BigBins pull_bins;  // by in-degree (CSC)
     gp::BigBins push_bins;  // by out-degree (CSR)
+    gp::BigBins bfs_bins;   // by out-degree at bfs_light_max (BFS top-down), when it differs from push_light_max
     gp::HotSet pull_hot;    // shared-memory contribution cache of the pull sweep
     gp::HotSet push_hot;    // shared-memory accumulators of the push scatter
     gp::PrWork pr;

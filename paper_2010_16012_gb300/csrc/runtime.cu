@@ -848,10 +848,11 @@ int gp_options_default(gp_options *opt) {
     opt->bfs_beta = 24.0f;
     opt->push_fp64_accum = -1;
     opt->pull_hot_slots = 20480;
-    opt->push_hot_slots = 16384;
+    opt->push_hot_slots = 32768;
     opt->sssp_alpha = 1.0f;
     opt->fe_alpha = 8.0f;
     opt->bc_alpha = 1.0f;
+    opt->bfs_light_max = 32;
     return GP_OK;
 }
 
@@ -949,6 +950,7 @@ int gp_profile_read(gp_kernel_time *out, int cap, int *count, int reset) {
 static int upload_fail(gp_graph *g, cudaStream_t s, int st) {
     g->pull_bins.mem.release(s);
     g->push_bins.mem.release(s);
+    g->bfs_bins.mem.release(s);
     g->pull_hot.mem.release(s);
     g->push_hot.mem.release(s);
     g->mem.release(s);
@@ -1111,6 +1113,7 @@ int gp_graph_free(gp_graph *g) {
     release_bc_work(g, s);
     g->pull_bins.mem.release(s);
     g->push_bins.mem.release(s);
+    g->bfs_bins.mem.release(s);
     g->pull_hot.mem.release(s);
     g->push_hot.mem.release(s);
     g->mem.release(s);
@@ -1136,8 +1139,8 @@ int gp_graph_info_get(const gp_graph *g, gp_graph_info *info) {
     info->isolated = g->isolated;
     info->symmetric = g->symmetric;
     info->weighted = g->weighted;
-    info->device_bytes = (int64_t)(g->mem.total + g->pull_bins.mem.total + g->push_bins.mem.total + g->pr.mem.total +
-                                   g->bfs.mem.total);
+    info->device_bytes = (int64_t)(g->mem.total + g->pull_bins.mem.total + g->push_bins.mem.total +
+                                   g->bfs_bins.mem.total + g->pr.mem.total + g->bfs.mem.total + g->bfs.mmem.total);
     return GP_OK;
 }
 
@@ -1156,7 +1159,8 @@ int gp_graph_set_options(gp_graph *g, const gp_options *opt, void *stream) {
         opt->blocks_per_sm < 1 || opt->blocks_per_sm > 32 || opt->poll_interval < 1 ||
         !(opt->bfs_alpha > 0.f) || !(opt->bfs_beta > 0.f) || !(opt->sssp_alpha > 0.f) || !(opt->fe_alpha > 0.f) || !(opt->bc_alpha > 0.f) || opt->pr_auto_mode < -1 || opt->pr_auto_mode > 1 ||
         opt->push_fp64_accum < -1 || opt->push_fp64_accum > 1 || opt->pull_hot_slots < 0 ||
-        opt->pull_hot_slots > 49152 || opt->push_hot_slots < 0 || opt->push_hot_slots > 49152)
+        opt->pull_hot_slots > 49152 || opt->push_hot_slots < 0 || opt->push_hot_slots > 49152 ||
+        opt->bfs_light_max < 0 || opt->bfs_light_max > (1 << 20))
         return set_error(GP_ERR_INVALID, "gp_graph_set_options: option out of range");
     cudaStream_t s = (cudaStream_t)stream;
     const gp_options old = g->opt;
@@ -1167,7 +1171,8 @@ int gp_graph_set_options(gp_graph *g, const gp_options *opt, void *stream) {
     if (st == GP_OK && (old.push_light_max != opt->push_light_max || old.chunk_edges != opt->chunk_edges))
         st = build_bins(g, g->push_bins, g->csr_off, opt->push_light_max, opt->chunk_edges, s);
     if (st == GP_OK && (old.blocks_per_sm != opt->blocks_per_sm || old.chunk_edges != opt->chunk_edges ||
-                        old.pull_light_max != opt->pull_light_max)) {
+                        old.pull_light_max != opt->pull_light_max || old.bfs_light_max != opt->bfs_light_max ||
+                        old.push_light_max != opt->push_light_max)) {
         // workspace sizes depend on the grid and the chunk count: rebuild lazily
         release_pr_work(g, s);
         release_bfs_work(g, s);

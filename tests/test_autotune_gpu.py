@@ -31,6 +31,7 @@ def test_autotune_and_cache(gp, tmp_path):
     assert o["pull_light_max"] in (8, 16, 32) and o["chunk_edges"] in (128, 256, 512)
     assert o["pull_hot_slots"] in (0, 8192, 16384, 20480, 24576) and o["push_light_max"] in (8, 16, 32, 64)
     assert o["pr_auto_mode"] in (gp.PUSH, gp.PULL) and o["bfs_alpha"] in (4, 8, 14, 24, 48)
+    assert o["bfs_light_max"] in (8, 16, 32, 64, 128)
     assert gp.options_dict(G.options()) == o
     # results with the tuned options
     O = oracle.OracleGraph.from_graph(g)

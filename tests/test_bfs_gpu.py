@@ -46,8 +46,10 @@ ZOO = [
     lambda: gg.erdos_renyi(3000, 9000, seed=4),
     lambda: gg.rmat(12, 16, seed=1),
 ]
-OPTS = [None, {"push_light_max": 0, "pull_light_max": 0, "chunk_edges": 32},
-        {"push_light_max": 3, "chunk_edges": 32}]
+OPTS = [None, {"push_light_max": 0, "pull_light_max": 0, "bfs_light_max": 0, "chunk_edges": 32},
+        {"push_light_max": 3, "chunk_edges": 32},  # BFS bins of their own (limit 32), push's at 3
+        {"bfs_light_max": 3, "chunk_edges": 32},   # BFS bins at 3, push's at their default
+        {"bfs_light_max": 1 << 20}]                # every frontier vertex in tiles
 MODES = [0, 1, 2]
 
 
@@ -282,3 +284,28 @@ def test_bottom_up_hubs_on_rmat(gp):
             for dirs in ([1], [1, 1, 0], [0, 1]):
                 lv, pa, _ = gp.bfs(G, int(src), dirs=dirs)
                 check(g, O, int(src), lv, pa)
+
+
+def test_bfs_light_limit_changes_between_searches(gp):
+    """The top-down bins follow bfs_light_max from one search to the next
+    (workspaces re-sized for the new chunk count), for single and grouped
+    searches; out-of-range values are rejected and leave the options as they were."""
+    g = gg.rmat(12, 16, seed=6)
+    G = gp.Graph.from_graphgen(g)
+    O = oracle.OracleGraph.from_graph(g)
+    srcs = gg.pick_vertices(g, 5, seed=3)
+    for lim in (32, 1, 0, 1 << 20, 8):
+        G.set_options(bfs_light_max=lim)
+        for s in srcs[:2]:
+            lv, pa, _ = gp.bfs(G, int(s), gp.PUSH)
+            check(g, O, int(s), lv, pa)
+        levels, parents, _ = gp.bfs_multi(G, srcs, gp.AUTO, groups=3)
+        for i, s in enumerate(srcs):
+            check(g, O, int(s), levels[i], parents[i])
+    before = gp.options_dict(G.options())
+    for bad in (-1, (1 << 20) + 1):
+        with pytest.raises(gp.GpError) as e:
+            G.set_options(bfs_light_max=bad)
+        assert e.value.status == gp.ERR_INVALID
+    assert gp.options_dict(G.options()) == before
+    G.free()

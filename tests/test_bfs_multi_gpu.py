@@ -66,7 +66,7 @@ def test_multi_small_options(gp):
     """Chunked hubs and the bottom-up hub pass inside groups of few blocks."""
     g = gg.rmat(12, 16, seed=5)
     G = gp.Graph.from_graphgen(g)
-    G.set_options(push_light_max=0, pull_light_max=0, chunk_edges=32)
+    G.set_options(push_light_max=0, pull_light_max=0, bfs_light_max=0, chunk_edges=32)
     O = oracle.OracleGraph.from_graph(g)
     sources = gg.pick_vertices(g, 9, seed=1)
     levels, parents, summary = gp.bfs_multi(G, sources, gp.AUTO, groups=9)
