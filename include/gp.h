@@ -600,6 +600,7 @@ typedef struct gp_batch_stats {
     float ms;        /* device time of the persistent launch (CUDA events) */
     int32_t blocks;  /* resident blocks of the cooperative launch */
     int32_t jobs;    /* PageRank: (graph, column slice) jobs the vectors were split into */
+    int32_t packed;  /* PageRank: columns their jobs left to packed jobs (see ppr_pack) */
 } gp_batch_stats;
 
 /* Tunables of a batch (gp_batch_autotune chooses them; results never depend on them). */
@@ -613,7 +614,10 @@ typedef struct gp_batch_options {
     float msbfs_beta;      /* BFS: back to top-down when the frontier is below n / beta */
     int32_t ppr_start;     /* PageRank start vector: 1 = each vector's seed one-hot e_seed
                               (default), 0 = uniform 1/n */
-    int32_t reserved[2];
+    int32_t ppr_pack;      /* PageRank: a job (one graph, one column slice) stops once at most
+                              this many of its columns still iterate; those continue, 32 to a
+                              job, in packed jobs after all slices (0 = never; at most 128) */
+    int32_t reserved[1];
 } gp_batch_options;
 
 int gp_batch_options_default(gp_batch_options *opt);

@@ -117,13 +117,13 @@ class gp_bc_stats(ctypes.Structure):
 
 class gp_batch_stats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int32), ("levels", ctypes.c_int32), ("ms", ctypes.c_float),
-                ("blocks", ctypes.c_int32), ("jobs", ctypes.c_int32)]
+                ("blocks", ctypes.c_int32), ("jobs", ctypes.c_int32), ("packed", ctypes.c_int32)]
 
 
 class gp_batch_options(ctypes.Structure):
     _fields_ = [("big_in_degree", ctypes.c_int32), ("chunk_edges", ctypes.c_int32), ("l2_budget_mb", ctypes.c_int32),
                 ("msbfs_alpha", ctypes.c_float), ("msbfs_beta", ctypes.c_float), ("ppr_start", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("ppr_pack", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class gp_batch_tune_result(ctypes.Structure):
@@ -616,7 +616,8 @@ class Batch:
         except Exception:
             pass
 
-    BATCH_OPTION_FIELDS = ("big_in_degree", "chunk_edges", "l2_budget_mb", "msbfs_alpha", "msbfs_beta", "ppr_start")
+    BATCH_OPTION_FIELDS = ("big_in_degree", "chunk_edges", "l2_budget_mb", "msbfs_alpha", "msbfs_beta", "ppr_start",
+                           "ppr_pack")
 
     def options(self) -> dict:
         o = gp_batch_options()
@@ -657,7 +658,8 @@ class Batch:
         st = gp_batch_stats()
         _check(load().gp_ppr_batched(self._h, _ptr(seeds), float(damping), int(iters), float(tol), optr, _ptr(done),
                                      ctypes.byref(st), _stream_ptr(stream)), "gp_ppr_batched")
-        return outs, done, {"sweeps": st.sweeps, "ms": st.ms, "blocks": st.blocks, "jobs": st.jobs}
+        return outs, done, {"sweeps": st.sweeps, "ms": st.ms, "blocks": st.blocks, "jobs": st.jobs,
+                            "packed": st.packed}
 
     def msbfs(self, sources, outs=None, stream=None):
         """sources: int array [ngraphs][nsrc] (nsrc <= 64).  Returns (list of [n_i, 64] int32 tensors, stats)."""

@@ -70,6 +70,13 @@ struct BJob {  // one graph and the column slice [c0, c0 + 32 * kpl)
     int32_t pad;
 };
 
+struct BPend {  // a PageRank column a job left iterating, for a packed job
+    int32_t graph;
+    int32_t col;    // its column in the graph's iterates
+    int32_t kdone;  // sweeps it has had
+    int32_t pad;
+};
+
 struct BatchDev {
     int ngraphs, K, nsrc;
     float d, one_minus_d;
@@ -89,7 +96,10 @@ struct BatchDev {
     const int32_t *seeds;   // [ngraphs][K]
     int32_t *iters_done;    // [ngraphs][K]
     const int32_t *sources; // [ngraphs][64] (MS-BFS)
-    int32_t *counters;      // [0] most PPR sweeps of any job, [1] BFS levels
+    int32_t *counters;      // [0] most PPR sweeps of any column, [1] BFS levels, [2] packed columns
+    int32_t pack_max;       // a job stops once at most this many of its columns iterate (0: never)
+    BPend *pend;            // [ngraphs * K] the columns left iterating, in job order
+    float *XP0, *XP1;       // [max n][32] iterates of a packed job
     unsigned long long *mcount;  // MS-BFS [2][ngraphs][4]: frontier vertices, their out-edges, open in-edges, new bits
     GridSync *sync;
 };
@@ -202,12 +212,27 @@ __device__ __forceinline__ float4 groups_total(Sum4 a) {
     return make_float4(a.hi[0] + a.lo[0], a.hi[1] + a.lo[1], a.hi[2] + a.lo[2], a.hi[3] + a.lo[3]);
 }
 
+// The columns one PageRank job iterates: a slice of a graph's own iterates
+// (pend == nullptr: columns c0 .. c0 + KS - 1 of X0/X1, rows K apart), or a
+// packed job over the batch's packed iterates (rows 32 apart), whose column j
+// continues the graph's column pend[j].col after pend[j].kdone sweeps.
+struct PView {
+    int graph;
+    float *X0, *X1;     // the start and the result are in X0
+    int ld;             // row stride of X0 and X1 (floats)
+    int c0;
+    const BPend *pend;  // packed job, or nullptr
+    int cnt;            // packed job: columns in use (the rest idle)
+    __device__ int col(int c) const { return pend ? pend[c].col : c0 + c; }
+    __device__ int kbase(int c) const { return pend ? pend[c].kdone : 0; }
+};
+
 // Writes the lane's four columns of row v of the slice of Y from the gathered
 // sum, carrying stopped columns forward; adds |y - x| of the columns still
 // iterating to the lane's residual slots (shared memory, one owner each).
-__device__ __forceinline__ void finish_seg(const BatchDev &B, const BJob &J, const float *Xc, float *Y, int64_t v,
+__device__ __forceinline__ void finish_seg(const BatchDev &B, const PView &V, const float *Xc, float *Y, int64_t v,
                                            int c4, float4 sum, float *my_res, const int *s_active) {
-    const int64_t o = v * B.K + J.c0 + 4 * c4;
+    const int64_t o = v * V.ld + V.c0 + 4 * c4;
     const float4 x = __ldcg(reinterpret_cast<const float4 *>(Xc + o));
     const float xs[4] = {x.x, x.y, x.z, x.w}, ss[4] = {sum.x, sum.y, sum.z, sum.w};
     float ys[4];
@@ -216,7 +241,7 @@ __device__ __forceinline__ void finish_seg(const BatchDev &B, const BJob &J, con
         const int c = 4 * c4 + q;
         ys[q] = xs[q];
         if (s_active[c]) {
-            const float base = (B.seeds[J.graph * B.K + J.c0 + c] == (int32_t)v) ? B.one_minus_d : 0.f;
+            const float base = (B.seeds[V.graph * B.K + V.col(c)] == (int32_t)v) ? B.one_minus_d : 0.f;
             ys[q] = base + B.d * ss[q];
             my_res[q] += fabsf(ys[q] - xs[q]);
         }
@@ -224,12 +249,15 @@ __device__ __forceinline__ void finish_seg(const BatchDev &B, const BJob &J, con
     *reinterpret_cast<float4 *>(Y + o) = make_float4(ys[0], ys[1], ys[2], ys[3]);
 }
 
-// One job: the slice's sweeps from 1/n to convergence.  Returns false when a
-// grid barrier gave up.
+// One job: the slice's sweeps from the start vector to convergence, or, for a
+// slice of the graph's own iterates, until at most B.pack_max of its columns
+// still iterate (those are then left, at their latest iterate, to a packed job).
+// Returns false when a grid barrier gave up.
 template <int KS>
-__device__ bool ppr_job(const BatchDev &B, const BJob &J, float (*s_res)[32][4], int *s_active) {
+__device__ bool ppr_job(const BatchDev &B, const PView &J, float (*s_res)[32][4], int *s_active) {
     constexpr int LPR = Lanes<KS>::LPR, NG = Lanes<KS>::NG;
     const int K = B.K;
+    const int ld = J.ld;
     const BGraph &G = B.graphs[J.graph];
     const int64_t n = G.n;
     const int lane = lane_id(), grp = lane / LPR, c4 = lane % LPR;
@@ -237,24 +265,33 @@ __device__ bool ppr_job(const BatchDev &B, const BJob &J, float (*s_res)[32][4],
     const int64_t gthread = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int64_t gwarp = gthread >> 5, nwarps = nthreads >> 5;
-    // start: every column at 1/n, or at its seed's one-hot vector
-    const float x0 = 1.0f / (float)n;
-    for (int64_t i = gthread; i < n * KS; i += nthreads) {
-        const int64_t v = i / KS;
-        const int c = (int)(i % KS);
-        G.X0[v * K + J.c0 + c] =
-            B.one_hot_start ? (B.seeds[J.graph * K + J.c0 + c] == (int32_t)v ? 1.0f : 0.0f) : x0;
+    if (!J.pend) {
+        // start: every column at 1/n, or at its seed's one-hot vector
+        const float x0 = 1.0f / (float)n;
+        for (int64_t i = gthread; i < n * KS; i += nthreads) {
+            const int64_t v = i / KS;
+            const int c = (int)(i % KS);
+            J.X0[v * ld + J.c0 + c] =
+                B.one_hot_start ? (B.seeds[J.graph * K + J.c0 + c] == (int32_t)v ? 1.0f : 0.0f) : x0;
+        }
+    } else {
+        // start: the packed columns' latest iterates (idle columns at zero)
+        for (int64_t i = gthread; i < n * KS; i += nthreads) {
+            const int64_t v = i / KS;
+            const int c = (int)(i % KS);
+            J.X0[v * ld + c] = c < J.cnt ? __ldcg(G.X0 + v * K + J.pend[c].col) : 0.f;
+        }
     }
-    for (int c = threadIdx.x; c < KS; c += blockDim.x) s_active[c] = 1;
+    for (int c = threadIdx.x; c < KS; c += blockDim.x) s_active[c] = !J.pend || (c < J.cnt && J.kbase(c) < B.iters);
     if (gthread < 3 * KS) B.res_acc[(gthread / KS) * K + (gthread % KS)] = 0.0;
     if (!grid_sync(B.sync, gridDim.x)) return false;
     const int64_t nseg = (n + BT_SEG - 1) / BT_SEG;
-    const float *Xj0 = G.X0 + J.c0, *Xj1 = G.X1 + J.c0;
+    const float *Xj0 = J.X0 + J.c0, *Xj1 = J.X1 + J.c0;
     int k = 1, last = 0;
     for (; k <= B.iters; ++k) {
-        const float *Xc = (k & 1) ? G.X0 : G.X1;
+        const float *Xc = (k & 1) ? J.X0 : J.X1;
         const float *Xs = (k & 1) ? Xj0 : Xj1;  // column c0 of the current iterate
-        float *Y = (k & 1) ? G.X1 : G.X0;
+        float *Y = (k & 1) ? J.X1 : J.X0;
         double *racc = B.res_acc + (k % 3) * K;
         if (blockIdx.x == 0)  // the ring slot of sweep k + 1 (last read two sweeps ago)
             for (int c = threadIdx.x; c < KS; c += blockDim.x) B.res_acc[((k + 1) % 3) * K + c] = 0.0;
@@ -269,13 +306,13 @@ __device__ bool ppr_job(const BatchDev &B, const BJob &J, float (*s_res)[32][4],
                 for (int64_t v = u * BT_SEG + grp; v < v1; v += NG) {
                     const int64_t b = G.csc_off[v], e = G.csc_off[v + 1];
                     if (e - b > B.big_min) continue;  // big vertex: finished in phase B
-                    const float4 sum = value4(gather_seg(G, Xs, K, b, e, 1, c4));
+                    const float4 sum = value4(gather_seg(G, Xs, ld, b, e, 1, c4));
                     finish_seg(B, J, Xc, Y, v, c4, sum, my_res, s_active);
                 }
             } else {
                 const int64_t c = u - nseg;
                 const BChunk ch = B.chunks[G.chunk0 + c];
-                const float4 sum = groups_total<KS>(gather_seg(G, Xs, K, ch.beg + grp, ch.beg + ch.len, NG, c4));
+                const float4 sum = groups_total<KS>(gather_seg(G, Xs, ld, ch.beg + grp, ch.beg + ch.len, NG, c4));
                 if (grp == 0) *reinterpret_cast<float4 *>(B.part + c * KS + 4 * c4) = sum;
             }
         }
@@ -313,23 +350,47 @@ __device__ bool ppr_job(const BatchDev &B, const BJob &J, float (*s_res)[32][4],
         for (int c = threadIdx.x; c < KS; c += blockDim.x) {
             if (!s_active[c]) continue;
             const double r = __ldcg(racc + c);
-            if (blockIdx.x == 0) B.iters_done[J.graph * K + J.c0 + c] = k;
-            if (r < B.tol)
+            const int kc = J.kbase(c) + k;  // the column's sweeps
+            if (blockIdx.x == 0) B.iters_done[J.graph * K + J.col(c)] = kc;
+            if (r < B.tol || kc >= B.iters)
                 s_active[c] = 0;
             else
                 any = 1;
         }
-        any = __syncthreads_or(any);
+        const int nact = __syncthreads_count(any);  // one column per thread (KS <= blockDim)
         last = k;
-        if (!any) break;
+        if (!nact) break;
+        if (!J.pend && nact <= B.pack_max) {
+            // the few columns left go to a packed job; block 0 lists them in column order
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                int at = atomicAdd(B.counters + 2, nact);
+                for (int c = 0; c < KS; ++c)
+                    if (s_active[c]) B.pend[at++] = BPend{J.graph, J.c0 + c, k, 0};
+            }
+            break;
+        }
     }
     // the slice's last iterate was written by sweep `last`: into X1 when odd
     if (last & 1)
         for (int64_t i = gthread; i < n * KS; i += nthreads) {
-            const int64_t o = (i / KS) * K + J.c0 + (i % KS);
-            G.X0[o] = __ldcg(G.X1 + o);
+            const int64_t o = (i / KS) * ld + J.c0 + (i % KS);
+            J.X0[o] = __ldcg(J.X1 + o);
         }
-    if (gthread == 0) B.counters[0] = max(B.counters[0], last);
+    if (J.pend) {
+        if (!grid_sync(B.sync, gridDim.x)) return false;
+        // the packed columns' results back into the graph's iterates
+        for (int64_t i = gthread; i < n * KS; i += nthreads) {
+            const int64_t v = i / KS;
+            const int c = (int)(i % KS);
+            if (c < J.cnt) G.X0[v * K + J.pend[c].col] = __ldcg(J.X0 + v * ld + c);
+        }
+    }
+    if (gthread == 0) {
+        // packed columns: their own counts (written by this block's threads before the last block barrier)
+        int most = J.pend ? 0 : last;
+        for (int c = 0; J.pend && c < J.cnt; ++c) most = max(most, B.iters_done[J.graph * K + J.pend[c].col]);
+        B.counters[0] = max(B.counters[0], most);
+    }
     return grid_sync(B.sync, gridDim.x);  // the next job reuses part and res_acc
 }
 
@@ -340,14 +401,27 @@ __global__ void __launch_bounds__(BT_THREADS, GP_BT_MINB) k_ppr_persistent(Batch
     __shared__ float s_res[BT_THREADS / 32][32][4];  // per lane: |y - x| of its four columns
     __shared__ int s_active[BT_MAX_KS];
     for (int ji = 0; ji < B.njobs; ++ji) {
-        const BJob J = B.jobs[ji];
+        const BJob Jb = B.jobs[ji];
+        const BGraph &G = B.graphs[Jb.graph];
+        const PView J = {Jb.graph, G.X0, G.X1, B.K, Jb.c0, nullptr, 0};
         bool ok;
-        switch (J.kpl) {
+        switch (Jb.kpl) {
             case 1: ok = ppr_job<32>(B, J, s_res, s_active); break;
             case 2: ok = ppr_job<64>(B, J, s_res, s_active); break;
             default: ok = ppr_job<128>(B, J, s_res, s_active); break;
         }
         if (!ok) return;
+    }
+    // the columns the jobs left: packed 32 at a time, a packed job never
+    // mixing graphs (the list is in job order, so a graph's columns are adjacent)
+    const int np = *(volatile int32_t *)(B.counters + 2);
+    for (int i = 0; i < np;) {
+        const int g = B.pend[i].graph;
+        int j = i + 1;
+        while (j < np && j - i < 32 && B.pend[j].graph == g) ++j;
+        const PView J = {g, B.XP0, B.XP1, 32, 0, B.pend + i, j - i};
+        if (!ppr_job<32>(B, J, s_res, s_active)) return;
+        i = j;
     }
 }
 
@@ -654,6 +728,7 @@ static int batch_layout(gp_batch *b, cudaStream_t s) {
     D.alpha = b->opt.msbfs_alpha;
     D.beta = b->opt.msbfs_beta;
     D.one_hot_start = b->opt.ppr_start;
+    D.pack_max = b->opt.ppr_pack;
     b->ppr_stale = b->bfs_stale = true;  // captured launches hold the old arguments
     return GP_OK;
 }
@@ -672,6 +747,7 @@ extern "C" int gp_batch_options_default(gp_batch_options *opt) {
     opt->msbfs_alpha = 16.0f;
     opt->msbfs_beta = 24.0f;
     opt->ppr_start = 1;
+    opt->ppr_pack = 16;
     return GP_OK;
 }
 
@@ -714,8 +790,10 @@ extern "C" int gp_batch_create(gp_batch **out, gp_graph *const *graphs, int ngra
     D.ngraphs = ngraphs;
     D.K = K;
     int st = GP_OK;
+    int64_t nmax = 1;
     for (int gi = 0; gi < ngraphs && st == GP_OK; ++gi) {
         gp_graph *g = graphs[gi];
+        nmax = std::max(nmax, g->n);
         BGraph &G = b->hg[gi];
         memset(&G, 0, sizeof(G));
         G.n = g->n;
@@ -740,6 +818,9 @@ extern "C" int gp_batch_create(gp_batch **out, gp_graph *const *graphs, int ngra
     if (st == GP_OK) st = b->mem.alloc(D.iters_done, (size_t)ngraphs * K, s);
     if (st == GP_OK) st = b->mem.alloc(b->counters, 8, s);
     if (st == GP_OK) st = b->mem.alloc(D.mcount, (size_t)ngraphs * 8, s);
+    if (st == GP_OK) st = b->mem.alloc(D.pend, (size_t)ngraphs * K, s);
+    if (st == GP_OK) st = b->mem.alloc(D.XP0, (size_t)nmax * 32, s);
+    if (st == GP_OK) st = b->mem.alloc(D.XP1, (size_t)nmax * 32, s);
     GridSync *sync = nullptr;
     if (st == GP_OK) st = b->mem.alloc(sync, 1, s);
     if (st != GP_OK) return fail(st);
@@ -765,7 +846,7 @@ extern "C" int gp_batch_set_options(gp_batch *b, const gp_batch_options *opt, vo
     if (!b || !opt) return set_error(GP_ERR_INVALID, "gp_batch_set_options: NULL argument");
     if (opt->big_in_degree < 0 || opt->chunk_edges < 32 || opt->chunk_edges > (1 << 20) || opt->l2_budget_mb < 1 ||
         opt->l2_budget_mb > (1 << 20) || !(opt->msbfs_alpha > 0.f) || !(opt->msbfs_beta > 0.f) ||
-        (opt->ppr_start != 0 && opt->ppr_start != 1))
+        (opt->ppr_start != 0 && opt->ppr_start != 1) || opt->ppr_pack < 0 || opt->ppr_pack > BT_MAX_KS)
         return set_error(GP_ERR_INVALID, "gp_batch_set_options: option out of range");
     const gp_batch_options old = b->opt;
     b->opt = *opt;
@@ -775,6 +856,7 @@ extern "C" int gp_batch_set_options(gp_batch *b, const gp_batch_options *opt, vo
     b->dev.alpha = opt->msbfs_alpha;
     b->dev.beta = opt->msbfs_beta;
     b->dev.one_hot_start = opt->ppr_start;
+    b->dev.pack_max = opt->ppr_pack;
     b->bfs_stale = b->ppr_stale = true;
     return GP_OK;
 }
@@ -856,6 +938,7 @@ extern "C" int gp_ppr_batched(gp_batch *b, const int32_t *seeds, float damping, 
         stats->ms = ms;
         stats->blocks = b->grid;
         stats->jobs = (int32_t)b->jobs.size();
+        stats->packed = b->hcounters[2];
     }
     if (hs.err) return set_error(GP_ERR_TIMEOUT, "batched PageRank: a grid barrier wait ran out");
     return GP_OK;

@@ -71,6 +71,52 @@ def test_ppr_batched_matches_oracle(gp, k, start):
     B.free()
 
 
+@pytest.mark.parametrize("pack", [1, 16, 128])
+def test_ppr_batched_packed_columns(gp, pack):
+    """Columns a job leaves to packed jobs (ppr_pack: 1, the default 16, and
+    128, which hands every column still iterating after the first sweep to
+    packed jobs) finish as the oracle does: each sampled vector within the
+    tolerance at its own sweep count, stopped at the oracle's first sweep under
+    tol (up to FP32 rounding: a packed job splits a column's sums over more
+    edge groups than its slice did, so its stop sweep can move within that
+    rounding window, as any change of the summation order can)."""
+    graphs = uneven_graphs() + [gg.rmat(13, 16, seed=46)]
+    G = [gp.Graph.from_graphgen(g) for g in graphs]
+    k = 128
+    B = gp.Batch(G, k_ppr=k)
+    seeds = np.stack([seeds_for(g, k, 210 + i) for i, g in enumerate(graphs)])
+    B.set_options(ppr_pack=0)
+    _, _, st0 = B.ppr(seeds, iters=500, tol=1e-6)
+    assert st0["packed"] == 0
+    B.set_options(ppr_pack=pack)
+    assert B.options()["ppr_pack"] == pack
+    outs, done, st = B.ppr(seeds, iters=500, tol=1e-6)
+    assert st["packed"] > 0 and st["sweeps"] == done.max()
+    rng = np.random.default_rng(pack)
+    rho = 8e-7
+    for i, g in enumerate(graphs):
+        O = oracle.OracleGraph.from_graph(g)
+        X = outs[i].cpu().numpy()
+        # the slowest columns (those most likely packed) and a few others
+        slow = np.argsort(done[i])[-6:].tolist()
+        for j in sorted(set(slow) | {0, k - 1, int(rng.integers(k))}):
+            e = np.zeros(g.n)
+            e[seeds[i, j]] = 1.0
+            kd = int(done[i, j])
+            ref, _, r, _ = O.pagerank(oracle.PULL, 0.85, iters=kd, personalization=e, x0=e)
+            err = np.abs(X[:, j].astype(np.float64) - ref)
+            assert err.max() <= MAX_ABS and err.sum() <= L1, (pack, i, j, err.max(), err.sum())
+            assert r < 1e-6 + rho, (pack, i, j, kd, r)
+            if kd > 1:
+                _, _, r_prev, _ = O.pagerank(oracle.PULL, 0.85, iters=kd - 1, personalization=e, x0=e)
+                assert r_prev >= 1e-6 - rho, (pack, i, j, kd, r_prev)
+    # the cap holds for packed columns too
+    B.set_options(ppr_pack=128)
+    _, done_c, st_c = B.ppr(seeds, iters=3, tol=1e-6)
+    assert done_c.max() <= 3 and st_c["sweeps"] <= 3
+    B.free()
+
+
 @pytest.mark.parametrize("k", [64, 128])
 def test_ppr_batched_matches_serial(gp, k):
     import torch
@@ -193,7 +239,8 @@ def test_batch_options_do_not_change_results(gp, oi):
 
 def test_batch_option_validation(gp):
     B = gp.Batch([gp.Graph.from_graphgen(gg.path(10))], k_ppr=32)
-    for bad in ({"chunk_edges": 8}, {"l2_budget_mb": 0}, {"msbfs_alpha": 0.0}, {"big_in_degree": -1}, {"ppr_start": 2}):
+    for bad in ({"chunk_edges": 8}, {"l2_budget_mb": 0}, {"msbfs_alpha": 0.0}, {"big_in_degree": -1}, {"ppr_start": 2},
+                {"ppr_pack": -1}, {"ppr_pack": 129}):
         with pytest.raises(gp.GpError):
             B.set_options(**bad)
 

@@ -30,5 +30,5 @@ def test_struct_layouts():
     import paper_2010_16012_gb300 as gp
 
     assert ctypes.sizeof(gp.gp_tune_result) == 80
-    assert ctypes.sizeof(gp.gp_batch_stats) == 20
+    assert ctypes.sizeof(gp.gp_batch_stats) == 24
     assert ctypes.sizeof(gp.gp_batch_options) == 32
