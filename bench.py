@@ -879,23 +879,17 @@ def run_batched(args, graphs_scales=None):
     max_err = max(float((xs[i][j] - outs[i][:, j]).abs().max()) for i in range(len(graphs)) for j in range(SAMPLE))
     nvec = len(graphs) * K
     edges = sum(g.m * int(done[i].sum()) for i, g in enumerate(graphs))
-    # roofline: compulsory bytes per sweep of a (graph, slice) job are the index
-    # stream and offsets (4m + 8n) plus the slice's iterate read once, written
-    # once and read for the residual (12 n KS); a graph runs until its slowest
-    # column stops.  Row gathers (m KS 4 bytes per job sweep) come from L2 by
-    # design and are reported as a rate beside it.
+    # roofline: compulsory bytes, whatever the slicing and packing: a graph's
+    # index stream and offsets (4m + 8n) once per sweep of its slowest column,
+    # and each column's iterate read once, written once and read for the
+    # residual (12 n) per sweep of its own.  Row gathers (4m bytes per column
+    # sweep) come from L2 by design and are reported as a rate beside it.
     bo = B.options()
-    budget = bo["l2_budget_mb"] << 20
-
-    def width(n):
-        return next((w for w in (128, 64) if w <= K and 2 * n * w * 4 <= budget), 32)
-
     comp_bytes = gath_bytes = 0.0
     for i, g in enumerate(graphs):
-        sw = int(done[i].max())
-        jobs = K // width(g.n)
-        comp_bytes += sw * (jobs * (4 * g.m + 8 * (g.n + 1)) + 12 * K * g.n)
-        gath_bytes += sw * g.m * K * 4.0
+        col_sweeps = float(done[i].sum())
+        comp_bytes += int(done[i].max()) * (4 * g.m + 8 * (g.n + 1)) + 12 * g.n * col_sweeps
+        gath_bytes += 4.0 * g.m * col_sweeps
     peak, peak_kind = measured_peak_gbs()
     kms = statistics.median(tk) if tk else None
     B.free()
