@@ -85,8 +85,17 @@ def test_rmat22_pagerank_to_tolerance(gp, rmat22, mode):
     # it stopped where the FP64 iteration first drops below tol, give or take the FP32 rounding of one sweep
     _, k_exact, _, conv = O.pagerank(oracle.PULL, 0.85, iters=300, tol=1e-7, nthreads=NT)
     assert conv and abs(k - k_exact) <= 1
-    mx, l1 = pr_errors(x, runs.at(k))
+    ref = runs.at(k)
+    mx, l1 = pr_errors(x, ref)
     assert mx <= MAX_ABS and l1 <= L1, (mode, k, mx, l1)
+    # the ranks above 1e-5 (mean rank 2.4e-7, so max-abs 1e-6 says little about
+    # them): relative error against the FP64 iterate, printed for the record;
+    # FP32 sums of a hub's in-list round to about 1e-6 relative per sweep,
+    # carried through the d-contraction as 1e-6 / (1 - d) ~ 7e-6
+    big = ref > 1e-5
+    rel = float((np.abs(x.cpu().numpy().astype(np.float64) - ref)[big] / ref[big]).max())
+    print(f"{mode}: {int(big.sum())} ranks above 1e-5, max relative error {rel:.2e}")
+    assert big.sum() > 0 and rel <= 1e-5, (mode, rel)
 
 
 def test_rmat22_bfs_auto(gp, rmat22):
