@@ -59,8 +59,8 @@ def parse_args(argv=None):
                    default=None,
                    help="profiling case: run only this part (fixed --sweeps for PageRank), no contract line")
     p.add_argument("--sweeps", type=int, default=4)
-    p.add_argument("--bfs-groups", type=int, default=0,
-                   help="groups of blocks of gp_bfs_multi in the step (0: the library's choice)")
+    p.add_argument("--groups", "--bfs-groups", dest="groups", type=int, default=0,
+                   help="groups of blocks of gp_bfs_multi (the step, the legs, --only bfs; 0: the library's choice)")
     p.add_argument("--batch-scale", type=int, default=None,
                    help="--only batched: one R-MAT graph of this scale instead of the 32-graph workload")
     p.add_argument("--delta", type=float, default=64.0, help="--only sssp: bucket width")
@@ -354,7 +354,7 @@ def run_ours(args, dist: Dist):
                 _, _, st = gp.bfs(G, int(s), gp.AUTO, level=lv_all[0], parent=pa_all[0])
                 bfs_stats[int(s)] = st
         else:
-            gp.bfs_multi(G, srcs, gp.AUTO, levels=lv_all, parents=pa_all, groups=args.bfs_groups, want_summary=False)
+            gp.bfs_multi(G, srcs, gp.AUTO, levels=lv_all, parents=pa_all, groups=args.groups, want_summary=False)
         torch.cuda.synchronize()
         bfs_ms = (time.perf_counter() - ta) * 1e3
         bfs_edges, switches = 0.0, 0
@@ -577,7 +577,7 @@ def run_legs(args, g2, srcs2, tuned_opts):
     legs["c2_bfs"] = {name: bfs_leg(gp, g2, G, srcs2, mode, peak, True, repeats=2)
                       for name, mode in (("top_down", gp.PUSH), ("bottom_up", gp.PULL), ("auto", gp.AUTO))}
     legs["c2_bfs"].update({name + "_multi": bfs_leg(gp, g2, G, srcs2, mode, peak, True, repeats=2,
-                                                     groups=args.bfs_groups)
+                                                     groups=args.groups)
                            for name, mode in (("top_down", gp.PUSH), ("bottom_up", gp.PULL), ("auto", gp.AUTO))})
     G.free()
     # C1
@@ -605,7 +605,7 @@ def run_legs(args, g2, srcs2, tuned_opts):
         c3[name] = pr_leg(gp, g3, G, mode, 20, peak)
     c3["bfs"] = {name: bfs_leg(gp, g3, G, s3, mode, peak, False, repeats=2)
                  for name, mode in (("top_down", gp.PUSH), ("bottom_up", gp.PULL), ("auto", gp.AUTO))}
-    c3["bfs"]["auto_multi"] = bfs_leg(gp, g3, G, s3, gp.AUTO, peak, False, repeats=2, groups=args.bfs_groups)
+    c3["bfs"]["auto_multi"] = bfs_leg(gp, g3, G, s3, gp.AUTO, peak, False, repeats=2, groups=args.groups)
     G.free()
     del g3
     legs["c3_er24"] = c3
@@ -669,7 +669,7 @@ def run_e2e(args, g, srcs, dist: Dist, tuned_opts=None):
             G.set_options(**tuned_opts)
         edges = 0.0
         first = not bfs_edges  # untimed first step: the sources' component sizes
-        _, _, summ = gp.bfs_multi(G, srcs, gp.AUTO, levels=lv_d, parents=pa_d, groups=args.bfs_groups,
+        _, _, summ = gp.bfs_multi(G, srcs, gp.AUTO, levels=lv_d, parents=pa_d, groups=args.groups,
                                   want_summary=first)
         if first:
             for s, st in zip(srcs, summ):
@@ -960,10 +960,10 @@ def run_only(args):
             torch.cuda.synchronize()
             gp.profile_read(reset=True)
             gp.profile_enable(True)
-        if args.only == "bfs" and args.bfs_groups > 0:
-            # all sources in one gp_bfs_multi launch with --bfs-groups groups
+        if args.only == "bfs" and args.groups > 0:
+            # all sources in one gp_bfs_multi launch with --groups groups
             bmode = {"push": gp.PUSH, "pull": gp.PULL, "auto": gp.AUTO}[args.mode]
-            _, _, summ = gp.bfs_multi(G, srcs, bmode, groups=args.bfs_groups)
+            _, _, summ = gp.bfs_multi(G, srcs, bmode, groups=args.groups)
             res = {"searches": len(summ), "levels": [x["levels"] for x in summ],
                    "reached": [x["reached"] for x in summ]}
         elif args.only == "bfs":
