@@ -345,8 +345,10 @@ __global__ void __launch_bounds__(512, GP_LIGHT_MIN_BLOCKS) k_pull_light(PrArgs 
     if (threadIdx.x == 0) a.partials[blockIdx.x] = r;
 }
 
-// c_hot[slot] = c[hot_id[slot]] for the sweep that reads c next.
-__global__ void k_hot_gather(const int32_t *hot_id, int64_t nhot, const float *c, float *c_hot) {
+// c_hot[slot] = c[hot_id[slot]] for the sweep that reads c next (none once
+// the iteration has stopped: the launches enqueued past that point return).
+__global__ void k_hot_gather(const int32_t *hot_id, int64_t nhot, const float *c, float *c_hot, const PrStatus *status) {
+    if (status && ((volatile const PrStatus *)status)->done) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nhot; i += stride) c_hot[i] = c[hot_id[i]];
 }
@@ -798,7 +800,7 @@ static int pr_iterate(gp_graph *g, const IterSpec &sp, float *out, PrStatus &fin
     auto enqueue_hot_gather = [&](const float *c_src) -> int {
         const int hb = (int)std::max<int64_t>(1, std::min<int64_t>((g->pull_hot.nhot + 255) / 256, 4096));
         GP_LAUNCH("hot_gather", s, (k_hot_gather<<<hb, 256, 0, s>>>(g->pull_hot.hot_id, g->pull_hot.nhot, c_src,
-                                                                    g->pull_hot.c_hot)));
+                                                                    g->pull_hot.c_hot, status)));
         return check_launch("hot_gather");
     };
     if (hot && !push) GP_TRY(enqueue_hot_gather(C[0]));
