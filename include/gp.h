@@ -379,7 +379,7 @@ typedef struct gp_bfs_summary {
  *               levels of search i (as gp_bfs's level_out).
  *   parent_out  NULL, or a host array of nsources device pointers (int32[n]
  *               each): a BFS parent per vertex (as gp_bfs's parent_out).
- *   groups      0: the library's choice (8); otherwise clamped to
+ *   groups      0: the library's choice (16); otherwise clamped to
  *               [1, min(nsources, resident blocks, 32)].
  *   summary     NULL, or host gp_bfs_summary[nsources] filled on return (the
  *               call then waits for the searches).

@@ -227,10 +227,10 @@ __device__ void bfs_topdown_step(const BfsArgs &a) {
 // then each lane writes its own word of the next frontier (zero on entry) and
 // of the candidates: each word has one writer, so vertex state needs no atomics.
 #ifndef GP_BFS_WARPS
-#define GP_BFS_WARPS 32
+#define GP_BFS_WARPS 16
 #endif
 #ifndef GP_BFS_MINB
-#define GP_BFS_MINB 1
+#define GP_BFS_MINB 2
 #endif
 constexpr int BFS_WARPS = GP_BFS_WARPS;  // warps per block of the persistent kernel
 #ifndef GP_BU_SCAN
@@ -490,8 +490,9 @@ struct BfsRun {
     GridSync *sync;
 };
 
-// 1024-thread blocks: fewer blocks arrive at each grid barrier (one global
-// counter), which is what a level's fixed cost is made of.
+// 512-thread blocks, two per SM (R-MAT 22, 64 searches: 11.5 ms one launch
+// per search and 5.8 ms in 16 groups, against 11.7 and 6.0 ms with one
+// 1024-thread block per SM, whose barriers have half the arrivals).
 constexpr int BFS_THREADS = BFS_WARPS * 32;
 
 // The outputs and source of one search.
@@ -1017,7 +1018,7 @@ static int ensure_bfs_multi(gp_graph *g, const BigBins &bins, int groups, int ns
 }
 
 // Groups when the caller leaves the choice to the library.
-constexpr int BFS_MULTI_GROUPS = 8;
+constexpr int BFS_MULTI_GROUPS = 16;
 
 static int bfs_multi(const gp_graph *gc, const int32_t *sources, int nsrc, int mode, int32_t *const *level_out,
                      int32_t *const *parent_out, int groups, gp_bfs_summary *summary, cudaStream_t s) {
