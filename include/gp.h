@@ -196,7 +196,9 @@ typedef struct gp_options {
                                  by whole warps, the others in 32-vertex tiles (default 32; its own
                                  setting, since the push sweep's best push_light_max can be far
                                  from the traversal's) */
-    int32_t reserved[1];
+    int32_t bfs_groups;       /* gp_bfs_multi called with groups 0: this many groups of blocks
+                                 (0 = the library's choice, 16; at most 32).  Changing it frees
+                                 the multi-search workspace, which the next call sizes anew */
 } gp_options;
 
 /* Fill *opt with the built-in defaults. */
@@ -213,7 +215,7 @@ int gp_graph_get_options(const gp_graph *g, gp_options *opt);
 #define GP_TUNE_PULL 0x1u /* pull_light_max, chunk_edges, pull_hot_slots */
 #define GP_TUNE_PUSH 0x2u /* push_light_max, blocks_per_sm, push_hot_slots */
 #define GP_TUNE_AUTO 0x4u /* pr_auto_mode: the faster of pull and push for this graph */
-#define GP_TUNE_BFS 0x8u  /* bfs_light_max, bfs_alpha, bfs_beta */
+#define GP_TUNE_BFS 0x8u  /* bfs_light_max, bfs_alpha, bfs_beta, then bfs_groups */
 #define GP_TUNE_ALL 0xFu
 
 typedef struct gp_tune_result {
@@ -379,7 +381,8 @@ typedef struct gp_bfs_summary {
  *               levels of search i (as gp_bfs's level_out).
  *   parent_out  NULL, or a host array of nsources device pointers (int32[n]
  *               each): a BFS parent per vertex (as gp_bfs's parent_out).
- *   groups      0: the library's choice (16); otherwise clamped to
+ *   groups      0: the graph's bfs_groups option (gp_autotune's GP_TUNE_BFS
+ *               sets it), or 16 when that is 0; the count is clamped to
  *               [1, min(nsources, resident blocks, 32)].
  *   summary     NULL, or host gp_bfs_summary[nsources] filled on return (the
  *               call then waits for the searches).

@@ -44,7 +44,7 @@ class gp_options(ctypes.Structure):
                 ("bfs_alpha", ctypes.c_float), ("bfs_beta", ctypes.c_float),
                 ("push_fp64_accum", ctypes.c_int32), ("pull_hot_slots", ctypes.c_int32),
                 ("push_hot_slots", ctypes.c_int32), ("sssp_alpha", ctypes.c_float), ("fe_alpha", ctypes.c_float),
-                ("bc_alpha", ctypes.c_float), ("bfs_light_max", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("bc_alpha", ctypes.c_float), ("bfs_light_max", ctypes.c_int32), ("bfs_groups", ctypes.c_int32)]
 
 
 class gp_graph_info(ctypes.Structure):
@@ -677,7 +677,7 @@ class Batch:
 
 OPTION_FIELDS = ["pull_light_max", "push_light_max", "chunk_edges", "blocks_per_sm", "poll_interval", "pr_auto_mode",
                  "bfs_alpha", "bfs_beta", "push_fp64_accum", "pull_hot_slots", "push_hot_slots", "sssp_alpha",
-                 "fe_alpha", "bc_alpha", "bfs_light_max"]
+                 "fe_alpha", "bc_alpha", "bfs_light_max", "bfs_groups"]
 
 
 def options_dict(o: gp_options) -> dict:

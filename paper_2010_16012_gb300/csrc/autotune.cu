@@ -12,7 +12,8 @@
 //   AUTO:          pr_auto_mode = whichever of pull and push sweeps faster
 //                  (the per-graph push/pull choice of the Generic-Switch idea, Section 5);
 //   BFS:           bfs_light_max, then bfs_alpha, then bfs_beta (gp_bfs(GP_AUTO)
-//                  from the given sources).
+//                  from the given sources), then bfs_groups (one gp_bfs_multi
+//                  over a batch of 64 searches, the given sources repeated).
 // The best options are left set on the graph and returned.
 #include <algorithm>
 #include <cstring>
@@ -69,6 +70,32 @@ int time_bfs(gp_graph *g, const int32_t *src, int nsrc, int32_t *level, cudaStre
     GP_CUDA(cudaEventRecord(t.b, s));
     GP_CUDA(cudaEventSynchronize(t.b));
     GP_CUDA(cudaEventElapsedTime(&ms_total, t.a, t.b));
+    return GP_OK;
+}
+
+// Searches per gp_bfs_multi call when the group count is timed.
+constexpr int TUNE_MULTI_SEARCHES = 64;
+
+// Milliseconds of one gp_bfs_multi(GP_AUTO) over `src` with the graph's
+// bfs_groups (one level vector per search): the faster of TUNE_REPS timed calls
+// after one that sizes the workspace.  The calls fill summaries, so each waits
+// for its searches and reports a barrier timeout at once.
+int time_bfs_multi(gp_graph *g, const std::vector<int32_t> &src, int32_t *const *levels, cudaStream_t s, float &ms) {
+    Timer t;
+    const int k = (int)src.size();
+    std::vector<gp_bfs_summary> sum((size_t)k);
+    GP_TRY(gp_bfs_multi(g, src.data(), k, GP_AUTO, levels, nullptr, 0, sum.data(), s));
+    float best = 0.f;
+    for (int r = 0; r < TUNE_REPS; ++r) {
+        GP_CUDA(cudaEventRecord(t.a, s));
+        GP_TRY(gp_bfs_multi(g, src.data(), k, GP_AUTO, levels, nullptr, 0, sum.data(), s));
+        GP_CUDA(cudaEventRecord(t.b, s));
+        GP_CUDA(cudaEventSynchronize(t.b));
+        float x = 0.f;
+        GP_CUDA(cudaEventElapsedTime(&x, t.a, t.b));
+        if (r == 0 || x < best) best = x;
+    }
+    ms = best;
     return GP_OK;
 }
 
@@ -160,6 +187,28 @@ extern "C" int gp_autotune(gp_graph *g, unsigned what, const int32_t *sources, i
             st = try_values<int32_t>(g, best, bfs_ms, &gp_options::bfs_light_max, {8, 16, 32, 64, 128}, s, bfs, evaluated);
         if (st == GP_OK) st = try_values<float>(g, best, bfs_ms, &gp_options::bfs_alpha, {4.f, 8.f, 14.f, 24.f, 48.f}, s, bfs, evaluated);
         if (st == GP_OK) st = try_values<float>(g, best, bfs_ms, &gp_options::bfs_beta, {8.f, 24.f, 64.f}, s, bfs, evaluated);
+        if (st == GP_OK) {
+            // the group count of several searches per launch, on a batch of
+            // TUNE_MULTI_SEARCHES searches with a level vector each (0 stands for
+            // the library's 16)
+            std::vector<int32_t> batch(TUNE_MULTI_SEARCHES);
+            for (int i = 0; i < TUNE_MULTI_SEARCHES; ++i) batch[(size_t)i] = sources[i % nsources];
+            DevBuf lv;
+            if (dev_alloc(lv, (size_t)TUNE_MULTI_SEARCHES * (size_t)g->n * sizeof(int32_t), s) == GP_OK) {
+                std::vector<int32_t *> ptr(TUNE_MULTI_SEARCHES);
+                for (int i = 0; i < TUNE_MULTI_SEARCHES; ++i) ptr[(size_t)i] = (int32_t *)lv.ptr + (size_t)i * (size_t)g->n;
+                float multi_ms = 0.f;
+                auto multi = [&](float &ms) { return time_bfs_multi(g, batch, ptr.data(), s, ms); };
+                st = multi(multi_ms);
+                ++evaluated;
+                if (st == GP_OK)
+                    st = try_values<int32_t>(g, best, multi_ms, &gp_options::bfs_groups, {0, 1, 2, 4, 8, 32}, s, multi,
+                                             evaluated);
+                dev_free(lv, s);
+            } else {
+                clear_error();  // no room for the batch's level vectors: the count is left as it is
+            }
+        }
     }
     cudaError_t e = cudaStreamSynchronize(s);
     dev_free(out, s);

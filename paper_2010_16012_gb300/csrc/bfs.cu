@@ -753,6 +753,24 @@ void release_bfs_work(gp_graph *g, cudaStream_t s) {
     g->bfs = BfsWork();
 }
 
+// The multi-search workspace alone (the group count changed); a pending
+// asynchronous gp_bfs_multi is waited for first.
+void release_bfs_multi(gp_graph *g, cudaStream_t s) {
+    BfsWork &w = g->bfs;
+    if (w.mdone_ev) cudaEventSynchronize(w.mdone_ev);
+    w.mpending = false;
+    pinned_free(w.mhost, w.mhost_bytes);
+    w.mhost = nullptr;
+    w.mhost_bytes = 0;
+    w.mmem.release(s);
+    w.mgrp.clear();
+    w.msrc_cap = 0;
+    w.mtab = nullptr;
+    w.msummary = nullptr;
+    w.msync = nullptr;
+    w.mdraw = nullptr;
+}
+
 // The out-degree bins top-down levels expand the frontier with: vertices above
 // bfs_light_max go by chunks.  The push sweep's bins when the two limits agree,
 // else the graph's BFS bins, built on first use for the current options.
@@ -1017,7 +1035,7 @@ static int ensure_bfs_multi(gp_graph *g, const BigBins &bins, int groups, int ns
     return GP_OK;
 }
 
-// Groups when the caller leaves the choice to the library.
+// Groups when neither the caller nor the graph's bfs_groups option chooses.
 constexpr int BFS_MULTI_GROUPS = 16;
 
 static int bfs_multi(const gp_graph *gc, const int32_t *sources, int nsrc, int mode, int32_t *const *level_out,
@@ -1051,7 +1069,7 @@ static int bfs_multi(const gp_graph *gc, const int32_t *sources, int nsrc, int m
     GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs_multi, BFS_THREADS, 0));
     if (per_sm < 1) return set_error(GP_ERR_UNSUPPORTED, "BFS kernel does not fit on an SM");
     const int blocks = per_sm * g->num_sms;
-    int G = groups > 0 ? groups : BFS_MULTI_GROUPS;
+    int G = groups > 0 ? groups : g->opt.bfs_groups > 0 ? g->opt.bfs_groups : BFS_MULTI_GROUPS;
     G = std::max(1, std::min(std::min(std::min(G, nsrc), blocks), BFS_MULTI_MAX_GROUPS));
     const int bpg = blocks / G;
     GP_TRY(ensure_bfs_multi(g, *bins, G, nsrc, s));

@@ -748,6 +748,7 @@ int build_bins(gp_graph *g, BigBins &b, const int64_t *off, int32_t light_max, i
 namespace gp {
 void release_pr_work(gp_graph *g, cudaStream_t s);
 void release_bfs_work(gp_graph *g, cudaStream_t s);
+void release_bfs_multi(gp_graph *g, cudaStream_t s);
 void release_sssp_work(gp_graph *g, cudaStream_t s);
 void release_fe_work(gp_graph *g, cudaStream_t s);
 void release_bc_work(gp_graph *g, cudaStream_t s);
@@ -1160,7 +1161,7 @@ int gp_graph_set_options(gp_graph *g, const gp_options *opt, void *stream) {
         !(opt->bfs_alpha > 0.f) || !(opt->bfs_beta > 0.f) || !(opt->sssp_alpha > 0.f) || !(opt->fe_alpha > 0.f) || !(opt->bc_alpha > 0.f) || opt->pr_auto_mode < -1 || opt->pr_auto_mode > 1 ||
         opt->push_fp64_accum < -1 || opt->push_fp64_accum > 1 || opt->pull_hot_slots < 0 ||
         opt->pull_hot_slots > 49152 || opt->push_hot_slots < 0 || opt->push_hot_slots > 49152 ||
-        opt->bfs_light_max < 0 || opt->bfs_light_max > (1 << 20))
+        opt->bfs_light_max < 0 || opt->bfs_light_max > (1 << 20) || opt->bfs_groups < 0 || opt->bfs_groups > 32)
         return set_error(GP_ERR_INVALID, "gp_graph_set_options: option out of range");
     cudaStream_t s = (cudaStream_t)stream;
     const gp_options old = g->opt;
@@ -1179,6 +1180,8 @@ int gp_graph_set_options(gp_graph *g, const gp_options *opt, void *stream) {
         release_sssp_work(g, s);
         release_fe_work(g, s);
         release_bc_work(g, s);
+    } else if (st == GP_OK && old.bfs_groups != opt->bfs_groups) {
+        release_bfs_multi(g, s);  // sized for the old group count
     }
     if (st != GP_OK) {
         g->opt = old;

@@ -31,7 +31,7 @@ def test_autotune_and_cache(gp, tmp_path):
     assert o["pull_light_max"] in (8, 16, 32) and o["chunk_edges"] in (128, 256, 512)
     assert o["pull_hot_slots"] in (0, 8192, 16384, 20480, 24576) and o["push_light_max"] in (8, 16, 32, 64)
     assert o["pr_auto_mode"] in (gp.PUSH, gp.PULL) and o["bfs_alpha"] in (4, 8, 14, 24, 48)
-    assert o["bfs_light_max"] in (8, 16, 32, 64, 128)
+    assert o["bfs_light_max"] in (8, 16, 32, 64, 128) and o["bfs_groups"] in (0, 1, 2, 4, 8, 32)
     assert gp.options_dict(G.options()) == o
     # results with the tuned options
     O = oracle.OracleGraph.from_graph(g)
@@ -44,6 +44,9 @@ def test_autotune_and_cache(gp, tmp_path):
     lref, _ = O.bfs(int(srcs[0]))
     lv, _, _ = gp.bfs(G, int(srcs[0]), gp.AUTO)
     assert np.array_equal(lv.cpu().numpy(), lref)
+    lvs, _, _ = gp.bfs_multi(G, srcs, gp.AUTO)  # the tuned group count
+    for i, s in enumerate(srcs):
+        assert np.array_equal(lvs[i].cpu().numpy(), O.bfs(int(s))[0])
     # a second graph handle of the same graph takes the cached options without timing
     G2 = gp.Graph.from_graphgen(g)
     r2 = gp.autotune(G2, gp.TUNE_ALL, sources=srcs, cache=path)

@@ -146,3 +146,27 @@ def test_multi_rejects_bad_input(gp):
     lv, pa, sm = gp.bfs_multi(G, np.array([3], dtype=np.int32))
     check_all(g, O, [3], lv, pa, sm)
     G.free()
+
+
+def test_multi_groups_option(gp):
+    """groups 0 takes the graph's bfs_groups option; changing the option frees
+    the multi-search workspace, which the next call sizes for the new count;
+    results never depend on it.  Out-of-range values are rejected."""
+    g = gg.rmat(12, 16, seed=6)
+    G = gp.Graph.from_graphgen(g)
+    O = oracle.OracleGraph.from_graph(g)
+    sources = gg.pick_vertices(g, 13, seed=5)
+    assert G.options().bfs_groups == 0  # the library's choice
+    for k in (32, 1, 5, 0, 2):
+        G.set_options(bfs_groups=k)
+        levels, parents, summary = gp.bfs_multi(G, sources, gp.AUTO)
+        check_all(g, O, sources, levels, parents, summary)
+        # an explicit count still wins over the option
+        levels, parents, summary = gp.bfs_multi(G, sources[:4], gp.PULL, groups=3)
+        check_all(g, O, sources[:4], levels, parents, summary)
+    for bad in (-1, 33):
+        with pytest.raises(gp.GpError) as e:
+            G.set_options(bfs_groups=bad)
+        assert e.value.status == gp.ERR_INVALID
+    assert G.options().bfs_groups == 2
+    G.free()
