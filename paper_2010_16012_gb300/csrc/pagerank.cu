@@ -89,6 +89,16 @@ __device__ __forceinline__ float base_term(const PrArgs &a, int64_t v) {
 __device__ __forceinline__ float post_factor(const PrArgs &a, int64_t v) { return a.post_scale ? a.post_scale[v] : 1.f; }
 __device__ __forceinline__ float c_factor(const PrArgs &a, int64_t v) { return a.cmul ? a.cmul[v] : 1.f; }
 
+// Whether the iteration has stopped, read by one thread per block: every warp
+// loading the flag itself would queue thousands of requests on the one L2 line
+// that holds it at each launch.  Called by all threads of the block.
+__device__ __forceinline__ bool pr_stopped(const PrStatus *status) {
+    __shared__ int stop;
+    if (threadIdx.x == 0) stop = ((volatile const PrStatus *)status)->done;
+    __syncthreads();
+    return stop != 0;
+}
+
 // Convergence gate at the start of sweep k: every block reduces the residual
 // partials of sweep k-1 in the same order, so all blocks take the same
 // decision; block 0 records it.  Returns true when the iteration has stopped.
@@ -266,7 +276,7 @@ constexpr int LIGHT_UNROLL = 8;  // in-edges of a light vertex in flight per lan
 template <bool W, bool HOT>
 __global__ void __launch_bounds__(512, GP_LIGHT_MIN_BLOCKS) k_pull_light(PrArgs a) {
     __shared__ double sm[32];
-    if (((volatile PrStatus *)a.status)->done) return;
+    if (pr_stopped(a.status)) return;
     const int lane = lane_id();
     ResSum res;
     const int64_t n = a.n;
@@ -348,7 +358,7 @@ __global__ void __launch_bounds__(512, GP_LIGHT_MIN_BLOCKS) k_pull_light(PrArgs 
 // c_hot[slot] = c[hot_id[slot]] for the sweep that reads c next (none once
 // the iteration has stopped: the launches enqueued past that point return).
 __global__ void k_hot_gather(const int32_t *hot_id, int64_t nhot, const float *c, float *c_hot, const PrStatus *status) {
-    if (status && ((volatile const PrStatus *)status)->done) return;
+    if (status && pr_stopped(status)) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nhot; i += stride) c_hot[i] = c[hot_id[i]];
 }
@@ -506,7 +516,7 @@ __global__ void __launch_bounds__(1024) k_push_scatter(PrArgs a) {
 template <class T>
 __global__ void __launch_bounds__(256) k_push_epilogue(PrArgs a) {
     __shared__ double sm[32];
-    if (((volatile PrStatus *)a.status)->done) return;
+    if (pr_stopped(a.status)) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     ResSum res;
     float *x_reset = const_cast<float *>(a.x);
