@@ -875,10 +875,18 @@ static int pr_iterate(gp_graph *g, const IterSpec &sp, float *out, PrStatus &fin
         if (st == GP_OK) st = enqueue_finish(iters + 1, 0);
         issued = iters;
     } else {
+        // Sweeps worth enqueuing: the cap, lowered once two polls give the
+        // residual's rate of decrease to the predicted stopping sweep plus one
+        // (sweeps enqueued past the stop only return at once, but each still costs
+        // a few microseconds of launches per kernel); raised again a batch at a
+        // time if the iteration outlives the prediction.
+        int limit = iters;
+        int k_last = 0;
+        double r_last = 0.0;
         while (st == GP_OK) {
             const int slot = batch & 1;
-            if (!stop && issued < iters && pending[slot] < 0) {
-                const int kb = std::min(poll, iters - issued);
+            if (!stop && issued < limit && pending[slot] < 0) {
+                const int kb = std::min(poll, limit - issued);
                 for (int i = 0; i < kb && st == GP_OK; ++i) st = enqueue_sweep(++issued);
                 if (st == GP_OK) st = enqueue_finish(issued + 1, slot);
                 if (st == GP_OK) {
@@ -889,7 +897,13 @@ static int pr_iterate(gp_graph *g, const IterSpec &sp, float *out, PrStatus &fin
                 continue;
             }
             const int os = oldest & 1;
-            if (pending[os] < 0) break;  // nothing outstanding
+            if (pending[os] < 0) {  // nothing outstanding
+                if (!stop && issued < iters) {
+                    limit = std::min(iters, issued + poll);
+                    continue;
+                }
+                break;
+            }
             cudaError_t e = cudaEventSynchronize(evs[os]);
             if (e != cudaSuccess) {
                 st = set_error(GP_ERR_CUDA, "pagerank poll: %s", cudaGetErrorString(e));
@@ -897,7 +911,19 @@ static int pr_iterate(gp_graph *g, const IterSpec &sp, float *out, PrStatus &fin
             }
             pending[os] = -1;
             ++oldest;
-            if (((PrStatus *)w.status_host)[os].done) stop = true;
+            const PrStatus ps = ((const PrStatus *)w.status_host)[os];
+            if (ps.done) {
+                stop = true;
+            } else {
+                if (k_last > 0 && ps.iters_done > k_last && ps.residual > 0.0 && ps.residual < r_last) {
+                    const double rate = std::pow(ps.residual / r_last, 1.0 / (ps.iters_done - k_last));
+                    const double more = std::ceil(std::log(sp.tol / ps.residual) / std::log(rate));
+                    if (more >= 0.0 && more < (double)iters)
+                        limit = std::max(issued, std::min(iters, ps.iters_done + (int)more + 1));
+                }
+                k_last = ps.iters_done;
+                r_last = ps.residual;
+            }
             if (stop && pending[oldest & 1] < 0) break;
             if (!stop && issued >= iters && pending[oldest & 1] < 0) break;
         }
