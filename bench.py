@@ -422,7 +422,7 @@ def run_ours(args, dist: Dist):
                         "frac": round(ach / peak, 4), "traffic": captured_traffic(top[0]), "peak_kind": peak_kind,
                         "bytes_per_launch": int(by / real), "avg_launch_ms": round(top[2] / real, 5),
                         "share": round(top[2] / total_kernel_ms, 4)}
-    # the pull sweep as a whole (both pull kernels): the benchmark spec's 40%-of-HBM figure
+    # the pull sweep as a whole (both pull kernels), the figure the 40%-of-HBM target is set on
     pull_sweep = None
     if "pull_light" in work and work["pull_light"][1]:
         tk = {k[0]: k for k in kt}
