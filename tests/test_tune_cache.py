@@ -14,6 +14,9 @@ def test_key_and_roundtrip(tmp_path, monkeypatch):
     path = str(tmp_path / "sub" / "tune.json")
     opts = gp.options_dict(gp.default_options())
     assert set(opts) == set(gp.OPTION_FIELDS)
+    # every field of gp_options is cached (a tuned value left out would be lost on a cache hit)
+    assert set(opts) == {f for f, _ in gp.gp_options._fields_ if not f.startswith("reserved")}
+    assert opts["bfs_groups"] == 0 and opts["bfs_light_max"] == 32 and opts["pull_hot_slots"] == 20480
     gp.tune_cache_store(path, k1, {"options": opts, "evaluated": 3})
     gp.tune_cache_store(path, "other", {"options": opts, "evaluated": 1})
     data = gp.tune_cache_load(path)
