@@ -919,7 +919,7 @@ static int pr_iterate(gp_graph *g, const IterSpec &sp, float *out, PrStatus &fin
                     const double rate = std::pow(ps.residual / r_last, 1.0 / (ps.iters_done - k_last));
                     const double more = std::ceil(std::log(sp.tol / ps.residual) / std::log(rate));
                     if (more >= 0.0 && more < (double)iters)
-                        limit = std::max(issued, std::min(iters, ps.iters_done + (int)more + 1));
+                        limit = std::max<int64_t>(issued, std::min<int64_t>(iters, (int64_t)ps.iters_done + (int64_t)more + 1));
                 }
                 k_last = ps.iters_done;
                 r_last = ps.residual;
