@@ -5,7 +5,6 @@ once; a BFS level's bytes follow its per-level counts; a traffic row counts only
 while its source key matches."""
 import types
 
-
 import bench
 import graphgen as gg
 
