@@ -171,7 +171,12 @@ typedef struct gp_options {
     int32_t push_light_max;   /* out-degree <= this: same for the push scatter and top-down BFS */
     int32_t chunk_edges;      /* edges per warp chunk for vertices above the light limits */
     int32_t blocks_per_sm;    /* resident blocks per SM for the grid-stride sweep kernels */
-    int32_t poll_interval;    /* PageRank sweeps enqueued between convergence read-backs */
+    int32_t poll_interval;    /* PageRank sweeps enqueued between convergence read-backs (at
+                                 most two batches in flight; once two read-backs give the
+                                 residual's rate of decrease, sweeps are enqueued only up to the
+                                 predicted stopping sweep plus one, then a batch at a time if
+                                 the iteration runs longer; the sweeps performed do not depend
+                                 on it) */
     int32_t pr_auto_mode;     /* what GP_AUTO means for PageRank: GP_PUSH, GP_PULL, or -1 = rule */
     float bfs_alpha;          /* top-down -> bottom-up when m_f > m_u / alpha */
     float bfs_beta;           /* bottom-up -> top-down when n_f < n / beta (frontier shrinking) */
