@@ -245,9 +245,12 @@ def measured_peak_gbs():
 
 # ------------------------------------------------------------------ algorithmic bytes per kernel launch
 
-def kernel_bytes(g, opt) -> dict:
+def kernel_bytes(g, opt, l2_bytes=None) -> dict:
     """Compulsory bytes of one (working) launch of each PageRank sweep kernel;
-    random re-gathers that miss L2 are not counted."""
+    random re-gathers that miss L2 are not counted.  The push accumulator is
+    FP64 unless push_fp64_accum turns it off, or leaves the choice to the library
+    (-1) and the library picks FP32: 8n bytes above half of `l2_bytes` and no
+    vertex with more than 4096 in-edges."""
     n, m = g.n, g.m
     din, dout = g.in_degree(), g.out_degree()
     C = opt.chunk_edges
@@ -257,6 +260,9 @@ def kernel_bytes(g, opt) -> dict:
     ch_in = int(((din[big_in] + C - 1) // C).sum())
     nb_in = int(big_in.sum())
     ch_out = int(((dout[big_out] + C - 1) // C).sum())
+    mode = getattr(opt, "push_fp64_accum", -1)
+    fp64 = mode == 1 or (mode == -1 and not (l2_bytes is not None and 8 * n > l2_bytes // 2
+                                             and int(din.max(initial=0)) <= 4096))
     return {
         # big in-edge lists: indices + chunk table + chunk partials written
         "pull_big": 4 * e_big_in + 16 * ch_in + 4 * ch_in,
@@ -264,8 +270,9 @@ def kernel_bytes(g, opt) -> dict:
         "pull_light": 4 * (m - e_big_in) + 8 * (n + 1) + 4 * n * 5 + 4 * ch_in + 12 * nb_in,
         # all out-edge lists + offsets + c + y read-modify-write + chunk table
         "push_scatter": 4 * m + 8 * (n + 1) + 4 * n + 8 * n + 16 * ch_out,
-        # y, x, inv_deg read; c and the reset buffer written
-        "push_epilogue": 20 * n,
+        # FP64: the accumulator read and reset, x and inv_deg read, y and c' written;
+        # FP32: y, x, inv_deg read, y, c' and the next accumulator (x) written
+        "push_epilogue": (32 if fp64 else 24) * n,
     }
 
 
@@ -314,7 +321,7 @@ def run_ours(args, dist: Dist):
     tuned_opts = tuned["options"]
     opt_struct = G0.options()
     G0.free()
-    kb = kernel_bytes(g, opt_struct)
+    kb = kernel_bytes(g, opt_struct, getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", None))
     pr_kernels = {gp.PULL: ("pull_big", "pull_light"), gp.PUSH: ("push_scatter", "push_epilogue")}
     bfs_stats = {}
     n_in = int(np.count_nonzero(np.diff(g.csc_off)))  # vertices with in-edges (every reached vertex has one)

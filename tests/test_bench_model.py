@@ -43,7 +43,13 @@ def test_pull_kernels_split_the_index_stream():
     # every vertex light: no big kernel bytes at all
     kb = bench.kernel_bytes(g, _opts(pull_light_max=int(din.max())))
     assert kb["pull_big"] == 0
-    assert kb["push_epilogue"] == 20 * n
+    # the push epilogue: FP64 accumulator (default) 32n, FP32 24n, as the library's rule picks
+    assert kb["push_epilogue"] == 32 * n
+    assert bench.kernel_bytes(g, _opts(push_fp64_accum=0))["push_epilogue"] == 24 * n
+    assert bench.kernel_bytes(g, _opts(push_fp64_accum=1), l2_bytes=1024)["push_epilogue"] == 32 * n
+    small_l2 = 8 * n  # the FP64 array is twice half the L2
+    want = 24 if int(din.max()) <= 4096 else 32
+    assert bench.kernel_bytes(g, _opts(), l2_bytes=small_l2)["push_epilogue"] == want * n
 
 
 def test_push_kernel_counts_every_out_edge():
